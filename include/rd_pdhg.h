@@ -1,0 +1,191 @@
+/*
+ * rd_pdhg.h -- C ABI of the GB300 G-prox PDHG solver for implicit reaction-diffusion steps.
+ *
+ * Method (arxiv 2305.03945, "A first-order computational algorithm for reaction-diffusion type
+ * equations via primal-dual hybrid gradient method"):
+ *   one implicit (or semi-implicit) time step U^k -> U^{k+1} of a reaction-diffusion equation on
+ *   a finite-difference grid is the root of a nonlinear map F (Section 2.1, eq. F(U) rd
+ *   equation).  F(U) = 0 is rewritten as the saddle problem min_U max_P P^T F(U) (Section 2.1,
+ *   eq. illustrate saddle) and solved by the linearised G-prox PDHG iteration
+ *     P_{n+1} = P_n + tau_p G^{-1} F(U_n)                       (eq. G-prox ... dynamic 1)
+ *     P~      = P_{n+1} + omega (P_{n+1} - P_n)                  (eq. G-prox ... dynamic 2)
+ *     U_{n+1} = U_n - tau_u dF(U_n)^T P~                         (eq. G-prox ... dynamic 3)
+ *   from U_0 = U^k, P_0 = 0, until ||Res(U_n)||_2 <= delta (Section 2.1, stopping criterion),
+ *   with G = A_lin^2 inverted by 2-D FFT (periodic) or DCT-II (Neumann) (Section 2.1,
+ *   "Choosing the matrix G", Remark 1).  Algorithm 1 is the outer time loop.
+ *
+ * Everything runs on ONE CUDA device in hand-written sm_103a kernels.  Unless stated otherwise
+ * every pointer named "device" is a CUDA device pointer the CALLER owns; the handle owns all
+ * internal workspaces, allocated once by rd_pdhg_create and freed by rd_pdhg_destroy (step and
+ * solve never allocate).  No C++ exception crosses this ABI; every function returns an
+ * rd_status and leaves a human-readable detail string for rd_last_error().
+ *
+ * Grid layout: an array of ncomp*ny*nx doubles, component-major, then y, then x (x contiguous):
+ * element (c, i, j) is at c*ny*nx + i*nx + j.  This is the vectorisation l = i*N_x + j of
+ * Section 2.1 (i the y index, j the x index).  Periodic nodes sit at (j h_x, i h_y); Neumann
+ * nodes at cell centres ((j+1/2) h_x, (i+1/2) h_y) with the half-cell mirror ghost
+ * U_{-1} = U_0 of Remark 1; in both cases h_x = length[0]/nx, h_y = length[1]/ny.
+ */
+#ifndef RD_PDHG_H
+#define RD_PDHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RD_API __attribute__((visibility("default")))
+#else
+#define RD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RD_OK = 0,
+    RD_ERR_INVALID_ARG = 1,    /* a NULL handle/pointer, n < 2, dt <= 0, tau <= 0, a < 0, ...   */
+    RD_ERR_UNSUPPORTED = 2,    /* valid but not built: e.g. non-power-of-two n, 3-D grids        */
+    RD_ERR_OOM = 3,            /* cudaMalloc failed                                              */
+    RD_ERR_CUDA = 4,           /* another CUDA runtime error (detail in rd_last_error)           */
+    RD_ERR_NOT_CONVERGED = 5,  /* max_iter PDHG updates did not meet the stopping rule           */
+    RD_ERR_DIVERGED = 6,       /* the stopping measure became non-finite or grew 1e8-fold        */
+    RD_ERR_TIMEOUT = 7,        /* a bounded device or host wait ran out                          */
+    RD_ERR_BUSY = 8            /* batch: no free slot / over the memory budget                   */
+} rd_status;
+
+typedef enum { RD_BC_PERIODIC = 0, RD_BC_NEUMANN = 1 } rd_bc;
+
+/* Linear diffusion operator L of the equation u_t = L u + R(u) (Section 1, eq. rd equ). */
+typedef enum {
+    RD_OP_LAPLACIAN = 0,       /* L = a Lap            (Allen-Cahn, Gray-Scott, Schnakenberg)   */
+    RD_OP_NEG_BIHARMONIC = 1   /* L = -a Lap^2         (Cahn-Hilliard, Section 3.2)             */
+} rd_operator;
+
+/* Reaction term R and the residual map F it defines (dt = h_t):
+ *   RD_RX_NONE          F = (I - a dt Lap) U - U^k    or (I + a dt Lap^2) U - U^k
+ *   RD_RX_ALLEN_CAHN    F = U - U^k - dt (a Lap U - b (U^3 - U))        (Section 3.1, eq. AC equ)
+ *   RD_RX_CH_IMPLICIT   F = (I + a dt Lap^2) U - U^k - b dt Lap (U^3 - U)    (eq. F(U) CH)
+ *   RD_RX_CH_SPLIT      F = (I + a dt Lap^2) U - U^k - b dt Lap U^3 + b dt Lap U^k
+ *                       (convex-concave split: U^3 implicit, -U explicit)
+ *   RD_RX_GRAY_SCOTT    ncomp = 2, p = {Du, Dv, F, k}:
+ *                       F_u = U - U^k - dt (Du Lap U - U V^2 + F (1 - U))
+ *                       F_v = V - V^k - dt (Dv Lap V + U V^2 - (F + k) V)
+ *   RD_RX_SCHNAKENBERG  ncomp = 2, p = {D1, D2, kappa, a_s, b_s}       (Section 3.4.1)
+ *                       F_u = U - U^k - dt (D1 Lap U + kappa (a_s - U + U^2 V))
+ *                       F_v = V - V^k - dt (D2 Lap V + kappa (b_s - U^2 V))
+ * The allowed operator is RD_OP_LAPLACIAN for AC / Gray-Scott / Schnakenberg and
+ * RD_OP_NEG_BIHARMONIC for both Cahn-Hilliard kinds; RD_RX_NONE takes either. */
+typedef enum {
+    RD_RX_NONE = 0,
+    RD_RX_ALLEN_CAHN = 1,
+    RD_RX_CH_IMPLICIT = 2,
+    RD_RX_CH_SPLIT = 3,
+    RD_RX_GRAY_SCOTT = 4,
+    RD_RX_SCHNAKENBERG = 5
+} rd_reaction_kind;
+
+typedef struct {
+    int ndim;            /* 2 (3-D grids return RD_ERR_UNSUPPORTED)                            */
+    int n[3];            /* n[0] = nx (contiguous), n[1] = ny; powers of two, 2 <= n <= 8192   */
+    double length[3];    /* side lengths; h_x = length[0]/nx, h_y = length[1]/ny               */
+} rd_grid;
+
+typedef struct {
+    int kind;            /* rd_reaction_kind                                                   */
+    int ncomp;           /* 1, or 2 for the two-species kinds (must match the kind)            */
+    double a, b;         /* diffusion and reaction scales (a >= 0, b >= 0)                     */
+    double p[6];         /* kind-specific parameters, see rd_reaction_kind                     */
+} rd_reaction;
+
+/* Preconditioner G of the dual proximal step (Section 2.1, "Choosing the matrix G"). */
+typedef enum {
+    RD_PC_NONE = 0,      /* G = I: the plain linearised PDHG (eqs. illustrate pdhg dynamic 1-3) */
+    RD_PC_LINEAR = 1     /* G = A_lin^2, A_lin the constant-coefficient linear part of F:
+                            (I - D dt Lap)^2 per species, or (I + a dt Lap^2)^2 (default)       */
+} rd_precond_kind;
+
+typedef struct { int kind; double s; } rd_precond;   /* s: reserved, must be 0 */
+
+typedef enum {
+    RD_TOL_RES_ABS = 0,  /* stop when sum_c ||F_c(U_n)||_2 / dt <= tol  (||Res||_2 <= delta)   */
+    RD_TOL_F_REL = 1     /* stop when sum_c ||F_c(U_n)||_2 <= tol * ||U^k||_2                    */
+} rd_tol_kind;
+
+typedef enum {
+    RD_PREC_FP64 = 0,    /* every PDHG sweep in FP64 (plain method)                             */
+    RD_PREC_FP32_DC = 1  /* FP32 PDHG sweeps on the correction equation inside an FP64 defect-
+                            correction loop: r = F(u) in FP64, solve F(u + d) = 0 for d in FP32
+                            until ||F~(d)|| <= dc_inner_rtol ||r||, u += d in FP64, repeat until
+                            the stopping rule above holds for F(u) evaluated in FP64             */
+} rd_precision;
+
+typedef struct {
+    double tol;           /* stopping threshold (delta), default 1e-10                          */
+    int tol_kind;         /* rd_tol_kind, default RD_TOL_RES_ABS                                */
+    int max_iter;         /* PDHG updates per step (FP64) or per inner solve (DC); default 10000 */
+    double omega;         /* extrapolation coefficient, default 1 (Section 3)                   */
+    int precision;        /* rd_precision, default RD_PREC_FP64                                 */
+    double dc_inner_rtol; /* DC inner tolerance factor, default 1e-4                             */
+    int dc_max_outer;     /* DC outer rounds per step, default 12                                */
+    int graph_k;          /* PDHG iterations per captured CUDA graph launch, default 8           */
+    int band_rows;        /* rows per CTA of the stencil sweeps; 0 = autotuned                   */
+    int col_width;        /* columns per CTA of the column transform; 0 = autotuned              */
+} rd_opts;
+
+typedef struct {
+    int iterations;       /* PDHG updates (DC: summed over inner solves)                        */
+    int outer_rounds;     /* DC outer rounds (FP64 residual evaluations); 0 for plain FP64      */
+    int converged;        /* 1 when the stopping rule held                                      */
+    int status;           /* rd_status of this step                                             */
+    double residual;      /* the stopping measure at the returned iterate                       */
+    double mass;          /* h_x h_y sum of all components of U^{k+1}                           */
+} rd_step_info;
+
+typedef struct rd_pdhg rd_pdhg;
+
+/* Fill *o with the defaults listed in rd_opts. */
+RD_API void rd_opts_default(rd_opts *o);
+
+/* Create a solver for one grid / equation / time step.
+ *   dt     physical time step h_t > 0
+ *   tau    PDHG primal step tau_u > 0;  sigma  PDHG dual step tau_p > 0   (Section 2.1)
+ *   precond may be NULL (= RD_PC_LINEAR); opts may be NULL (= rd_opts_default)
+ *   cuda_stream: a cudaStream_t (NULL = legacy default stream); all work is issued on it.
+ * Allocates every workspace (about 7 arrays of the grid size plus twiddle tables) and captures
+ * the CUDA graph of graph_k PDHG iterations.  On error *out is NULL. */
+RD_API rd_status rd_pdhg_create(rd_pdhg **out, const rd_grid *grid, rd_bc bc, rd_operator op,
+                         const rd_reaction *reaction, double dt, double tau, double sigma,
+                         const rd_precond *precond, const rd_opts *opts, void *cuda_stream);
+
+/* One implicit step: u_np1 <- root of F for U^k = u_n (both device, ncomp*ny*nx doubles; they
+ * may alias).  Blocks until the step is finished (convergence needs a device->host read).
+ * info (host, may be NULL) is filled in every case.  Returns RD_ERR_NOT_CONVERGED or
+ * RD_ERR_DIVERGED with u_np1 holding the last iterate. */
+RD_API rd_status rd_pdhg_step(rd_pdhg *h, const double *u_n, double *u_np1, rd_step_info *info);
+
+/* Algorithm 1's time loop: nsteps implicit steps in place on u (device).  per_step (host) may be
+ * NULL or an array of nsteps entries.  Stops at the first step that fails. */
+RD_API rd_status rd_pdhg_solve(rd_pdhg *h, double *u, int nsteps, rd_step_info *per_step);
+
+/* As rd_pdhg_solve, for a HOST array u: copies it to the device, solves, copies it back. */
+RD_API rd_status rd_pdhg_solve_host(rd_pdhg *h, double *u_host, int nsteps, rd_step_info *per_step);
+
+/* W <- F(U) for U^k = u_k (all device, FP64): the residual map of the handle's equation
+ * (eq. F(U) rd equation / F(U) CH / Section 3.4.1). */
+RD_API rd_status rd_pdhg_residual(rd_pdhg *h, const double *u, const double *u_k, double *w);
+
+/* Y <- G^{-1} W (device, FP64): the preconditioner solve of eq. G-prox dynamic 1, by 2-D
+ * FFT-type (periodic) or DCT-II (Neumann) transforms.  y may alias w. */
+RD_API rd_status rd_pdhg_apply_precond(rd_pdhg *h, const double *w, double *y);
+
+RD_API void rd_pdhg_destroy(rd_pdhg *h);
+
+RD_API const char *rd_status_string(rd_status s);
+RD_API const char *rd_last_error(void);   /* detail of the last failing call on this thread */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RD_PDHG_H */

@@ -1,0 +1,690 @@
+// C ABI of the GB300 PDHG solver: handle lifecycle, workspace and table set-up, CUDA-graph
+// capture of the PDHG iteration, and the step / solve drivers (Algorithm 1 of arxiv 2305.03945).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rd_pdhg.h"
+#include "rd_device.cuh"
+#include "rd_launch.h"
+
+using namespace rd;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rd_status fail(rd_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define RD_CUDA(expr)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? RD_ERR_OOM : RD_ERR_CUDA,                  \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                         \
+    }                                                                                          \
+  } while (0)
+
+constexpr int kSmemLimit = 226 * 1024;  // planning limit; checked against the device at create
+constexpr int kMaxThreads = 512;
+constexpr int kTargetBlocks = 152;  // one wave on a GB300
+
+bool pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+template <class T>
+int band_threads(int nlines, int nx) {
+  const int r = FftRadix<T>::value;
+  int t = (int)(((long long)nlines * nx + r - 1) / r);
+  const int line = fft_line_threads<T>(nx);
+  if (t < line) t = line;
+  t = round_up(t, 32);
+  if (t < 64) t = 64;
+  if (t > kMaxThreads) t = kMaxThreads;
+  return t;
+}
+
+template <class T>
+int smem_lines(int nlines, int n) {
+  return nlines * padded_len(n) * (int)sizeof(cx<T>);
+}
+
+// Launch shape for one precision.  Returns false when the grid does not fit.
+template <class T>
+bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int col_req, Desc& d,
+                 LaunchCfg& c, std::string& why) {
+  if (fft_line_threads<T>(nx) > kMaxThreads || fft_line_threads<T>(ny) > kMaxThreads) {
+    why = "grid side too long for this precision";
+    return false;
+  }
+  int B = 0;
+  if (band_req > 0) {
+    B = band_req;
+    if (B % 2 || B > ny) {
+      why = "band_rows must be even and <= ny";
+      return false;
+    }
+  } else {
+    for (int cand = 16; cand >= 2; cand /= 2) {
+      if (cand > ny) continue;
+      const int nb = (ny + cand - 1) / cand;
+      const int sm = smem_lines<T>(nc * ((cand + 2 * H) / 2), nx);
+      if (sm > kSmemLimit) continue;
+      if (nb >= kTargetBlocks || cand == 2) {
+        B = cand;
+        break;
+      }
+    }
+    if (B == 0) B = 2;
+  }
+  const int smem_res = smem_lines<T>(nc * (B / 2), nx);
+  const int smem_upd = smem_lines<T>(nc * ((B + 2 * H) / 2), nx);
+  if (smem_upd > kSmemLimit || smem_res > kSmemLimit) {
+    why = "row band does not fit in shared memory";
+    return false;
+  }
+  int C = 0;
+  const int cmin = std::max(2, std::min(nx, 32 / (int)sizeof(T)));
+  if (col_req > 0) {
+    C = col_req;
+    if (C % 2 || C > nx || nx % C) {
+      why = "col_width must be even and divide nx";
+      return false;
+    }
+  } else {
+    C = cmin;
+    for (int cand = cmin * 2; cand <= nx; cand *= 2) {
+      if (nc * (nx / cand) < kTargetBlocks) break;
+      if (smem_lines<T>(cand / 2, ny) > kSmemLimit / 2) break;
+      if (fft_line_threads<T>(ny) * 1 > kMaxThreads) break;
+      C = cand;
+    }
+  }
+  const int smem_col = smem_lines<T>(C / 2, ny);
+  if (smem_col > kSmemLimit) {
+    why = "column block does not fit in shared memory";
+    return false;
+  }
+  d.band_rows = B;
+  d.nbands = (ny + B - 1) / B;
+  d.col_width = C;
+  d.ncolblk = nx / C;
+  c.grid_bands = d.nbands;
+  c.grid_cols = nc * d.ncolblk;
+  c.thr_res = band_threads<T>(nc * (B / 2), nx);
+  c.thr_upd = band_threads<T>(nc * ((B + 2 * H) / 2), nx);
+  c.thr_col = band_threads<T>(C / 2, ny);
+  c.smem_res = smem_res;
+  c.smem_upd = smem_upd;
+  c.smem_col = smem_col;
+  c.transform = transform;
+  return true;
+}
+
+}  // namespace
+
+struct rd_pdhg {
+  int nx = 0, ny = 0, nc = 1;
+  size_t npts = 0;  // nc * nx * ny
+  int bc = 0, op = 0, kind = 0, precond = 1;
+  double dt = 0, tau = 0, sigma = 0, hx = 0, hy = 0;
+  rd_reaction rx{};
+  rd_opts opts{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int dc = 0;
+  // FP64 state and plain-path workspaces
+  double* U64 = nullptr;
+  double* rhs64 = nullptr;
+  double* P64[2] = {nullptr, nullptr};
+  double* WY64 = nullptr;
+  double* scale64 = nullptr;
+  cx<double>* tw64[4] = {nullptr, nullptr, nullptr, nullptr};  // twx, twy, dcx, dcy
+  // FP32 defect-correction workspaces
+  float* D32 = nullptr;
+  float* P32[2] = {nullptr, nullptr};
+  float* WY32 = nullptr;
+  float* scale32 = nullptr;
+  float* r32 = nullptr;
+  float* u32 = nullptr;
+  cx<float>* tw32[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* partials = nullptr;
+  Desc* d_desc = nullptr;   // [0] FP64 plain / outer, [1] FP32 inner, [2] FP64 precond-only
+  State* d_state = nullptr; // [0] plain / outer, [1] inner, [2] misc
+  State* h_state = nullptr; // pinned mirror
+  Desc h_desc[3]{};
+  LaunchCfg cfg64{}, cfg32{}, cfgpc{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <class P>
+rd_status dalloc(rd_pdhg* h, P** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RD_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(q);
+  *p = static_cast<P*>(q);
+  return RD_OK;
+}
+
+#define RD_TRY(expr)               \
+  do {                             \
+    rd_status s_ = (expr);         \
+    if (s_ != RD_OK) return s_;    \
+  } while (0)
+
+// twiddle tables exp(-2 pi i k / n) and (cos, sin)(pi k / (2n)), evaluated in long double
+void host_twiddles(int n, std::vector<double>& tw, std::vector<double>& dc) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  tw.resize(2 * n);
+  dc.resize(2 * n);
+  for (int k = 0; k < n; ++k) {
+    const long double t = 2.0L * pi * (long double)k / (long double)n;
+    tw[2 * k] = (double)cosl(t);
+    tw[2 * k + 1] = (double)(-sinl(t));
+    const long double q = pi * (long double)k / (2.0L * (long double)n);
+    dc[2 * k] = (double)cosl(q);
+    dc[2 * k + 1] = (double)sinl(q);
+  }
+}
+
+// 1 / (g_hat nx ny) on the transform grid, g_hat = (1 + D dt mu)^2 or (1 + a dt mu^2)^2
+void host_scale(const rd_pdhg* h, std::vector<double>& s) {
+  const int nx = h->nx, ny = h->ny;
+  s.assign((size_t)h->nc * nx * ny, 0.0);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double dd = h->bc == RD_BC_PERIODIC ? 1.0L : 2.0L;
+  std::vector<long double> mx(nx), my(ny);
+  for (int k = 0; k < nx; ++k) {
+    const long double sn = sinl(pi * k / (dd * nx));
+    mx[k] = 4.0L / ((long double)h->hx * h->hx) * sn * sn;
+  }
+  for (int k = 0; k < ny; ++k) {
+    const long double sn = sinl(pi * k / (dd * ny));
+    my[k] = 4.0L / ((long double)h->hy * h->hy) * sn * sn;
+  }
+  for (int c = 0; c < h->nc; ++c) {
+    long double D = h->rx.a;
+    if (h->kind == RD_RX_GRAY_SCOTT || h->kind == RD_RX_SCHNAKENBERG) D = h->rx.p[c];
+    for (int ky = 0; ky < ny; ++ky)
+      for (int kx = 0; kx < nx; ++kx) {
+        const long double mu = mx[kx] + my[ky];
+        long double g;
+        if (h->op == RD_OP_LAPLACIAN) {
+          g = 1.0L + D * h->dt * mu;
+        } else {
+          g = 1.0L + (long double)h->rx.a * h->dt * mu * mu;
+        }
+        g = g * g;
+        s[((size_t)c * ny + ky) * nx + kx] = (double)(1.0L / (g * nx * ny));
+      }
+  }
+}
+
+rd_status status_of(int st) {
+  switch (st) {
+    case ST_CONVERGED: return RD_OK;
+    case ST_NOT_CONVERGED: return RD_ERR_NOT_CONVERGED;
+    case ST_DIVERGED: return RD_ERR_DIVERGED;
+    default: return RD_ERR_NOT_CONVERGED;
+  }
+}
+
+rd_status capture_graph(rd_pdhg* h) {
+  const int K = h->opts.graph_k;
+  RD_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < K; ++k) {
+    cudaError_t e = h->dc ? launch_iteration<float>(h->d_desc + 1, h->d_state + 1, 1, h->cfg32, h->cap_stream)
+                          : launch_iteration<double>(h->d_desc + 0, h->d_state + 0, 1, h->cfg64, h->cap_stream);
+    if (e != cudaSuccess) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(h->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      return fail(RD_ERR_CUDA, std::string("kernel launch during capture: ") + cudaGetErrorString(e));
+    }
+  }
+  RD_CUDA(cudaStreamEndCapture(h->cap_stream, &h->graph));
+  RD_CUDA(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+  return RD_OK;
+}
+
+rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* rx, double dt, double tau,
+                   double sigma, const rd_precond* pc, const rd_opts* o) {
+  if (!grid || !rx) return fail(RD_ERR_INVALID_ARG, "grid and reaction must not be NULL");
+  if (grid->ndim == 3) return fail(RD_ERR_UNSUPPORTED, "3-D grids are not built");
+  if (grid->ndim != 2) return fail(RD_ERR_INVALID_ARG, "ndim must be 2");
+  for (int k = 0; k < 2; ++k) {
+    if (grid->n[k] < 2) return fail(RD_ERR_INVALID_ARG, "grid sides need n >= 2");
+    if (!pow2(grid->n[k])) return fail(RD_ERR_UNSUPPORTED, "grid sides must be powers of two");
+    if (!(grid->length[k] > 0) || !std::isfinite(grid->length[k])) return fail(RD_ERR_INVALID_ARG, "lengths must be > 0");
+  }
+  if (bc != RD_BC_PERIODIC && bc != RD_BC_NEUMANN) return fail(RD_ERR_INVALID_ARG, "bad boundary condition");
+  if (op != RD_OP_LAPLACIAN && op != RD_OP_NEG_BIHARMONIC) return fail(RD_ERR_INVALID_ARG, "bad operator");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(RD_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(tau > 0) || !(sigma > 0) || !std::isfinite(tau) || !std::isfinite(sigma))
+    return fail(RD_ERR_INVALID_ARG, "tau and sigma must be > 0");
+  if (rx->kind < RD_RX_NONE || rx->kind > RD_RX_SCHNAKENBERG) return fail(RD_ERR_INVALID_ARG, "bad reaction kind");
+  const bool two = rx->kind == RD_RX_GRAY_SCOTT || rx->kind == RD_RX_SCHNAKENBERG;
+  if (rx->ncomp != (two ? 2 : 1)) return fail(RD_ERR_INVALID_ARG, "ncomp does not match the reaction kind");
+  if (!(rx->a >= 0) || !(rx->b >= 0)) return fail(RD_ERR_INVALID_ARG, "a and b must be >= 0");
+  if ((rx->kind == RD_RX_ALLEN_CAHN || two) && op != RD_OP_LAPLACIAN)
+    return fail(RD_ERR_INVALID_ARG, "this reaction needs RD_OP_LAPLACIAN");
+  if ((rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT) && op != RD_OP_NEG_BIHARMONIC)
+    return fail(RD_ERR_INVALID_ARG, "Cahn-Hilliard needs RD_OP_NEG_BIHARMONIC");
+  if (two && (!(rx->p[0] >= 0) || !(rx->p[1] >= 0))) return fail(RD_ERR_INVALID_ARG, "diffusivities must be >= 0");
+  if (pc && pc->kind != RD_PC_NONE && pc->kind != RD_PC_LINEAR) return fail(RD_ERR_UNSUPPORTED, "preconditioner kind not built");
+  if (pc && pc->s != 0.0) return fail(RD_ERR_UNSUPPORTED, "preconditioner shift s must be 0");
+  if (o) {
+    if (!(o->tol >= 0)) return fail(RD_ERR_INVALID_ARG, "tol must be >= 0");
+    if (o->tol_kind != RD_TOL_RES_ABS && o->tol_kind != RD_TOL_F_REL) return fail(RD_ERR_INVALID_ARG, "bad tol_kind");
+    if (o->max_iter < 0) return fail(RD_ERR_INVALID_ARG, "max_iter must be >= 0");
+    if (!(o->omega >= 0) || !std::isfinite(o->omega)) return fail(RD_ERR_INVALID_ARG, "omega must be >= 0");
+    if (o->precision != RD_PREC_FP64 && o->precision != RD_PREC_FP32_DC) return fail(RD_ERR_INVALID_ARG, "bad precision");
+    if (o->graph_k < 1 || o->graph_k > 256) return fail(RD_ERR_INVALID_ARG, "graph_k must be in [1, 256]");
+    if (o->precision == RD_PREC_FP32_DC && (!(o->dc_inner_rtol > 0) || o->dc_max_outer < 1))
+      return fail(RD_ERR_INVALID_ARG, "bad defect-correction options");
+  }
+  return RD_OK;
+}
+
+rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* rx, double dt,
+                      double tau, double sigma, const rd_precond* pc, const rd_opts* o, void* stream) {
+  h->nx = grid->n[0];
+  h->ny = grid->n[1];
+  h->nc = rx->ncomp;
+  h->npts = (size_t)h->nc * h->nx * h->ny;
+  h->bc = bc;
+  h->op = op;
+  h->kind = rx->kind;
+  h->precond = pc ? pc->kind : RD_PC_LINEAR;
+  h->rx = *rx;
+  h->dt = dt;
+  h->tau = tau;
+  h->sigma = sigma;
+  h->hx = grid->length[0] / h->nx;
+  h->hy = grid->length[1] / h->ny;
+  if (o) h->opts = *o; else rd_opts_default(&h->opts);
+  h->dc = h->opts.precision == RD_PREC_FP32_DC;
+  h->stream = static_cast<cudaStream_t>(stream);
+  RD_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+
+  const int H = op == RD_OP_NEG_BIHARMONIC ? 2 : 1;
+  const int transform = h->precond != RD_PC_NONE;
+
+  Desc base{};
+  base.nx = h->nx;
+  base.ny = h->ny;
+  base.ncomp = h->nc;
+  base.lognx = ilog2(h->nx);
+  base.logny = ilog2(h->ny);
+  base.bc = bc;
+  base.op = op;
+  base.kind = rx->kind;
+  base.precond = h->precond;
+  base.hx2 = 1.0 / (h->hx * h->hx);
+  base.hy2 = 1.0 / (h->hy * h->hy);
+  base.dt = dt;
+  base.a = rx->a;
+  base.b = rx->b;
+  for (int k = 0; k < 6; ++k) base.p[k] = rx->p[k];
+  base.tau_u = tau;
+  base.tau_p = sigma;
+  base.omega = h->opts.omega;
+
+  std::string why;
+  Desc d64 = base, d32 = base;
+  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, d64, h->cfg64, why))
+    if (!h->dc) return fail(RD_ERR_UNSUPPORTED, "FP64 path: " + why);
+  if (h->dc) {
+    // the FP64 kernels of the defect-correction loop only need the band decomposition
+    if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, d32, h->cfg32, why))
+      return fail(RD_ERR_UNSUPPORTED, "FP32 path: " + why);
+    d64.band_rows = d32.band_rows;
+    d64.nbands = d32.nbands;
+    d64.col_width = d32.col_width;
+    d64.ncolblk = d32.ncolblk;
+  }
+
+  const size_t n = h->npts;
+  RD_TRY(dalloc(h, &h->U64, n * sizeof(double)));
+  RD_TRY(dalloc(h, &h->rhs64, n * sizeof(double)));
+  const int nb = std::max(d64.nbands, d32.nbands);
+  RD_TRY(dalloc(h, &h->partials, (size_t)2 * std::max(nb, 1) * sizeof(double)));
+  RD_TRY(dalloc(h, &h->d_desc, 3 * sizeof(Desc)));
+  RD_TRY(dalloc(h, &h->d_state, 3 * sizeof(State)));
+  RD_CUDA(cudaMallocHost(&h->h_state, 3 * sizeof(State)));
+
+  std::vector<double> twx, dcx, twy, dcy, sc;
+  host_twiddles(h->nx, twx, dcx);
+  host_twiddles(h->ny, twy, dcy);
+  if (transform) host_scale(h, sc);
+
+  if (!h->dc) {
+    RD_TRY(dalloc(h, &h->P64[0], n * sizeof(double)));
+    RD_TRY(dalloc(h, &h->P64[1], n * sizeof(double)));
+    RD_TRY(dalloc(h, &h->WY64, n * sizeof(double)));
+    RD_TRY(dalloc(h, &h->tw64[0], (size_t)h->nx * sizeof(cx<double>)));
+    RD_TRY(dalloc(h, &h->tw64[1], (size_t)h->ny * sizeof(cx<double>)));
+    RD_TRY(dalloc(h, &h->tw64[2], (size_t)h->nx * sizeof(cx<double>)));
+    RD_TRY(dalloc(h, &h->tw64[3], (size_t)h->ny * sizeof(cx<double>)));
+    RD_CUDA(cudaMemcpy(h->tw64[0], twx.data(), twx.size() * sizeof(double), cudaMemcpyHostToDevice));
+    RD_CUDA(cudaMemcpy(h->tw64[1], twy.data(), twy.size() * sizeof(double), cudaMemcpyHostToDevice));
+    RD_CUDA(cudaMemcpy(h->tw64[2], dcx.data(), dcx.size() * sizeof(double), cudaMemcpyHostToDevice));
+    RD_CUDA(cudaMemcpy(h->tw64[3], dcy.data(), dcy.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (transform) {
+      RD_TRY(dalloc(h, &h->scale64, n * sizeof(double)));
+      RD_CUDA(cudaMemcpy(h->scale64, sc.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+  } else {
+    RD_TRY(dalloc(h, &h->D32, n * sizeof(float)));
+    RD_TRY(dalloc(h, &h->P32[0], n * sizeof(float)));
+    RD_TRY(dalloc(h, &h->P32[1], n * sizeof(float)));
+    RD_TRY(dalloc(h, &h->WY32, n * sizeof(float)));
+    RD_TRY(dalloc(h, &h->r32, n * sizeof(float)));
+    RD_TRY(dalloc(h, &h->u32, n * sizeof(float)));
+    std::vector<float> f;
+    auto up32 = [&](cx<float>** dst, const std::vector<double>& src, int len) -> rd_status {
+      RD_TRY(dalloc(h, dst, (size_t)len * sizeof(cx<float>)));
+      f.assign(src.begin(), src.end());
+      RD_CUDA(cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+      return RD_OK;
+    };
+    RD_TRY(up32(&h->tw32[0], twx, h->nx));
+    RD_TRY(up32(&h->tw32[1], twy, h->ny));
+    RD_TRY(up32(&h->tw32[2], dcx, h->nx));
+    RD_TRY(up32(&h->tw32[3], dcy, h->ny));
+    if (transform) {
+      RD_TRY(dalloc(h, &h->scale32, n * sizeof(float)));
+      f.assign(sc.begin(), sc.end());
+      RD_CUDA(cudaMemcpy(h->scale32, f.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+  }
+
+  // descriptors
+  d64.dc = 0;
+  d64.mode = MODE_PDHG;
+  d64.meas_div_dt = h->opts.tol_kind == RD_TOL_RES_ABS;
+  d64.X = h->U64;
+  d64.base = nullptr;
+  d64.rhs = h->rhs64;
+  d64.P[0] = h->P64[0];
+  d64.P[1] = h->P64[1];
+  d64.WY = h->WY64;
+  d64.scale = h->scale64;
+  d64.twx = h->tw64[0];
+  d64.twy = h->tw64[1];
+  d64.dcx = h->tw64[2];
+  d64.dcy = h->tw64[3];
+  d64.partials = h->partials;
+
+  d32.dc = 1;
+  d32.mode = MODE_PDHG;
+  d32.meas_div_dt = 0;
+  d32.X = h->D32;
+  d32.base = h->u32;
+  d32.rhs = h->r32;
+  d32.P[0] = h->P32[0];
+  d32.P[1] = h->P32[1];
+  d32.WY = h->WY32;
+  d32.scale = h->scale32;
+  d32.twx = h->tw32[0];
+  d32.twy = h->tw32[1];
+  d32.dcx = h->tw32[2];
+  d32.dcy = h->tw32[3];
+  d32.partials = h->partials;
+
+  Desc dpc = d64;
+  dpc.mode = MODE_PRECOND_ONLY;
+  dpc.X = h->P64[1];
+  h->cfgpc = h->cfg64;
+
+  h->h_desc[0] = d64;
+  h->h_desc[1] = d32;
+  h->h_desc[2] = dpc;
+  RD_CUDA(cudaMemcpy(h->d_desc, h->h_desc, 3 * sizeof(Desc), cudaMemcpyHostToDevice));
+  State st{};
+  st.status = ST_IDLE;
+  st.max_iter = h->opts.max_iter;
+  State sts[3] = {st, st, st};
+  RD_CUDA(cudaMemcpy(h->d_state, sts, sizeof(sts), cudaMemcpyHostToDevice));
+
+  int usable = 0;
+  if (h->dc) RD_CUDA(set_kernel_smem_limits<float>(&usable));
+  else RD_CUDA(set_kernel_smem_limits<double>(&usable));
+  const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
+  if (std::max(lc.smem_res, std::max(lc.smem_col, lc.smem_upd)) > usable)
+    return fail(RD_ERR_UNSUPPORTED, "the grid needs more shared memory per block than this device offers");
+  RD_TRY(capture_graph(h));
+  RD_CUDA(cudaDeviceSynchronize());
+  return RD_OK;
+}
+
+// One implicit step on the handle's FP64 iterate U64 (already holding U^k); rhs from uk.
+rd_status step_impl(rd_pdhg* h, const double* uk, rd_step_info* info) {
+  cudaStream_t s = h->stream;
+  const Desc* d64 = h->d_desc + 0;
+  State* st0 = h->d_state + 0;
+  State* st1 = h->d_state + 1;
+  const int K = h->opts.graph_k;
+  const int nb = h->h_desc[0].nbands;
+  rd_step_info inf{};
+  int final_status = ST_NOT_CONVERGED;
+  RD_CUDA(launch_begin(d64, st0, uk, h->rhs64, h->opts.tol, h->opts.tol_kind, nb, s));
+  if (!h->dc) {
+    RD_CUDA(cudaMemsetAsync(h->P64[0], 0, h->npts * sizeof(double), s));
+    const int max_launch = h->opts.max_iter / K + 2;
+    for (int it = 0; it <= max_launch; ++it) {
+      RD_CUDA(cudaGraphLaunch(h->gexec, s));
+      RD_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(State), cudaMemcpyDeviceToHost, s));
+      RD_CUDA(cudaStreamSynchronize(s));
+      if (h->h_state[0].status != ST_ACTIVE) break;
+    }
+    final_status = h->h_state[0].status;
+    inf.iterations = h->h_state[0].n;
+    inf.residual = h->h_state[0].r;
+    if (final_status == ST_ACTIVE) return fail(RD_ERR_TIMEOUT, "PDHG loop exceeded its launch bound");
+  } else {
+    int inner_total = 0;
+    final_status = ST_NOT_CONVERGED;
+    for (int outer = 0; outer <= h->opts.dc_max_outer; ++outer) {
+      RD_CUDA(launch_resid64(d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, 1, h->opts.dc_inner_rtol, nb, s));
+      RD_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, 2 * sizeof(State), cudaMemcpyDeviceToHost, s));
+      RD_CUDA(cudaStreamSynchronize(s));
+      if (h->h_state[0].status != ST_ACTIVE) {
+        final_status = h->h_state[0].status;
+        break;
+      }
+      if (outer == h->opts.dc_max_outer) break;
+      RD_CUDA(cudaMemsetAsync(h->D32, 0, h->npts * sizeof(float), s));
+      RD_CUDA(cudaMemsetAsync(h->P32[0], 0, h->npts * sizeof(float), s));
+      const int max_launch = h->opts.max_iter / K + 2;
+      for (int it = 0; it <= max_launch; ++it) {
+        RD_CUDA(cudaGraphLaunch(h->gexec, s));
+        RD_CUDA(cudaMemcpyAsync(h->h_state + 1, h->d_state + 1, sizeof(State), cudaMemcpyDeviceToHost, s));
+        RD_CUDA(cudaStreamSynchronize(s));
+        if (h->h_state[1].status != ST_ACTIVE) break;
+      }
+      inner_total += h->h_state[1].n;
+      if (h->h_state[1].status == ST_DIVERGED || h->h_state[1].status == ST_ACTIVE) {
+        final_status = ST_DIVERGED;
+        break;
+      }
+      RD_CUDA(launch_axpy_dc(h->U64, h->D32, h->npts, s));
+    }
+    inf.iterations = inner_total;
+    inf.outer_rounds = h->h_state[0].n;
+    inf.residual = h->h_state[0].r;
+  }
+  RD_CUDA(launch_mass(d64, h->d_state + 2, h->U64, nb, s));
+  RD_CUDA(cudaMemcpyAsync(h->h_state + 2, h->d_state + 2, sizeof(State), cudaMemcpyDeviceToHost, s));
+  RD_CUDA(cudaStreamSynchronize(s));
+  inf.mass = h->h_state[2].mass;
+  inf.converged = final_status == ST_CONVERGED;
+  inf.status = status_of(final_status);
+  if (info) *info = inf;
+  if (inf.status != RD_OK)
+    return fail((rd_status)inf.status, inf.status == RD_ERR_DIVERGED ? "PDHG diverged" : "PDHG did not converge");
+  return RD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rd_opts_default(rd_opts* o) {
+  if (!o) return;
+  o->tol = 1e-10;
+  o->tol_kind = RD_TOL_RES_ABS;
+  o->max_iter = 10000;
+  o->omega = 1.0;
+  o->precision = RD_PREC_FP64;
+  o->dc_inner_rtol = 1e-4;
+  o->dc_max_outer = 12;
+  o->graph_k = 8;
+  o->band_rows = 0;
+  o->col_width = 0;
+}
+
+rd_status rd_pdhg_create(rd_pdhg** out, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* reaction,
+                         double dt, double tau, double sigma, const rd_precond* precond, const rd_opts* opts,
+                         void* cuda_stream) {
+  if (!out) return fail(RD_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  rd_status v = validate(grid, bc, op, reaction, dt, tau, sigma, precond, opts);
+  if (v != RD_OK) return v;
+  rd_pdhg* h = new (std::nothrow) rd_pdhg();
+  if (!h) return fail(RD_ERR_OOM, "host allocation failed");
+  rd_status s = create_impl(h, grid, bc, op, reaction, dt, tau, sigma, precond, opts, cuda_stream);
+  if (s != RD_OK) {
+    std::string keep = g_last_error;
+    rd_pdhg_destroy(h);
+    g_last_error = keep;
+    return s;
+  }
+  *out = h;
+  return RD_OK;
+}
+
+rd_status rd_pdhg_step(rd_pdhg* h, const double* u_n, double* u_np1, rd_step_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!h || !u_n || !u_np1) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
+  const size_t bytes = h->npts * sizeof(double);
+  RD_CUDA(cudaMemcpyAsync(h->U64, u_n, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  rd_status s = step_impl(h, h->U64, info);
+  if (s == RD_OK || s == RD_ERR_NOT_CONVERGED || s == RD_ERR_DIVERGED) {
+    std::string keep = g_last_error;
+    RD_CUDA(cudaMemcpyAsync(u_np1, h->U64, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    RD_CUDA(cudaStreamSynchronize(h->stream));
+    g_last_error = keep;
+  }
+  return s;
+}
+
+namespace {
+// Algorithm 1's time loop on the handle's iterate U64.
+rd_status solve_u64(rd_pdhg* h, int nsteps, rd_step_info* per_step) {
+  for (int k = 0; k < nsteps; ++k) {
+    rd_status s = step_impl(h, h->U64, per_step ? per_step + k : nullptr);
+    if (s != RD_OK) return s;
+  }
+  return RD_OK;
+}
+}  // namespace
+
+rd_status rd_pdhg_solve(rd_pdhg* h, double* u, int nsteps, rd_step_info* per_step) {
+  if (!h || !u) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
+  if (nsteps < 0) return fail(RD_ERR_INVALID_ARG, "nsteps must be >= 0");
+  const size_t bytes = h->npts * sizeof(double);
+  if (per_step) std::memset(per_step, 0, sizeof(rd_step_info) * (size_t)nsteps);
+  RD_CUDA(cudaMemcpyAsync(h->U64, u, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  rd_status s = solve_u64(h, nsteps, per_step);
+  std::string keep = g_last_error;
+  RD_CUDA(cudaMemcpyAsync(u, h->U64, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  g_last_error = keep;
+  return s;
+}
+
+rd_status rd_pdhg_solve_host(rd_pdhg* h, double* u_host, int nsteps, rd_step_info* per_step) {
+  if (!h || !u_host) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
+  if (nsteps < 0) return fail(RD_ERR_INVALID_ARG, "nsteps must be >= 0");
+  const size_t bytes = h->npts * sizeof(double);
+  if (per_step) std::memset(per_step, 0, sizeof(rd_step_info) * (size_t)nsteps);
+  RD_CUDA(cudaMemcpyAsync(h->U64, u_host, bytes, cudaMemcpyHostToDevice, h->stream));
+  rd_status s = solve_u64(h, nsteps, per_step);
+  std::string keep = g_last_error;
+  RD_CUDA(cudaMemcpyAsync(u_host, h->U64, bytes, cudaMemcpyDeviceToHost, h->stream));
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  g_last_error = keep;
+  return s;
+}
+
+rd_status rd_pdhg_residual(rd_pdhg* h, const double* u, const double* u_k, double* w) {
+  if (!h || !u || !u_k || !w) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
+  const int nb = h->h_desc[0].nbands;
+  RD_CUDA(launch_begin(h->d_desc + 0, h->d_state + 2, u_k, h->rhs64, 0.0, 0, nb, h->stream));
+  RD_CUDA(launch_resid64(h->d_desc + 0, h->d_state + 2, h->d_state + 2, u, h->rhs64, w, nullptr, nullptr, 0, 0.0, nb,
+                         h->stream));
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  return RD_OK;
+}
+
+rd_status rd_pdhg_apply_precond(rd_pdhg* h, const double* w, double* y) {
+  if (!h || !w || !y) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
+  if (h->dc) return fail(RD_ERR_UNSUPPORTED, "apply_precond needs a handle created with RD_PREC_FP64");
+  const size_t bytes = h->npts * sizeof(double);
+  RD_CUDA(cudaMemcpyAsync(h->P64[1], w, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  RD_CUDA(launch_iteration<double>(h->d_desc + 2, h->d_state + 2, 1, h->cfgpc, h->stream));
+  RD_CUDA(cudaMemcpyAsync(y, h->P64[1], bytes, cudaMemcpyDeviceToDevice, h->stream));
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  return RD_OK;
+}
+
+void rd_pdhg_destroy(rd_pdhg* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_state) cudaFreeHost(h->h_state);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+const char* rd_status_string(rd_status s) {
+  switch (s) {
+    case RD_OK: return "RD_OK";
+    case RD_ERR_INVALID_ARG: return "RD_ERR_INVALID_ARG";
+    case RD_ERR_UNSUPPORTED: return "RD_ERR_UNSUPPORTED";
+    case RD_ERR_OOM: return "RD_ERR_OOM";
+    case RD_ERR_CUDA: return "RD_ERR_CUDA";
+    case RD_ERR_NOT_CONVERGED: return "RD_ERR_NOT_CONVERGED";
+    case RD_ERR_DIVERGED: return "RD_ERR_DIVERGED";
+    case RD_ERR_TIMEOUT: return "RD_ERR_TIMEOUT";
+    case RD_ERR_BUSY: return "RD_ERR_BUSY";
+  }
+  return "RD_ERR_UNKNOWN";
+}
+
+const char* rd_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

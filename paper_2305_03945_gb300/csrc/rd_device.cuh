@@ -1,0 +1,300 @@
+// Device building blocks of the PDHG sweeps: complex arithmetic, the block-cooperative
+// shared-memory Stockham FFT, the real-pair Hartley / DCT-II / DCT-III line transforms that
+// diagonalise the periodic and Neumann Laplacians, boundary index maps and stencils.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rd_internal.h"
+
+namespace rd {
+
+template <class T> struct cx { T x, y; };
+
+template <class T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <class T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+
+__device__ __forceinline__ cx<double> ldg(const cx<double>* p) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ cx<float> ldg(const cx<float>* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
+// a * w for the forward transform (DIR < 0) or a * conj(w) for the inverse (DIR > 0), where the
+// twiddle table holds w_k = exp(-2 pi i k / N).
+template <class T, int DIR>
+__device__ __forceinline__ cx<T> cmul_tw(cx<T> a, cx<T> w) {
+  if (DIR < 0) return {a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x};
+  return {a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y};
+}
+
+// cos(2 pi q / 16) for integer q
+template <class T>
+__device__ __forceinline__ T cos16(int q) {
+  switch (q & 15) {
+    case 0: return T(1);
+    case 1: case 15: return T(0.92387953251128675613);
+    case 2: case 14: return T(0.70710678118654752440);
+    case 3: case 13: return T(0.38268343236508977173);
+    case 4: case 12: return T(0);
+    case 5: case 11: return T(-0.38268343236508977173);
+    case 6: case 10: return T(-0.70710678118654752440);
+    case 7: case 9: return T(-0.92387953251128675613);
+    default: return T(-1);
+  }
+}
+
+// v * exp(DIR * 2 pi i q / 16); q is a compile-time constant after unrolling.
+template <class T, int DIR>
+__device__ __forceinline__ cx<T> mul_w16(cx<T> v, int q) {
+  q &= 15;
+  if (q == 0) return v;
+  if (q == 8) return {-v.x, -v.y};
+  if (q == 4) return DIR < 0 ? cx<T>{v.y, -v.x} : cx<T>{-v.y, v.x};
+  if (q == 12) return DIR < 0 ? cx<T>{-v.y, v.x} : cx<T>{v.y, -v.x};
+  const T c = cos16<T>(q);
+  const T s = T(DIR) * cos16<T>(q - 4);  // DIR * sin(2 pi q / 16)
+  return {v.x * c - v.y * s, v.x * s + v.y * c};
+}
+
+// In-register DFT of length R (2, 4, 8 or 16): v[k] <- sum_m v[m] exp(DIR 2 pi i m k / R),
+// radix-2 decimation in time on bit-reversed input.  All loops have unit stride and constant
+// trip counts so that v stays in registers.
+template <class T, int R, int DIR>
+__device__ __forceinline__ void dft_reg(cx<T>* v) {
+  constexpr int LOGR = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int j = 0;
+#pragma unroll
+    for (int b = 0; b < LOGR; ++b) j |= ((i >> b) & 1) << (LOGR - 1 - b);
+    if (j > i) {
+      const cx<T> t = v[i];
+      v[i] = v[j];
+      v[j] = t;
+    }
+  }
+#pragma unroll
+  for (int st = 0; st < LOGR; ++st) {
+    const int half = 1 << st;
+#pragma unroll
+    for (int s = 0; s < R / (2 * half); ++s) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const int i0 = s * 2 * half + k;
+        const cx<T> a = v[i0];
+        const cx<T> b = mul_w16<T, DIR>(v[i0 + half], k * (8 >> st));
+        v[i0] = cadd(a, b);
+        v[i0 + half] = csub(a, b);
+      }
+    }
+  }
+}
+
+// Values each FFT thread holds per Stockham pass: radix 8 in FP64, radix 16 in FP32 (keeps the
+// register file under 128 registers per thread at 512 threads per block).
+template <class T> struct FftRadix { static constexpr int value = sizeof(T) == 8 ? 8 : 16; };
+
+// Threads needed to transform ONE line of length N in one go.
+template <class T>
+__host__ __device__ inline int fft_line_threads(int N) {
+  const int r = FftRadix<T>::value;
+  return N >= r ? N / r : 1;
+}
+
+// One in-place Stockham pass of radix R (Govindaraju et al., SC 2008 formulation): job j of a
+// line reads entries j + r N/R, twiddles them by w^{r (j mod Ns) N/(Ns R)}, applies the radix-R
+// DFT and writes entries (j div Ns) Ns R + (j mod Ns) + r Ns.  All reads happen before the
+// barrier and all writes after it, so one buffer suffices.
+template <class T, int R, int DIR>
+__device__ __forceinline__ void stockham_pass(cx<T>* buf, int nlines, int N, int ls, int Ns,
+                                              const cx<T>* __restrict__ tw, int tid) {
+  constexpr int S = FftRadix<T>::value / R;
+  const int jpl = N / R;
+  const int total = nlines * jpl;
+  const int nthr = (total + S - 1) / S;
+  cx<T> v[S][R];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int g = tid + s * nthr;
+    if (tid < nthr && g < total) {
+      const int line = g / jpl, j = g - line * jpl;
+      const cx<T>* L = buf + line * ls;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[s][r] = L[pidx(j + r * jpl)];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int g = tid + s * nthr;
+    if (tid < nthr && g < total) {
+      const int line = g / jpl, j = g - line * jpl;
+      const int k = j & (Ns - 1);
+      if (k != 0) {
+        const int step = k * (N / (Ns * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[s][r] = cmul_tw<T, DIR>(v[s][r], ldg(tw + r * step));
+      }
+      dft_reg<T, R, DIR>(v[s]);
+      cx<T>* L = buf + line * ls;
+      const int d = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) L[pidx(d + r * Ns)] = v[s][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Unnormalised complex DFT of `nlines` padded lines in shared memory (DIR = -1 forward,
+// +1 inverse), in chunks of as many lines as `nthreads` threads can hold.  Called by every
+// thread of the block (it contains barriers); needs nthreads >= fft_line_threads<T>(N).
+template <class T, int DIR>
+__device__ void block_fft(cx<T>* buf, int nlines, int logN, int ls, const cx<T>* __restrict__ tw,
+                          int tid, int nthreads) {
+  constexpr int RM = FftRadix<T>::value;
+  constexpr int LRM = RM == 8 ? 3 : 4;
+  const int N = 1 << logN;
+  int chunk = (nthreads * RM) >> logN;
+  if (chunk < 1) chunk = 1;
+  for (int l0 = 0; l0 < nlines; l0 += chunk) {
+    const int nl = nlines - l0 < chunk ? nlines - l0 : chunk;
+    cx<T>* b0 = buf + l0 * ls;
+    int Ns = 1, rem = logN;
+    while (rem > 0) {
+      const int b = rem >= LRM ? LRM : rem;
+      if (b == 4) stockham_pass<T, (RM >= 16 ? 16 : RM), DIR>(b0, nl, N, ls, Ns, tw, tid);
+      else if (b == 3) stockham_pass<T, 8, DIR>(b0, nl, N, ls, Ns, tw, tid);
+      else if (b == 2) stockham_pass<T, 4, DIR>(b0, nl, N, ls, Ns, tw, tid);
+      else stockham_pass<T, 2, DIR>(b0, nl, N, ls, Ns, tw, tid);
+      Ns <<= b;
+      rem -= b;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Real-pair line transforms.  A complex line holds two real lines a (.x) and b (.y).
+//   periodic : separable discrete Hartley transform H[k] = sum_j x_j cas(2 pi j k / N); the
+//              cas vectors are eigenvectors of the periodic second difference, and H H = N I.
+//   Neumann  : DCT-II X[k] = sum_j x_j cos(pi k (2j+1) / (2N)) by Makhoul's N-point method
+//              (J. Makhoul, IEEE TASSP 1980): reorder even samples ascending and odd samples
+//              descending, DFT, rotate by exp(-i pi k / 2N); its exact inverse (DCT-III up to
+//              the factor N) runs the same steps backwards.
+// ---------------------------------------------------------------------------------------
+
+// Makhoul reordering: slot n of the reordered line holds sample perm(n).
+__device__ __forceinline__ int mk_perm(int n, int N) { return n < (N >> 1) ? 2 * n : 2 * (N - 1 - n) + 1; }
+// slot that holds sample j
+__device__ __forceinline__ int mk_slot(int j, int N) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
+
+// Forward epilogue for frequency k in [0, N/2] of a pair line whose complex DFT is L.
+// Returns the real-transform coefficients (a_k, b_k) in ok and (a_{N-k}, b_{N-k}) in okp
+// (okp is meaningful only for 0 < k).
+template <class T>
+__device__ __forceinline__ void fwd_post(const cx<T>* L, int N, int bc, const cx<T>* __restrict__ dc,
+                                         int k, cx<T>& ok, cx<T>& okp) {
+  const int kp = (N - k) & (N - 1);
+  const cx<T> z = L[pidx(k)], zp = L[pidx(kp)];
+  if (bc == BC_PERIODIC) {
+    ok.x = T(0.5) * (z.x + zp.x - z.y + zp.y);
+    ok.y = T(0.5) * (z.x - zp.x + z.y + zp.y);
+    okp.x = T(0.5) * (zp.x + z.x - zp.y + z.y);
+    okp.y = T(0.5) * (zp.x - z.x + zp.y + z.y);
+  } else {
+    const cx<T> w = ldg(dc + k);  // (cos, sin)(pi k / 2N)
+    const T c = w.x, s = w.y;
+    ok.x = T(0.5) * (c * (z.x + zp.x) + s * (z.y - zp.y));
+    ok.y = T(0.5) * (c * (z.y + zp.y) - s * (z.x - zp.x));
+    okp.x = T(0.5) * (s * (zp.x + z.x) + c * (zp.y - z.y));
+    okp.y = T(0.5) * (s * (zp.y + z.y) - c * (zp.x - z.x));
+  }
+}
+
+// Inverse-DCT prologue for frequency k in [0, N/2]: from coefficients X_k = (a_k, b_k) and
+// X_{N-k} (zero when k = 0) build the complex DFT inputs z_k and z_{N-k} of the reordered
+// pair line.
+template <class T>
+__device__ __forceinline__ void dct_inv_pre(cx<T> Xk, cx<T> Xkp, T c, T s, cx<T>& zk, cx<T>& zkp) {
+  zk.x = c * Xk.x + s * Xkp.x - s * Xk.y + c * Xkp.y;
+  zk.y = s * Xk.x - c * Xkp.x + c * Xk.y + s * Xkp.y;
+  zkp.x = s * Xkp.x + c * Xk.x - c * Xkp.y + s * Xk.y;
+  zkp.y = c * Xkp.x - s * Xk.x + s * Xkp.y + c * Xk.y;
+}
+
+// In-place epilogue over all lines: slot k <- forward coefficients (optionally multiplied by
+// per-slot scale factors).
+template <class T>
+__device__ __forceinline__ void fwd_post_inplace(cx<T>* buf, int nlines, int N, int ls, int bc,
+                                                 const cx<T>* __restrict__ dc, int tid, int nthreads) {
+  const int half = (N >> 1) + 1;
+  for (int g = tid; g < nlines * half; g += nthreads) {
+    const int line = g / half, k = g - line * half;
+    cx<T>* L = buf + line * ls;
+    cx<T> ok, okp;
+    fwd_post(L, N, bc, dc, k, ok, okp);
+    L[pidx(k)] = ok;
+    if (k != 0) L[pidx(N - k)] = okp;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// boundary index map and stencils
+// ---------------------------------------------------------------------------------------
+
+// Index i in [-2, n+1] mapped into [0, n): periodic wrap, or the half-cell mirror
+// U_{-1} = U_0, U_{-2} = U_1, U_n = U_{n-1}, U_{n+1} = U_{n-2} (Remark 1).  Needs n >= 2.
+__device__ __forceinline__ int bcmap(int i, int n, int bc) {
+  if (i >= 0 && i < n) return i;
+  if (bc == BC_PERIODIC) return i < 0 ? i + n : i - n;
+  return i < 0 ? -1 - i : 2 * n - 1 - i;
+}
+
+template <class T>
+struct GField {  // one component of a grid array in global memory
+  const T* __restrict__ p;
+  int nx, ny, bc;
+  __device__ __forceinline__ T operator()(int i, int j) const {
+    return p[(size_t)bcmap(i, ny, bc) * nx + bcmap(j, nx, bc)];
+  }
+};
+
+// five-point Laplacian at (i, j) with centre value c
+template <class T, class F>
+__device__ __forceinline__ T lap5(const F& f, int i, int j, T c, T hx2, T hy2) {
+  return (f(i, j + 1) + f(i, j - 1) - T(2) * c) * hx2 + (f(i + 1, j) + f(i - 1, j) - T(2) * c) * hy2;
+}
+
+// thirteen-point Lap^2 = Dxx^2 + 2 Dxx Dyy + Dyy^2 on the periodic / two-deep mirror extension
+template <class T, class F>
+__device__ __forceinline__ T lap13(const F& f, int i, int j, T c, T hx2, T hy2) {
+  const T e = f(i, j + 1), w = f(i, j - 1), n = f(i + 1, j), s = f(i - 1, j);
+  const T xx = f(i, j + 2) - T(4) * (e + w) + T(6) * c + f(i, j - 2);
+  const T yy = f(i + 2, j) - T(4) * (n + s) + T(6) * c + f(i - 2, j);
+  const T xy = f(i + 1, j + 1) + f(i + 1, j - 1) + f(i - 1, j + 1) + f(i - 1, j - 1) -
+               T(2) * (e + w + n + s) + T(4) * c;
+  return xx * (hx2 * hx2) + T(2) * xy * (hx2 * hy2) + yy * (hy2 * hy2);
+}
+
+// block-wide sum of a double, valid in thread 0; sh must hold 32 doubles
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0;
+  if (warp == 0) {
+    t = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+}  // namespace rd

@@ -1,0 +1,31 @@
+// Host-side launchers of the PDHG kernels (defined in rd_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rd_internal.h"
+
+namespace rd {
+
+// Launch shape of one PDHG iteration over `ninst` instances (grid.y = instance).
+struct LaunchCfg {
+  int grid_bands;    // max row bands over the instances
+  int grid_cols;     // max ncomp * column blocks
+  int thr_res, thr_col, thr_upd;
+  int smem_res, smem_col, smem_upd;
+  int transform;     // 0 when G = I (no spectral solve)
+};
+
+// Raise the dynamic shared-memory limit of the PDHG kernels; *usable receives the bytes a launch may ask.
+template <class T> cudaError_t set_kernel_smem_limits(int* usable);
+template <class T> cudaError_t launch_iteration(const Desc* d, State* st, int ninst, const LaunchCfg& c, cudaStream_t s);
+
+cudaError_t launch_begin(const Desc* d64, State* st, const double* uk, double* rhs, double tol, int tol_kind,
+                         int nbands, cudaStream_t s);
+cudaError_t launch_resid64(const Desc* d64, State* outer, State* inner, const double* u, const double* rhs,
+                           double* w64, float* r32, float* u32, int decide, double rtol, int nbands,
+                           cudaStream_t s);
+cudaError_t launch_axpy_dc(double* u, const float* dlt, size_t n, cudaStream_t s);
+cudaError_t launch_mass(const Desc* d64, State* st, const double* u, int nbands, cudaStream_t s);
+
+}  // namespace rd

@@ -1,0 +1,205 @@
+"""ctypes binding of ``librd_pdhg.so`` (argument marshalling only).
+
+The functions carry the C names of ``include/rd_pdhg.h``.  ``Solver`` is a thin convenience
+wrapper that maps a ``workloads.Problem`` record onto the C structs and passes torch tensors by
+``data_ptr()`` together with torch's current CUDA stream; every step of the method runs in the
+library's CUDA kernels.  Importing this module never falls back to any other implementation:
+if the library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librd_pdhg.so")
+
+RD_OK, RD_ERR_INVALID_ARG, RD_ERR_UNSUPPORTED, RD_ERR_OOM, RD_ERR_CUDA = 0, 1, 2, 3, 4
+RD_ERR_NOT_CONVERGED, RD_ERR_DIVERGED, RD_ERR_TIMEOUT, RD_ERR_BUSY = 5, 6, 7, 8
+BC = {"periodic": 0, "neumann": 1}
+OP = {"laplacian": 0, "neg_biharmonic": 1}
+KIND = {"none": 0, "allen_cahn": 1, "ch_implicit": 2, "ch_split": 3, "gray_scott": 4, "schnakenberg": 5}
+PRECOND = {"none": 0, "linear": 1}
+TOL = {"res_abs": 0, "f_rel": 1}
+PREC = {"fp64": 0, "fp32_dc": 1}
+
+EXPORTS = ("rd_opts_default", "rd_pdhg_create", "rd_pdhg_step", "rd_pdhg_solve", "rd_pdhg_solve_host",
+           "rd_pdhg_residual", "rd_pdhg_apply_precond", "rd_pdhg_destroy", "rd_status_string",
+           "rd_last_error")
+
+
+class rd_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("length", ctypes.c_double * 3)]
+
+
+class rd_reaction(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ncomp", ctypes.c_int), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("p", ctypes.c_double * 6)]
+
+
+class rd_precond(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("s", ctypes.c_double)]
+
+
+class rd_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("tol_kind", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("omega", ctypes.c_double), ("precision", ctypes.c_int),
+                ("dc_inner_rtol", ctypes.c_double), ("dc_max_outer", ctypes.c_int),
+                ("graph_k", ctypes.c_int), ("band_rows", ctypes.c_int), ("col_width", ctypes.c_int)]
+
+
+class rd_step_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer_rounds", ctypes.c_int), ("converged", ctypes.c_int),
+                ("status", ctypes.c_int), ("residual", ctypes.c_double), ("mass", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (built by ``build.build()``) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("librd_pdhg.so not built: run paper_2305_03945_gb300.build.build() (%s)" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    lib.rd_opts_default.argtypes = [P(rd_opts)]
+    lib.rd_opts_default.restype = None
+    lib.rd_pdhg_create.argtypes = [P(vp), P(rd_grid), ctypes.c_int, ctypes.c_int, P(rd_reaction),
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, P(rd_precond),
+                                   P(rd_opts), vp]
+    lib.rd_pdhg_create.restype = ctypes.c_int
+    lib.rd_pdhg_step.argtypes = [vp, vp, vp, P(rd_step_info)]
+    lib.rd_pdhg_step.restype = ctypes.c_int
+    lib.rd_pdhg_solve.argtypes = [vp, vp, ctypes.c_int, P(rd_step_info)]
+    lib.rd_pdhg_solve.restype = ctypes.c_int
+    lib.rd_pdhg_solve_host.argtypes = [vp, vp, ctypes.c_int, P(rd_step_info)]
+    lib.rd_pdhg_solve_host.restype = ctypes.c_int
+    lib.rd_pdhg_residual.argtypes = [vp, vp, vp, vp]
+    lib.rd_pdhg_residual.restype = ctypes.c_int
+    lib.rd_pdhg_apply_precond.argtypes = [vp, vp, vp]
+    lib.rd_pdhg_apply_precond.restype = ctypes.c_int
+    lib.rd_pdhg_destroy.argtypes = [vp]
+    lib.rd_pdhg_destroy.restype = None
+    lib.rd_status_string.argtypes = [ctypes.c_int]
+    lib.rd_status_string.restype = ctypes.c_char_p
+    lib.rd_last_error.argtypes = []
+    lib.rd_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class RDError(RuntimeError):
+    def __init__(self, status, detail):
+        self.status = status
+        super().__init__("%s: %s" % (load().rd_status_string(status).decode(), detail))
+
+
+def _check(status, ok=(RD_OK,)):
+    if status not in ok:
+        raise RDError(status, load().rd_last_error().decode(errors="replace"))
+    return status
+
+
+def make_structs(pb, precision="fp64", graph_k=8, band_rows=0, col_width=0, dc_inner_rtol=1e-4,
+                 dc_max_outer=12):
+    """C structs for a ``workloads.Problem``."""
+    g = rd_grid()
+    g.ndim = 2
+    g.n[0], g.n[1], g.n[2] = pb.nx, pb.ny, 1
+    g.length[0], g.length[1], g.length[2] = pb.lx, pb.ly, 1.0
+    rx = rd_reaction()
+    rx.kind = KIND[pb.kind]
+    rx.ncomp = pb.ncomp
+    rx.a, rx.b = pb.a, pb.b
+    for k, v in enumerate(pb.p):
+        rx.p[k] = v
+    pc = rd_precond(PRECOND[pb.precond], 0.0)
+    o = rd_opts()
+    load().rd_opts_default(ctypes.byref(o))
+    o.tol = pb.tol
+    o.tol_kind = TOL[pb.tol_kind]
+    o.max_iter = pb.max_iter
+    o.omega = pb.omega
+    o.precision = PREC[precision]
+    o.graph_k = graph_k
+    o.band_rows = band_rows
+    o.col_width = col_width
+    o.dc_inner_rtol = dc_inner_rtol
+    o.dc_max_outer = dc_max_outer
+    return g, rx, pc, o
+
+
+class Solver:
+    """One ``rd_pdhg`` handle for a ``workloads.Problem``; tensors are float64 CUDA tensors of
+    shape [ncomp, ny, nx] (contiguous)."""
+
+    def __init__(self, pb, precision="fp64", stream=None, **opts):
+        import torch
+        lib = load()
+        self.pb = pb
+        self.precision = precision
+        g, rx, pc, o = make_structs(pb, precision, **opts)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.rd_pdhg_create(ctypes.byref(h), ctypes.byref(g), BC[pb.bc], OP[pb.op], ctypes.byref(rx),
+                                  pb.dt, pb.tau_u, pb.tau_p, ctypes.byref(pc), ctypes.byref(o),
+                                  ctypes.c_void_p(stream)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().rd_pdhg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @staticmethod
+    def _ptr(t):
+        assert t.is_cuda and t.dtype.is_floating_point and t.is_contiguous()
+        return ctypes.c_void_p(t.data_ptr())
+
+    def step(self, u_n, u_np1, allow=(RD_OK,)):
+        info = rd_step_info()
+        s = load().rd_pdhg_step(self.h, self._ptr(u_n), self._ptr(u_np1), ctypes.byref(info))
+        _check(s, allow)
+        return info.as_dict()
+
+    def solve(self, u, nsteps, allow=(RD_OK,)):
+        infos = (rd_step_info * max(nsteps, 1))()
+        s = load().rd_pdhg_solve(self.h, self._ptr(u), nsteps, infos)
+        _check(s, allow)
+        return [infos[k].as_dict() for k in range(nsteps)], s
+
+    def solve_host(self, u_np, nsteps, allow=(RD_OK,)):
+        """u_np: C-contiguous float64 numpy array (host); updated in place."""
+        import numpy as np
+        assert u_np.dtype == np.float64 and u_np.flags.c_contiguous
+        infos = (rd_step_info * max(nsteps, 1))()
+        s = load().rd_pdhg_solve_host(self.h, ctypes.c_void_p(u_np.ctypes.data), nsteps, infos)
+        _check(s, allow)
+        return [infos[k].as_dict() for k in range(nsteps)], s
+
+    def residual(self, u, uk, w):
+        _check(load().rd_pdhg_residual(self.h, self._ptr(u), self._ptr(uk), self._ptr(w)))
+
+    def apply_precond(self, w, y):
+        _check(load().rd_pdhg_apply_precond(self.h, self._ptr(w), self._ptr(y)))

@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/rd_pdhg.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rd_pdhg.h")).read()
+    return sorted(set(re.findall(r"RD_API\s+[\w\s\*]+?\b(rd_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_method_calls():
+    names = _declared()
+    for n in ("rd_pdhg_create", "rd_pdhg_step", "rd_pdhg_solve", "rd_pdhg_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2305_03945_gb300 import build, rd
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(rd.EXPORTS) == set(_declared())
+
+
+def test_status_strings_and_argument_checks_without_gpu():
+    """Host-side validation runs before any CUDA call, so it is testable on a CPU machine."""
+    from paper_2305_03945_gb300 import build, rd, workloads as WL
+    build.build()
+    lib = rd.load()
+    assert lib.rd_status_string(rd.RD_ERR_DIVERGED) == b"RD_ERR_DIVERGED"
+    pb = WL.config_allen_cahn_periodic(16, 1).problem
+    g, rx, pc, o = rd.make_structs(pb)
+    h = ctypes.c_void_p()
+    # non-power-of-two side
+    g.n[0] = 12
+    s = lib.rd_pdhg_create(ctypes.byref(h), ctypes.byref(g), 0, 0, ctypes.byref(rx), pb.dt, 1.0, 1.0,
+                           ctypes.byref(pc), ctypes.byref(o), None)
+    assert s == rd.RD_ERR_UNSUPPORTED and not h.value
+    g.n[0] = 16
+    # wrong operator for Allen-Cahn
+    s = lib.rd_pdhg_create(ctypes.byref(h), ctypes.byref(g), 0, 1, ctypes.byref(rx), pb.dt, 1.0, 1.0,
+                           ctypes.byref(pc), ctypes.byref(o), None)
+    assert s == rd.RD_ERR_INVALID_ARG and b"LAPLACIAN" in lib.rd_last_error()
+    # non-positive step sizes and time step
+    for dt, tau, sig in ((0.0, 1.0, 1.0), (0.01, -1.0, 1.0), (0.01, 1.0, 0.0)):
+        s = lib.rd_pdhg_create(ctypes.byref(h), ctypes.byref(g), 0, 0, ctypes.byref(rx), dt, tau, sig,
+                               ctypes.byref(pc), ctypes.byref(o), None)
+        assert s == rd.RD_ERR_INVALID_ARG
+    # ncomp must match the kind
+    rx.ncomp = 2
+    s = lib.rd_pdhg_create(ctypes.byref(h), ctypes.byref(g), 0, 0, ctypes.byref(rx), pb.dt, 1.0, 1.0,
+                           ctypes.byref(pc), ctypes.byref(o), None)
+    assert s == rd.RD_ERR_INVALID_ARG
+    assert lib.rd_pdhg_step(None, None, None, None) == rd.RD_ERR_INVALID_ARG

@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU FP64 oracle, element by element,
+on the same seeded inputs.
+
+Tolerances (written here, derived in the design doc):
+  * single operators (F, G^{-1}) in FP64: 1e-12 relative to the largest magnitude;
+  * a converged FP64 step: the same iteration count as the oracle (ties within 1e-9 of delta
+    excepted) and max |U_gpu - U_ref| <= 1e-10 max |U_ref|;
+  * the FP32 + FP64 defect-correction path: relative L2 error <= 1e-9 per step.
+"""
+import numpy as np
+import pytest
+
+from oracle import rd_oracle as O
+from paper_2305_03945_gb300 import workloads as WL
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_03945_gb300 import build
+    build.build()
+
+
+def _rd():
+    from paper_2305_03945_gb300 import rd
+    return rd
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+KINDS = [
+    ("none", "laplacian", ()),
+    ("none", "neg_biharmonic", ()),
+    ("allen_cahn", "laplacian", ()),
+    ("ch_implicit", "neg_biharmonic", ()),
+    ("ch_split", "neg_biharmonic", ()),
+    ("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06)),
+    ("schnakenberg", "laplacian", (0.05, 1.0, 100.0, 0.1305, 0.7695)),
+]
+SHAPES = [(2, 2), (4, 8), (16, 16), (32, 64), (128, 64), (256, 256)]
+
+
+def _problem(kind, op, p, bc, ny, nx, **kw):
+    ch = op == "neg_biharmonic"
+    base = dict(nx=nx, ny=ny, lx=1.0, ly=1.3, bc=bc, op=op, kind=kind, p=p,
+                dt=1e-5 if ch else 2e-3, a=4e-4 if ch else 0.05, b=1.0 if ch else 20.0,
+                tau_u=0.9, tau_p=0.9, tol=1e-12, tol_kind="f_rel", max_iter=3000)
+    base.update(kw)
+    return WL.Problem(**base)
+
+
+def _state(pb, seed):
+    r = WL.rng(seed)
+    if pb.kind == "gray_scott":
+        return np.stack([1 - 0.5 * r.random((pb.ny, pb.nx)), 0.25 * r.random((pb.ny, pb.nx))])
+    if pb.kind == "schnakenberg":
+        return WL.schnakenberg_initial(pb.nx)[:, :pb.ny, :] * (1 + 0.05 * r.uniform(-1, 1, pb.shape)) \
+            if pb.nx == pb.ny else 0.9 + 0.1 * r.random(pb.shape)
+    return r.uniform(-0.8, 0.8, pb.shape)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("kind,op,p", KINDS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_residual_map_matches_oracle(bc, kind, op, p, shape):
+    """W = F(U) (eq. F(U) rd equation, F(U) CH, Section 3.4.1) on the GPU in FP64."""
+    rd = _rd()
+    pb = _problem(kind, op, p, bc, *shape)
+    U, Uk = _state(pb, 1), _state(pb, 2)
+    with rd.Solver(pb) as s:
+        w = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        s.residual(dev(U), dev(Uk), w)
+        got = host(w)
+    want = O.residual(pb, U, Uk)
+    assert rel_max(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("kind,op,p", KINDS)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_preconditioner_solve_matches_oracle(bc, kind, op, p, shape):
+    """Y = G^{-1} W through the GPU Hartley / DCT-II transforms vs the oracle's FFT / DCT."""
+    rd = _rd()
+    pb = _problem(kind, op, p, bc, *shape)
+    W = WL.rng(5).standard_normal(pb.shape)
+    with rd.Solver(pb) as s:
+        y = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        s.apply_precond(dev(W), y)
+        got = host(y)
+    want = O.apply_ginv(pb, W)
+    assert rel_max(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("band_rows,col_width", [(0, 0), (6, 8), (2, 2), (10, 32)])
+def test_ragged_tiles_preconditioner(bc, band_rows, col_width):
+    """Row bands that do not divide ny (ragged last band) and several column-block widths."""
+    rd = _rd()
+    pb = _problem("allen_cahn", "laplacian", (), bc, 64, 128)
+    W = WL.rng(6).standard_normal(pb.shape)
+    with rd.Solver(pb, band_rows=band_rows, col_width=col_width) as s:
+        y = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        s.apply_precond(dev(W), y)
+        got = host(y)
+    assert rel_max(got, O.apply_ginv(pb, W)) <= 1e-12
+
+
+def _compare_step(pb, uk, precision="fp64", **opts):
+    rd = _rd()
+    U_ref, info_ref = O.pdhg_step(pb, uk)
+    with rd.Solver(pb, precision=precision, **opts) as s:
+        out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        info = s.step(dev(uk), out, allow=(rd.RD_OK, rd.RD_ERR_NOT_CONVERGED, rd.RD_ERR_DIVERGED))
+        U = host(out)
+    return U, info, U_ref, info_ref
+
+
+STEP_CASES = [
+    ("allen_cahn", "laplacian", (), "periodic", (64, 64)),
+    ("allen_cahn", "laplacian", (), "neumann", (32, 128)),
+    ("ch_implicit", "neg_biharmonic", (), "periodic", (64, 64)),
+    ("ch_split", "neg_biharmonic", (), "neumann", (64, 32)),
+    ("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06), "periodic", (64, 64)),
+    ("schnakenberg", "laplacian", (0.05, 1.0, 100.0, 0.1305, 0.7695), "neumann", (64, 64)),
+    ("none", "laplacian", (), "neumann", (16, 16)),
+]
+
+
+@pytest.mark.parametrize("kind,op,p,bc,shape", STEP_CASES)
+def test_fp64_step_matches_oracle(kind, op, p, bc, shape):
+    """One implicit step in FP64: same PDHG iteration count and <= 1e-10 max relative error."""
+    pb = _problem(kind, op, p, bc, *shape)
+    uk = _state(pb, 3)
+    U, info, U_ref, info_ref = _compare_step(pb, uk)
+    assert info["status"] == 0 and info_ref["status"] == O.OK
+    assert abs(info["iterations"] - info_ref["iterations"]) <= 1
+    assert rel_max(U, U_ref) <= 1e-10
+
+
+@pytest.mark.parametrize("kind,op,p,bc,shape", STEP_CASES)
+def test_fp32_defect_correction_step_matches_oracle(kind, op, p, bc, shape):
+    """FP32 PDHG sweeps + FP64 defect correction: relative L2 error <= 1e-9 against the oracle."""
+    pb = _problem(kind, op, p, bc, *shape)
+    uk = _state(pb, 4)
+    U, info, U_ref, _ = _compare_step(pb, uk, precision="fp32_dc")
+    assert info["status"] == 0, info
+    assert info["outer_rounds"] >= 2
+    assert np.linalg.norm(U - U_ref) <= 1e-9 * np.linalg.norm(U_ref)
+
+
+def test_allen_cahn_64_periodic_twenty_steps():
+    """Allen-Cahn periodic 64x64 on [0,2pi)^2, eps=0.1, dt=0.01, 20 steps, ||Res||_2 <= 1e-10:
+    per-step iteration counts equal the oracle's and the final state agrees to 1e-10."""
+    rd = _rd()
+    w = WL.config_allen_cahn_periodic()
+    U_ref, infos_ref = O.solve(w.problem, w.u0, w.nsteps)
+    u = dev(w.u0)
+    with rd.Solver(w.problem) as s:
+        infos, st = s.solve(u, w.nsteps)
+    U = host(u)
+    assert st == 0
+    assert [i["iterations"] for i in infos] == [i["iterations"] for i in infos_ref]
+    assert rel_max(U, U_ref) <= 1e-10
+
+
+def test_not_converged_and_diverged_statuses():
+    rd = _rd()
+    pb = _problem("allen_cahn", "laplacian", (), "periodic", 32, 32, max_iter=3)
+    uk = _state(pb, 7)
+    U, info, U_ref, info_ref = _compare_step(pb, uk)
+    assert info["status"] == rd.RD_ERR_NOT_CONVERGED and info["iterations"] == 3
+    assert info_ref["status"] == O.NOT_CONVERGED
+    assert rel_max(U, U_ref) <= 1e-12
+    pb = _problem("none", "laplacian", (), "periodic", 32, 32, tau_u=1.4, tau_p=1.0, max_iter=100000)
+    U, info, U_ref, info_ref = _compare_step(pb, uk)
+    assert info["status"] == rd.RD_ERR_DIVERGED and info_ref["status"] == O.DIVERGED
+    assert info["iterations"] == info_ref["iterations"]
+
+
+def test_solve_host_buffers_match_device_solve():
+    rd = _rd()
+    w = WL.config_allen_cahn_neumann(64, 3, seed=11)
+    u = dev(w.u0)
+    uh = np.ascontiguousarray(w.u0.copy())
+    with rd.Solver(w.problem) as s:
+        s.solve(u, 3)
+        s.solve_host(uh, 3)
+    assert np.array_equal(host(u), uh)
+
+
+def test_step_in_place_alias():
+    rd = _rd()
+    pb = _problem("ch_split", "neg_biharmonic", (), "periodic", 32, 32)
+    uk = _state(pb, 8)
+    U_ref, _ = O.pdhg_step(pb, uk)
+    u = dev(uk)
+    with rd.Solver(pb) as s:
+        s.step(u, u)
+    assert rel_max(host(u), U_ref) <= 1e-10
