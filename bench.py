@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 PDHG solver for implicit reaction-diffusion steps.
+
+Workload (default): Allen-Cahn, Neumann, 1024 x 1024 cell-centred grid on [0,1]^2, eps = 0.01
+(a = eps, b = 1/eps), dt = 1e-4, u0 = tanh of seeded smoothed Gaussian noise, each implicit
+step solved to ||F||_2 <= 1e-11 ||U^k||_2 with FP32 PDHG sweeps inside FP64 defect correction.
+One benchmark step = one implicit time step (every PDHG iteration of it, the FP64 residual
+passes and the defect-correction updates) continuing from the previous step's state.
+
+Metric: PDHG Gpoint-iterations/s = sum over timed steps of (grid points x components x PDHG
+iterations) / device time.  L2 is flushed (256 MiB write) between timed steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle instead (the
+paper has no code; its method restated plainly is the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+WORKLOADS = ("allen_cahn_neumann_1024", "cahn_hilliard_split_512", "gray_scott_2048", "allen_cahn_periodic_64")
+
+
+def workload(name):
+    from paper_2305_03945_gb300 import workloads as WL
+    if name == "allen_cahn_neumann_1024":
+        return WL.config_allen_cahn_neumann()
+    if name == "cahn_hilliard_split_512":
+        return WL.config_cahn_hilliard_split()
+    if name == "gray_scott_2048":
+        return WL.config_gray_scott()
+    if name == "allen_cahn_periodic_64":
+        return WL.config_allen_cahn_periodic()
+    raise SystemExit("unknown workload " + name)
+
+
+def load_peaks():
+    p = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(HERE, "paper_2305_03945_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# --------------------------------------------------------------------------------------------
+# clock sampling during the timed region
+# --------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------------
+# algorithmic bytes per launch of the three PDHG kernels
+# --------------------------------------------------------------------------------------------
+def kernel_bytes(pb, precision):
+    """Array touches per grid point of each kernel at the algorithmic minimum, times the point
+    count: k_res reads the unknown, the FP32 base state (defect correction, nonlinear kinds)
+    and the right-hand side and writes the row-transformed residual; k_col reads and writes
+    the spectrum once; k_upd reads Y, P, the unknown (and the base state) and writes the
+    unknown and P."""
+    es = 4 if precision == "fp32_dc" else 8
+    npts = pb.ncomp * pb.nx * pb.ny
+    base = 1 if (precision == "fp32_dc" and pb.kind != "none") else 0
+    return {"k_res": (3 + base) * es * npts, "k_col": 2 * es * npts, "k_upd": (5 + base) * es * npts}
+
+
+def read_traffic(name, kernel, shash):
+    p = os.path.join(HERE, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(name, {}).get(kernel)
+    if not e or e.get("source_hash") != shash:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# --------------------------------------------------------------------------------------------
+def oracle_steps(w, nsteps):
+    from oracle import rd_oracle as O
+    U = w.u0.copy()
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(nsteps):
+        U, info = O.pdhg_step(w.problem, U)
+        its += info["iterations"]
+    dt = time.perf_counter() - t0
+    return U, its, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    pb = w.problem
+    npts = pb.ncomp * pb.nx * pb.ny
+    from oracle import rd_oracle as O
+    U = w.u0.copy()
+    for _ in range(args.warmup):
+        U, _ = O.pdhg_step(pb, U)
+    its, tot = 0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        U, info = O.pdhg_step(pb, U)
+        tot += time.perf_counter() - t0
+        its += info["iterations"]
+    v = npts * its / tot / 1e9
+    line = {"impl": "reference", "metric": "PDHG Gpoint-iters/s", "value": v, "unit": "Gpoint-iter/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "grid": "%dx%d" % (pb.nx, pb.ny),
+                                            "solver": "CPU FP64 oracle (numpy), one implicit step per bench step"},
+            "cpu_baseline": {"value": v, "unit": "Gpoint-iter/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d implicit steps after %d warm-up steps" % (args.steps, args.warmup)},
+            "e2e": {"value": v, "unit": "Gpoint-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2305_03945_gb300 import build, rd
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload(args.workload)
+    pb = w.problem
+    npts = pb.ncomp * pb.nx * pb.ny
+    dist = world > 1
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed_steps(solver, u, nsteps, warm):
+        for _ in range(warm):
+            solver.step(u, u)
+        solver.reset_stats()
+        barrier()
+        torch.cuda.synchronize()
+        tot_ms, its, infos = 0.0, 0, []
+        for k in range(nsteps):
+            flush.fill_(k & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = solver.step(u, u)
+            e1.record(stream)
+            e1.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+            its += info["iterations"]
+            infos.append(info)
+        torch.cuda.synchronize()
+        barrier()
+        return tot_ms, its, infos
+
+    # ---- chosen form: FP32 sweeps + FP64 defect correction ----
+    u = torch.from_numpy(w.u0.copy()).to(dev)
+    sv = rd.Solver(pb, precision=args.precision, profile=1)
+    with ClockSampler(local_rank) as clk:
+        tot_ms, its, infos = timed_steps(sv, u, args.steps, args.warmup)
+    st = sv.stats()
+    # max over ranks of the timed device time
+    t_all = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+    it_all = torch.tensor([its], device=dev, dtype=torch.float64)
+    if dist:
+        torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(it_all, op=torch.distributed.ReduceOp.SUM)
+    t_max = float(t_all.item())
+    value = npts * float(it_all.item()) / (t_max * 1e-3) / 1e9
+
+    # per-kernel roofline from the live CUDA-event samples
+    peak, peak_kind = load_peaks()
+    kb = kernel_bytes(pb, args.precision)
+    names = ("k_res", "k_col", "k_upd")
+    per = {}
+    for i, nm in enumerate(names):
+        n = st["kernel_samples"][i]
+        if n:
+            avg_ms = st["kernel_ms"][i] / n
+            per[nm] = {"avg_us": 1e3 * avg_ms, "algorithmic_bytes": kb[nm],
+                       "achieved_gbs": kb[nm] / (avg_ms * 1e-3) / 1e9, "samples": n}
+    dom = max(per, key=lambda k: per[k]["avg_us"]) if per else None
+    shash = source_hash()
+    roof = None
+    if dom:
+        ach = per[dom]["achieved_gbs"]
+        roof = {"bound": "hbm", "kernel": dom + ("<float>" if args.precision == "fp32_dc" else "<double>"),
+                "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "traffic": read_traffic(args.workload, dom, shash), "per_kernel": per}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.from_numpy(w.u0.copy()).pin_memory()
+        uh_np = uh.numpy()
+        sv_e = rd.Solver(pb, precision=args.precision)
+        for _ in range(args.warmup):
+            sv_e.solve_host(uh_np, 1)
+        barrier()
+        torch.cuda.synchronize()
+        t_e, its_e = 0.0, 0
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            infos_e, _ = sv_e.solve_host(uh_np, 1)
+            t_e += time.perf_counter() - t0
+            its_e += infos_e[0]["iterations"]
+        sv_e.close()
+        te = torch.tensor([t_e], device=dev, dtype=torch.float64)
+        ie = torch.tensor([its_e], device=dev, dtype=torch.float64)
+        if dist:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.all_reduce(ie, op=torch.distributed.ReduceOp.SUM)
+        e2e = {"value": npts * float(ie.item()) / float(te.item()) / 1e9, "unit": "Gpoint-iter/s",
+               "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8,
+               "ms_per_step": 1e3 * float(te.item()) / args.steps}
+
+    # ---- plain FP64 path on the same workload (context: the method without mixed precision) ----
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64":
+        u64 = torch.from_numpy(w.u0.copy()).to(dev)
+        sv64 = rd.Solver(pb, precision="fp64", profile=1)
+        ms64, its64, _ = timed_steps(sv64, u64, args.fp64_steps, 1)
+        st64 = sv64.stats()
+        kb64 = kernel_bytes(pb, "fp64")
+        per64 = {}
+        for i, nm in enumerate(names):
+            n = st64["kernel_samples"][i]
+            if n:
+                a = st64["kernel_ms"][i] / n
+                per64[nm] = {"avg_us": 1e3 * a, "achieved_gbs": kb64[nm] / (a * 1e-3) / 1e9}
+        fp64 = {"value": npts * its64 / (ms64 * 1e-3) / 1e9, "unit": "Gpoint-iter/s",
+                "ms_per_step": ms64 / args.fp64_steps, "iterations_per_step": its64 / args.fp64_steps,
+                "steps": args.fp64_steps, "per_kernel": per64}
+        sv64.close()
+
+    # ---- CPU oracle baseline and full-size parity sample (rank 0, N = 1) ----
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns = args.cpu_steps
+        U_ref, its_ref, dt_ref = oracle_steps(w, ns)
+        cpu = {"value": npts * its_ref / dt_ref / 1e9, "unit": "Gpoint-iter/s", "cores": 1, "kind": "oracle",
+               "sample": "first %d implicit steps of the full workload from u0 (%d PDHG iterations, %.1f s)"
+                         % (ns, its_ref, dt_ref)}
+        up = torch.from_numpy(w.u0.copy()).to(dev)
+        sp = rd.Solver(pb, precision=args.precision)
+        infos_p, _ = sp.solve(up, ns)
+        sp.close()
+        got = up.cpu().numpy()
+        parity = {"steps": ns, "rel_l2_vs_oracle": float(np.linalg.norm(got - U_ref) / np.linalg.norm(U_ref)),
+                  "max_rel_vs_oracle": float(np.max(np.abs(got - U_ref)) / np.max(np.abs(U_ref)))}
+
+    sv.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "PDHG Gpoint-iters/s", "value": value, "unit": "Gpoint-iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "fp32_dc" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": "%dx%dx%d" % (pb.ncomp, pb.ny, pb.nx), "bc": pb.bc,
+                   "kind": pb.kind, "dt": pb.dt, "tol": "%s %g" % (pb.tol_kind, pb.tol),
+                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "iterations_per_step": its / args.steps,
+                   "residual_passes_per_step": st["residual_passes"] / args.steps},
+        "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "parity_full_size": parity, "fp64_plain": fp64,
+        "gpu_launches": st["kernel_launches"], "clocks": clk.summary(), "source_hash": shash,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="allen_cahn_neumann_1024", choices=WORKLOADS)
+    ap.add_argument("--precision", default="fp32_dc", choices=("fp32_dc", "fp64"))
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            rc = run_reference(args, rank, world)
+        else:
+            rc = run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -131,6 +131,8 @@ typedef struct {
     int graph_k;          /* PDHG iterations per captured CUDA graph launch, default 8           */
     int band_rows;        /* rows per CTA of the stencil sweeps; 0 = autotuned                   */
     int col_width;        /* columns per CTA of the column transform; 0 = autotuned              */
+    int profile;          /* 1: time the three PDHG kernels of the first iteration of every graph
+                             launch with CUDA events (read back by rd_pdhg_get_stats)            */
 } rd_opts;
 
 typedef struct {
@@ -141,6 +143,17 @@ typedef struct {
     double residual;      /* the stopping measure at the returned iterate                       */
     double mass;          /* h_x h_y sum of all components of U^{k+1}                           */
 } rd_step_info;
+
+/* Counters of a handle since creation (or the last rd_pdhg_reset_stats). */
+typedef struct {
+    long long kernel_launches;   /* kernels this library launched (graph nodes included)        */
+    long long graph_launches;    /* CUDA graph launches of the PDHG iteration                   */
+    long long pdhg_iterations;   /* PDHG updates (FP64 plain or FP32 inner)                     */
+    long long residual_passes;   /* FP64 residual evaluations of defect correction              */
+    long long host_syncs;        /* device -> host status reads                                 */
+    double kernel_ms[3];         /* profile = 1: summed CUDA-event time of k_res, k_col, k_upd   */
+    long long kernel_samples[3]; /* number of timed launches behind kernel_ms                    */
+} rd_stats;
 
 typedef struct rd_pdhg rd_pdhg;
 
@@ -178,6 +191,10 @@ RD_API rd_status rd_pdhg_residual(rd_pdhg *h, const double *u, const double *u_k
 /* Y <- G^{-1} W (device, FP64): the preconditioner solve of eq. G-prox dynamic 1, by 2-D
  * FFT-type (periodic) or DCT-II (Neumann) transforms.  y may alias w. */
 RD_API rd_status rd_pdhg_apply_precond(rd_pdhg *h, const double *w, double *y);
+
+/* Copy the handle's counters to *out (host). */
+RD_API rd_status rd_pdhg_get_stats(const rd_pdhg *h, rd_stats *out);
+RD_API rd_status rd_pdhg_reset_stats(rd_pdhg *h);
 
 RD_API void rd_pdhg_destroy(rd_pdhg *h);
 

@@ -168,6 +168,9 @@ struct rd_pdhg {
   LaunchCfg cfg64{}, cfg32{}, cfgpc{};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // around the first iteration's kernels
+  int kernels_per_graph = 0;
+  rd_stats stats{};
   std::vector<void*> allocs;
 };
 
@@ -251,10 +254,19 @@ rd_status status_of(int st) {
 
 rd_status capture_graph(rd_pdhg* h) {
   const int K = h->opts.graph_k;
+  const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
+  h->kernels_per_graph = K * (lc.transform ? 3 : 2);
+  if (h->opts.profile)
+    for (int i = 0; i < 4; ++i) RD_CUDA(cudaEventCreate(&h->ev[i]));
   RD_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   for (int k = 0; k < K; ++k) {
-    cudaError_t e = h->dc ? launch_iteration<float>(h->d_desc + 1, h->d_state + 1, 1, h->cfg32, h->cap_stream)
-                          : launch_iteration<double>(h->d_desc + 0, h->d_state + 0, 1, h->cfg64, h->cap_stream);
+    cudaError_t e;
+    if (k == 0 && h->opts.profile)
+      e = h->dc ? launch_iteration_timed<float>(h->d_desc + 1, h->d_state + 1, 1, h->cfg32, h->cap_stream, h->ev)
+                : launch_iteration_timed<double>(h->d_desc + 0, h->d_state + 0, 1, h->cfg64, h->cap_stream, h->ev);
+    else
+      e = h->dc ? launch_iteration<float>(h->d_desc + 1, h->d_state + 1, 1, h->cfg32, h->cap_stream)
+                : launch_iteration<double>(h->d_desc + 0, h->d_state + 0, 1, h->cfg64, h->cap_stream);
     if (e != cudaSuccess) {
       cudaGraph_t g = nullptr;
       cudaStreamEndCapture(h->cap_stream, &g);
@@ -478,6 +490,37 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   return RD_OK;
 }
 
+// Launch the K-iteration graph, read the solve state `which` back and account the launch.
+rd_status graph_round(rd_pdhg* h, int which) {
+  cudaStream_t s = h->stream;
+  const int n_before = h->h_state[which].n;
+  RD_CUDA(cudaGraphLaunch(h->gexec, s));
+  RD_CUDA(cudaMemcpyAsync(h->h_state + which, h->d_state + which, sizeof(State), cudaMemcpyDeviceToHost, s));
+  RD_CUDA(cudaStreamSynchronize(s));
+  h->stats.graph_launches += 1;
+  h->stats.kernel_launches += h->kernels_per_graph;
+  h->stats.host_syncs += 1;
+  h->stats.pdhg_iterations += h->h_state[which].n - n_before;
+  if (h->opts.profile) {
+    float ms = 0.f;
+    RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+    h->stats.kernel_ms[0] += ms;
+    h->stats.kernel_samples[0] += 1;
+    if (h->h_state[which].n > n_before) {  // the first iteration updated: k_col and k_upd ran
+      const int tr = (h->dc ? h->cfg32 : h->cfg64).transform;
+      if (tr) {
+        RD_CUDA(cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]));
+        h->stats.kernel_ms[1] += ms;
+        h->stats.kernel_samples[1] += 1;
+      }
+      RD_CUDA(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
+      h->stats.kernel_ms[2] += ms;
+      h->stats.kernel_samples[2] += 1;
+    }
+  }
+  return RD_OK;
+}
+
 // One implicit step on the handle's FP64 iterate U64 (already holding U^k); rhs from uk.
 rd_status step_impl(rd_pdhg* h, const double* uk, rd_step_info* info) {
   cudaStream_t s = h->stream;
@@ -489,13 +532,15 @@ rd_status step_impl(rd_pdhg* h, const double* uk, rd_step_info* info) {
   rd_step_info inf{};
   int final_status = ST_NOT_CONVERGED;
   RD_CUDA(launch_begin(d64, st0, uk, h->rhs64, h->opts.tol, h->opts.tol_kind, nb, s));
+  h->h_state[0].n = 0;
+  h->h_state[1].n = 0;
   if (!h->dc) {
     RD_CUDA(cudaMemsetAsync(h->P64[0], 0, h->npts * sizeof(double), s));
+    h->stats.kernel_launches += 1;
+    h->h_state[0].n = 0;
     const int max_launch = h->opts.max_iter / K + 2;
     for (int it = 0; it <= max_launch; ++it) {
-      RD_CUDA(cudaGraphLaunch(h->gexec, s));
-      RD_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(State), cudaMemcpyDeviceToHost, s));
-      RD_CUDA(cudaStreamSynchronize(s));
+      RD_TRY(graph_round(h, 0));
       if (h->h_state[0].status != ST_ACTIVE) break;
     }
     final_status = h->h_state[0].status;
@@ -509,6 +554,9 @@ rd_status step_impl(rd_pdhg* h, const double* uk, rd_step_info* info) {
       RD_CUDA(launch_resid64(d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, 1, h->opts.dc_inner_rtol, nb, s));
       RD_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, 2 * sizeof(State), cudaMemcpyDeviceToHost, s));
       RD_CUDA(cudaStreamSynchronize(s));
+      h->stats.kernel_launches += 1;
+      h->stats.residual_passes += 1;
+      h->stats.host_syncs += 1;
       if (h->h_state[0].status != ST_ACTIVE) {
         final_status = h->h_state[0].status;
         break;
@@ -518,9 +566,7 @@ rd_status step_impl(rd_pdhg* h, const double* uk, rd_step_info* info) {
       RD_CUDA(cudaMemsetAsync(h->P32[0], 0, h->npts * sizeof(float), s));
       const int max_launch = h->opts.max_iter / K + 2;
       for (int it = 0; it <= max_launch; ++it) {
-        RD_CUDA(cudaGraphLaunch(h->gexec, s));
-        RD_CUDA(cudaMemcpyAsync(h->h_state + 1, h->d_state + 1, sizeof(State), cudaMemcpyDeviceToHost, s));
-        RD_CUDA(cudaStreamSynchronize(s));
+        RD_TRY(graph_round(h, 1));
         if (h->h_state[1].status != ST_ACTIVE) break;
       }
       inner_total += h->h_state[1].n;
@@ -529,12 +575,15 @@ rd_status step_impl(rd_pdhg* h, const double* uk, rd_step_info* info) {
         break;
       }
       RD_CUDA(launch_axpy_dc(h->U64, h->D32, h->npts, s));
+      h->stats.kernel_launches += 1;
     }
     inf.iterations = inner_total;
     inf.outer_rounds = h->h_state[0].n;
     inf.residual = h->h_state[0].r;
   }
   RD_CUDA(launch_mass(d64, h->d_state + 2, h->U64, nb, s));
+  h->stats.kernel_launches += 2;  // begin + mass
+  h->stats.host_syncs += 1;
   RD_CUDA(cudaMemcpyAsync(h->h_state + 2, h->d_state + 2, sizeof(State), cudaMemcpyDeviceToHost, s));
   RD_CUDA(cudaStreamSynchronize(s));
   inf.mass = h->h_state[2].mass;
@@ -562,6 +611,7 @@ void rd_opts_default(rd_opts* o) {
   o->graph_k = 8;
   o->band_rows = 0;
   o->col_width = 0;
+  o->profile = 0;
 }
 
 rd_status rd_pdhg_create(rd_pdhg** out, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* reaction,
@@ -659,8 +709,22 @@ rd_status rd_pdhg_apply_precond(rd_pdhg* h, const double* w, double* y) {
   return RD_OK;
 }
 
+rd_status rd_pdhg_get_stats(const rd_pdhg* h, rd_stats* out) {
+  if (!h || !out) return fail(RD_ERR_INVALID_ARG, "NULL handle or output");
+  *out = h->stats;
+  return RD_OK;
+}
+
+rd_status rd_pdhg_reset_stats(rd_pdhg* h) {
+  if (!h) return fail(RD_ERR_INVALID_ARG, "NULL handle");
+  h->stats = rd_stats{};
+  return RD_OK;
+}
+
 void rd_pdhg_destroy(rd_pdhg* h) {
   if (!h) return;
+  for (int i = 0; i < 4; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);

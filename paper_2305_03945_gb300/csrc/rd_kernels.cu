@@ -721,6 +721,22 @@ cudaError_t launch_iteration(const Desc* d, State* st, int ninst, const LaunchCf
   return cudaGetLastError();
 }
 
+// As launch_iteration, with events recorded before k_res and after each kernel.
+template <class T>
+cudaError_t launch_iteration_timed(const Desc* d, State* st, int ninst, const LaunchCfg& c, cudaStream_t s,
+                                   cudaEvent_t* ev) {
+  cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  k_res<T><<<dim3(c.grid_bands, ninst), c.thr_res, c.smem_res, s>>>(d, st);
+  cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+  if (c.transform) k_col<T><<<dim3(c.grid_cols, ninst), c.thr_col, c.smem_col, s>>>(d, st);
+  cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
+  k_upd<T><<<dim3(c.grid_bands, ninst), c.thr_upd, c.smem_upd, s>>>(d, st);
+  cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_iteration_timed<float>(const Desc*, State*, int, const LaunchCfg&, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_iteration_timed<double>(const Desc*, State*, int, const LaunchCfg&, cudaStream_t, cudaEvent_t*);
 template cudaError_t set_kernel_smem_limits<float>(int*);
 template cudaError_t set_kernel_smem_limits<double>(int*);
 template cudaError_t launch_iteration<float>(const Desc*, State*, int, const LaunchCfg&, cudaStream_t);

@@ -20,6 +20,10 @@ struct LaunchCfg {
 template <class T> cudaError_t set_kernel_smem_limits(int* usable);
 template <class T> cudaError_t launch_iteration(const Desc* d, State* st, int ninst, const LaunchCfg& c, cudaStream_t s);
 
+template <class T>
+cudaError_t launch_iteration_timed(const Desc* d, State* st, int ninst, const LaunchCfg& c, cudaStream_t s,
+                                   cudaEvent_t* ev);
+
 cudaError_t launch_begin(const Desc* d64, State* st, const double* uk, double* rhs, double tol, int tol_kind,
                          int nbands, cudaStream_t s);
 cudaError_t launch_resid64(const Desc* d64, State* outer, State* inner, const double* u, const double* rhs,

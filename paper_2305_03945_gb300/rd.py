@@ -24,8 +24,8 @@ TOL = {"res_abs": 0, "f_rel": 1}
 PREC = {"fp64": 0, "fp32_dc": 1}
 
 EXPORTS = ("rd_opts_default", "rd_pdhg_create", "rd_pdhg_step", "rd_pdhg_solve", "rd_pdhg_solve_host",
-           "rd_pdhg_residual", "rd_pdhg_apply_precond", "rd_pdhg_destroy", "rd_status_string",
-           "rd_last_error")
+           "rd_pdhg_residual", "rd_pdhg_apply_precond", "rd_pdhg_get_stats", "rd_pdhg_reset_stats",
+           "rd_pdhg_destroy", "rd_status_string", "rd_last_error")
 
 
 class rd_grid(ctypes.Structure):
@@ -45,7 +45,21 @@ class rd_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("tol_kind", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("omega", ctypes.c_double), ("precision", ctypes.c_int),
                 ("dc_inner_rtol", ctypes.c_double), ("dc_max_outer", ctypes.c_int),
-                ("graph_k", ctypes.c_int), ("band_rows", ctypes.c_int), ("col_width", ctypes.c_int)]
+                ("graph_k", ctypes.c_int), ("band_rows", ctypes.c_int), ("col_width", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class rd_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("graph_launches", ctypes.c_longlong),
+                ("pdhg_iterations", ctypes.c_longlong), ("residual_passes", ctypes.c_longlong),
+                ("host_syncs", ctypes.c_longlong), ("kernel_ms", ctypes.c_double * 3),
+                ("kernel_samples", ctypes.c_longlong * 3)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["kernel_ms"] = list(self.kernel_ms)
+        d["kernel_samples"] = list(self.kernel_samples)
+        return d
 
 
 class rd_step_info(ctypes.Structure):
@@ -85,6 +99,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rd_pdhg_residual.restype = ctypes.c_int
     lib.rd_pdhg_apply_precond.argtypes = [vp, vp, vp]
     lib.rd_pdhg_apply_precond.restype = ctypes.c_int
+    lib.rd_pdhg_get_stats.argtypes = [vp, P(rd_stats)]
+    lib.rd_pdhg_get_stats.restype = ctypes.c_int
+    lib.rd_pdhg_reset_stats.argtypes = [vp]
+    lib.rd_pdhg_reset_stats.restype = ctypes.c_int
     lib.rd_pdhg_destroy.argtypes = [vp]
     lib.rd_pdhg_destroy.restype = None
     lib.rd_status_string.argtypes = [ctypes.c_int]
@@ -108,7 +126,7 @@ def _check(status, ok=(RD_OK,)):
 
 
 def make_structs(pb, precision="fp64", graph_k=8, band_rows=0, col_width=0, dc_inner_rtol=1e-4,
-                 dc_max_outer=12):
+                 dc_max_outer=12, profile=0):
     """C structs for a ``workloads.Problem``."""
     g = rd_grid()
     g.ndim = 2
@@ -133,6 +151,7 @@ def make_structs(pb, precision="fp64", graph_k=8, band_rows=0, col_width=0, dc_i
     o.col_width = col_width
     o.dc_inner_rtol = dc_inner_rtol
     o.dc_max_outer = dc_max_outer
+    o.profile = profile
     return g, rx, pc, o
 
 
@@ -200,6 +219,14 @@ class Solver:
 
     def residual(self, u, uk, w):
         _check(load().rd_pdhg_residual(self.h, self._ptr(u), self._ptr(uk), self._ptr(w)))
+
+    def stats(self):
+        st = rd_stats()
+        _check(load().rd_pdhg_get_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def reset_stats(self):
+        _check(load().rd_pdhg_reset_stats(self.h))
 
     def apply_precond(self, w, y):
         _check(load().rd_pdhg_apply_precond(self.h, self._ptr(w), self._ptr(y)))
