@@ -33,8 +33,11 @@ rd_status fail(rd_status s, const std::string& msg) {
   } while (0)
 
 constexpr int kSmemLimit = 226 * 1024;  // planning limit; checked against the device at create
-constexpr int kMaxThreads = 512;
 constexpr int kTargetBlocks = 152;  // one wave on a GB300
+// The FP32 inner solve of defect correction stops, as converged, once its residual has not
+// halved over this many updates: it has reached the FP32 rounding floor of the correction
+// equation and the FP64 outer loop takes over.
+constexpr int kDcStallWindow = 32;
 
 bool pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
 int ilog2(int n) {
@@ -52,7 +55,7 @@ int band_threads(int nlines, int nx) {
   if (t < line) t = line;
   t = round_up(t, 32);
   if (t < 64) t = 64;
-  if (t > kMaxThreads) t = kMaxThreads;
+  if (t > MaxThreads<T>::value) t = MaxThreads<T>::value;
   return t;
 }
 
@@ -63,9 +66,9 @@ int smem_lines(int nlines, int n) {
 
 // Launch shape for one precision.  Returns false when the grid does not fit.
 template <class T>
-bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int col_req, Desc& d,
+bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int col_req, int dc, Desc& d,
                  LaunchCfg& c, std::string& why) {
-  if (fft_line_threads<T>(nx) > kMaxThreads || fft_line_threads<T>(ny) > kMaxThreads) {
+  if (fft_line_threads<T>(nx) > MaxThreads<T>::value || fft_line_threads<T>(ny) > MaxThreads<T>::value) {
     why = "grid side too long for this precision";
     return false;
   }
@@ -80,7 +83,7 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     for (int cand = 16; cand >= 2; cand /= 2) {
       if (cand > ny) continue;
       const int nb = (ny + cand - 1) / cand;
-      const int sm = smem_lines<T>(nc * ((cand + 2 * H) / 2), nx);
+      const int sm = std::max(smem_lines<T>(nc * ((cand + 2 * H) / 2), nx), res_smem_bytes<T>(nc, cand, H, nx, dc));
       if (sm > kSmemLimit) continue;
       if (nb >= kTargetBlocks || cand == 2) {
         B = cand;
@@ -89,14 +92,14 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     }
     if (B == 0) B = 2;
   }
-  const int smem_res = smem_lines<T>(nc * (B / 2), nx);
+  const int smem_res = res_smem_bytes<T>(nc, B, H, nx, dc);
   const int smem_upd = smem_lines<T>(nc * ((B + 2 * H) / 2), nx);
   if (smem_upd > kSmemLimit || smem_res > kSmemLimit) {
     why = "row band does not fit in shared memory";
     return false;
   }
   int C = 0;
-  const int cmin = std::max(2, std::min(nx, 32 / (int)sizeof(T)));
+  const int cmin = std::max(2, std::min(nx, 16 / (int)sizeof(T)));
   if (col_req > 0) {
     C = col_req;
     if (C % 2 || C > nx || nx % C) {
@@ -106,9 +109,9 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
   } else {
     C = cmin;
     for (int cand = cmin * 2; cand <= nx; cand *= 2) {
-      if (nc * (nx / cand) < kTargetBlocks) break;
+      if (nc * (nx / cand) < 2 * kTargetBlocks) break;
       if (smem_lines<T>(cand / 2, ny) > kSmemLimit / 2) break;
-      if (fft_line_threads<T>(ny) * 1 > kMaxThreads) break;
+
       C = cand;
     }
   }
@@ -261,12 +264,9 @@ rd_status capture_graph(rd_pdhg* h) {
   RD_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   for (int k = 0; k < K; ++k) {
     cudaError_t e;
-    if (k == 0 && h->opts.profile)
-      e = h->dc ? launch_iteration_timed<float>(h->d_desc + 1, h->d_state + 1, 1, h->cfg32, h->cap_stream, h->ev)
-                : launch_iteration_timed<double>(h->d_desc + 0, h->d_state + 0, 1, h->cfg64, h->cap_stream, h->ev);
-    else
-      e = h->dc ? launch_iteration<float>(h->d_desc + 1, h->d_state + 1, 1, h->cfg32, h->cap_stream)
-                : launch_iteration<double>(h->d_desc + 0, h->d_state + 0, 1, h->cfg64, h->cap_stream);
+    cudaEvent_t* ev = (k == 0 && h->opts.profile) ? h->ev : nullptr;
+    e = h->dc ? launch_iteration<float>(h->h_desc[1], h->d_state + 1, h->cfg32, h->cap_stream, ev)
+              : launch_iteration<double>(h->h_desc[0], h->d_state + 0, h->cfg64, h->cap_stream, ev);
     if (e != cudaSuccess) {
       cudaGraph_t g = nullptr;
       cudaStreamEndCapture(h->cap_stream, &g);
@@ -364,11 +364,11 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
 
   std::string why;
   Desc d64 = base, d32 = base;
-  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, d64, h->cfg64, why))
+  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 0, d64, h->cfg64, why))
     if (!h->dc) return fail(RD_ERR_UNSUPPORTED, "FP64 path: " + why);
   if (h->dc) {
     // the FP64 kernels of the defect-correction loop only need the band decomposition
-    if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, d32, h->cfg32, why))
+    if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 1, d32, h->cfg32, why))
       return fail(RD_ERR_UNSUPPORTED, "FP32 path: " + why);
     d64.band_rows = d32.band_rows;
     d64.nbands = d32.nbands;
@@ -451,6 +451,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   d32.dc = 1;
   d32.mode = MODE_PDHG;
   d32.meas_div_dt = 0;
+  d32.stall_window = kDcStallWindow;
   d32.X = h->D32;
   d32.base = h->u32;
   d32.rhs = h->r32;
@@ -551,7 +552,8 @@ rd_status step_impl(rd_pdhg* h, const double* uk, rd_step_info* info) {
     int inner_total = 0;
     final_status = ST_NOT_CONVERGED;
     for (int outer = 0; outer <= h->opts.dc_max_outer; ++outer) {
-      RD_CUDA(launch_resid64(d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, 1, h->opts.dc_inner_rtol, nb, s));
+      RD_CUDA(launch_resid64(h->h_desc[0], d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, h->D32,
+                             h->P32[0], 1, h->opts.dc_inner_rtol, nb, s));
       RD_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, 2 * sizeof(State), cudaMemcpyDeviceToHost, s));
       RD_CUDA(cudaStreamSynchronize(s));
       h->stats.kernel_launches += 1;
@@ -562,8 +564,6 @@ rd_status step_impl(rd_pdhg* h, const double* uk, rd_step_info* info) {
         break;
       }
       if (outer == h->opts.dc_max_outer) break;
-      RD_CUDA(cudaMemsetAsync(h->D32, 0, h->npts * sizeof(float), s));
-      RD_CUDA(cudaMemsetAsync(h->P32[0], 0, h->npts * sizeof(float), s));
       const int max_launch = h->opts.max_iter / K + 2;
       for (int it = 0; it <= max_launch; ++it) {
         RD_TRY(graph_round(h, 1));
@@ -692,8 +692,8 @@ rd_status rd_pdhg_residual(rd_pdhg* h, const double* u, const double* u_k, doubl
   if (!h || !u || !u_k || !w) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
   const int nb = h->h_desc[0].nbands;
   RD_CUDA(launch_begin(h->d_desc + 0, h->d_state + 2, u_k, h->rhs64, 0.0, 0, nb, h->stream));
-  RD_CUDA(launch_resid64(h->d_desc + 0, h->d_state + 2, h->d_state + 2, u, h->rhs64, w, nullptr, nullptr, 0, 0.0, nb,
-                         h->stream));
+  RD_CUDA(launch_resid64(h->h_desc[0], h->d_desc + 0, h->d_state + 2, h->d_state + 2, u, h->rhs64, w, nullptr,
+                         nullptr, nullptr, nullptr, 0, 0.0, nb, h->stream));
   RD_CUDA(cudaStreamSynchronize(h->stream));
   return RD_OK;
 }
@@ -703,7 +703,7 @@ rd_status rd_pdhg_apply_precond(rd_pdhg* h, const double* w, double* y) {
   if (h->dc) return fail(RD_ERR_UNSUPPORTED, "apply_precond needs a handle created with RD_PREC_FP64");
   const size_t bytes = h->npts * sizeof(double);
   RD_CUDA(cudaMemcpyAsync(h->P64[1], w, bytes, cudaMemcpyDeviceToDevice, h->stream));
-  RD_CUDA(launch_iteration<double>(h->d_desc + 2, h->d_state + 2, 1, h->cfgpc, h->stream));
+  RD_CUDA(launch_iteration<double>(h->h_desc[2], h->d_state + 2, h->cfgpc, h->stream, nullptr));
   RD_CUDA(cudaMemcpyAsync(y, h->P64[1], bytes, cudaMemcpyDeviceToDevice, h->stream));
   RD_CUDA(cudaStreamSynchronize(h->stream));
   return RD_OK;

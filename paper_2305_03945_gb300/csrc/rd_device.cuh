@@ -94,9 +94,13 @@ __device__ __forceinline__ void dft_reg(cx<T>* v) {
   }
 }
 
-// Values each FFT thread holds per Stockham pass: radix 8 in FP64, radix 16 in FP32 (keeps the
-// register file under 128 registers per thread at 512 threads per block).
-template <class T> struct FftRadix { static constexpr int value = sizeof(T) == 8 ? 8 : 16; };
+// Values each FFT thread holds per Stockham pass (radix 8), and the block-size cap of the sweep
+// kernels: FP32 blocks of <= 256 threads at <= 85 registers (three blocks per SM, no spills),
+// FP64 blocks of <= 512 threads at <= 128 registers.  One line of length N needs N/8 threads,
+// so rows and columns are limited to 2048 points in FP32 and 4096 in FP64.
+template <class T> struct FftRadix { static constexpr int value = 8; };
+template <class T> struct MaxThreads { static constexpr int value = sizeof(T) == 4 ? 256 : 512; };
+template <class T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
 
 // Threads needed to transform ONE line of length N in one go.
 template <class T>
@@ -105,26 +109,58 @@ __host__ __device__ inline int fft_line_threads(int N) {
   return N >= r ? N / r : 1;
 }
 
+template <class T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// Twiddles w^r, r = 1..R-1, of one Stockham job from the table entries w^1, w^2, w^4, w^8
+// (w = exp(-2 pi i step / N)) and products of them.
+template <class T, int R>
+__device__ __forceinline__ void job_twiddles(const cx<T>* __restrict__ tw, int step, cx<T>* w) {
+  w[1] = ldg(tw + step);
+  if constexpr (R > 2) {
+    w[2] = ldg(tw + 2 * step);
+    w[3] = cmul(w[1], w[2]);
+  }
+  if constexpr (R > 4) {
+    w[4] = ldg(tw + 4 * step);
+    w[5] = cmul(w[1], w[4]);
+    w[6] = cmul(w[2], w[4]);
+    w[7] = cmul(w[3], w[4]);
+  }
+  if constexpr (R > 8) {
+    w[8] = ldg(tw + 8 * step);
+#pragma unroll
+    for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+  }
+}
+
 // One in-place Stockham pass of radix R (Govindaraju et al., SC 2008 formulation): job j of a
 // line reads entries j + r N/R, twiddles them by w^{r (j mod Ns) N/(Ns R)}, applies the radix-R
 // DFT and writes entries (j div Ns) Ns R + (j mod Ns) + r Ns.  All reads happen before the
-// barrier and all writes after it, so one buffer suffices.
+// barrier and all writes after it, so one buffer suffices.  Sizes enter as base-2 logarithms.
 template <class T, int R, int DIR>
-__device__ __forceinline__ void stockham_pass(cx<T>* buf, int nlines, int N, int ls, int Ns,
+__device__ __forceinline__ void stockham_pass(cx<T>* buf, int nlines, int logN, int ls, int logNs,
                                               const cx<T>* __restrict__ tw, int tid) {
-  constexpr int S = FftRadix<T>::value / R;
-  const int jpl = N / R;
-  const int total = nlines * jpl;
+  constexpr int RM = FftRadix<T>::value;
+  constexpr int S = RM / R;
+  constexpr int LR = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4));
+  const int lj = logN - LR;  // log2 jobs per line
+  const int jpl = 1 << lj;
+  const int total = nlines << lj;
   const int nthr = (total + S - 1) / S;
+  const int Ns = 1 << logNs;
+  const int tws = logN - logNs - LR;  // log2(N / (Ns R))
   cx<T> v[S][R];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int g = tid + s * nthr;
     if (tid < nthr && g < total) {
-      const int line = g / jpl, j = g - line * jpl;
-      const cx<T>* L = buf + line * ls;
+      const cx<T>* L = buf + (g >> lj) * ls;
+      const int j = g & (jpl - 1);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[s][r] = L[pidx(j + r * jpl)];
+      for (int r = 0; r < R; ++r) v[s][r] = L[pidx(j + (r << lj))];
     }
   }
   __syncthreads();
@@ -132,18 +168,19 @@ __device__ __forceinline__ void stockham_pass(cx<T>* buf, int nlines, int N, int
   for (int s = 0; s < S; ++s) {
     const int g = tid + s * nthr;
     if (tid < nthr && g < total) {
-      const int line = g / jpl, j = g - line * jpl;
+      const int j = g & (jpl - 1);
       const int k = j & (Ns - 1);
       if (k != 0) {
-        const int step = k * (N / (Ns * R));
+        cx<T> w[R];
+        job_twiddles<T, R>(tw, k << tws, w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[s][r] = cmul_tw<T, DIR>(v[s][r], ldg(tw + r * step));
+        for (int r = 1; r < R; ++r) v[s][r] = cmul_tw<T, DIR>(v[s][r], w[r]);
       }
       dft_reg<T, R, DIR>(v[s]);
-      cx<T>* L = buf + line * ls;
-      const int d = (j - k) * R + k;
+      cx<T>* L = buf + (g >> lj) * ls;
+      const int d = ((j - k) << LR) + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) L[pidx(d + r * Ns)] = v[s][r];
+      for (int r = 0; r < R; ++r) L[pidx(d + (r << logNs))] = v[s][r];
     }
   }
   __syncthreads();
@@ -157,20 +194,19 @@ __device__ void block_fft(cx<T>* buf, int nlines, int logN, int ls, const cx<T>*
                           int tid, int nthreads) {
   constexpr int RM = FftRadix<T>::value;
   constexpr int LRM = RM == 8 ? 3 : 4;
-  const int N = 1 << logN;
   int chunk = (nthreads * RM) >> logN;
   if (chunk < 1) chunk = 1;
   for (int l0 = 0; l0 < nlines; l0 += chunk) {
     const int nl = nlines - l0 < chunk ? nlines - l0 : chunk;
     cx<T>* b0 = buf + l0 * ls;
-    int Ns = 1, rem = logN;
+    int logNs = 0, rem = logN;
     while (rem > 0) {
       const int b = rem >= LRM ? LRM : rem;
-      if (b == 4) stockham_pass<T, (RM >= 16 ? 16 : RM), DIR>(b0, nl, N, ls, Ns, tw, tid);
-      else if (b == 3) stockham_pass<T, 8, DIR>(b0, nl, N, ls, Ns, tw, tid);
-      else if (b == 2) stockham_pass<T, 4, DIR>(b0, nl, N, ls, Ns, tw, tid);
-      else stockham_pass<T, 2, DIR>(b0, nl, N, ls, Ns, tw, tid);
-      Ns <<= b;
+      if (b == 4) stockham_pass<T, (RM >= 16 ? 16 : RM), DIR>(b0, nl, logN, ls, logNs, tw, tid);
+      else if (b == 3) stockham_pass<T, 8, DIR>(b0, nl, logN, ls, logNs, tw, tid);
+      else if (b == 2) stockham_pass<T, 4, DIR>(b0, nl, logN, ls, logNs, tw, tid);
+      else stockham_pass<T, 2, DIR>(b0, nl, logN, ls, logNs, tw, tid);
+      logNs += b;
       rem -= b;
     }
   }
@@ -277,6 +313,17 @@ __device__ __forceinline__ T lap13(const F& f, int i, int j, T c, T hx2, T hy2) 
   const T xy = f(i + 1, j + 1) + f(i + 1, j - 1) + f(i - 1, j + 1) + f(i - 1, j - 1) -
                T(2) * (e + w + n + s) + T(4) * c;
   return xx * (hx2 * hx2) + T(2) * xy * (hx2 * hy2) + yy * (hy2 * hy2);
+}
+
+// Shared-memory bytes of the residual band kernel: the complex transform buffer first, then
+// the staged real rows of the unknown (and of the defect-correction base state); every region
+// starts 16-byte aligned.
+template <class T>
+__host__ __device__ inline int res_smem_bytes(int nc, int rows, int H, int nx, int dc) {
+  const int ls = padded_len(nx);
+  const int buf = nc * (rows >> 1) * ls * (int)sizeof(cx<T>);
+  const int stg = nc * (rows + 2 * H) * nx * (int)sizeof(T);
+  return buf + stg * (dc ? 2 : 1);
 }
 
 // block-wide sum of a double, valid in thread 0; sh must hold 32 doubles

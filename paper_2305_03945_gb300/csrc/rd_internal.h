@@ -20,7 +20,8 @@ constexpr int kRadix = 16;              // values each FFT thread holds per Stoc
 // Padded index inside a shared-memory complex line: one pad slot every 16 entries, so that the
 // stride-16 stores of the first Stockham pass spread over all banks.
 __host__ __device__ inline int pidx(int i) { return i + (i >> 4); }
-__host__ __device__ inline int padded_len(int n) { return n + (n >> 4) + 1; }
+// line stride in complex entries; even, so every line starts 16-byte aligned
+__host__ __device__ inline int padded_len(int n) { return (n + (n >> 4) + 2) & ~1; }
 
 // One solve instance: grid, equation, PDHG parameters and device buffers.
 // All pointers are device pointers owned by the host handle.  T-typed buffers hold the
@@ -35,7 +36,7 @@ struct Desc {
   int col_width;     // columns per CTA of the column transform (even, divides nx)
   int ncolblk;       // nx / col_width
   int meas_div_dt;   // 1: stopping measure is sum ||F_c|| / dt, else sum ||F_c||
-  int pad0;
+  int stall_window;  // > 0: stop (as converged) when the measure has not halved for this many updates
   double hx2, hy2;   // 1/h_x^2, 1/h_y^2
   double dt, a, b;
   double p[6];
@@ -63,8 +64,9 @@ struct State {
   double thresh;     // stopping threshold on the measure
   double aux;        // begin kernel: ||U^k||_2
   double mass;       // h_x h_y sum of all components (mass kernel)
+  double best;       // smallest measure at which the measure last halved (stall detection)
+  int best_n;        // update count at that point
   unsigned int ticket;
-  unsigned int pad2;
 };
 
 }  // namespace rd

@@ -18,17 +18,18 @@ struct LaunchCfg {
 
 // Raise the dynamic shared-memory limit of the PDHG kernels; *usable receives the bytes a launch may ask.
 template <class T> cudaError_t set_kernel_smem_limits(int* usable);
-template <class T> cudaError_t launch_iteration(const Desc* d, State* st, int ninst, const LaunchCfg& c, cudaStream_t s);
-
+// One PDHG iteration (k_res, k_col, k_upd) of the solve described by d (passed by value to the
+// kernels); with ev != NULL, events ev[0..3] are recorded around the three kernels.
 template <class T>
-cudaError_t launch_iteration_timed(const Desc* d, State* st, int ninst, const LaunchCfg& c, cudaStream_t s,
-                                   cudaEvent_t* ev);
+cudaError_t launch_iteration(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
+
 
 cudaError_t launch_begin(const Desc* d64, State* st, const double* uk, double* rhs, double tol, int tol_kind,
                          int nbands, cudaStream_t s);
-cudaError_t launch_resid64(const Desc* d64, State* outer, State* inner, const double* u, const double* rhs,
-                           double* w64, float* r32, float* u32, int decide, double rtol, int nbands,
-                           cudaStream_t s);
+cudaError_t launch_resid64(const Desc& hd, const Desc* d64, State* outer, State* inner, const double* u,
+                           const double* rhs, double* w64, float* r32, float* u32, float* z0, float* z1, int decide,
+                           double rtol, int nbands, cudaStream_t s);
+
 cudaError_t launch_axpy_dc(double* u, const float* dlt, size_t n, cudaStream_t s);
 cudaError_t launch_mass(const Desc* d64, State* st, const double* u, int nbands, cudaStream_t s);
 

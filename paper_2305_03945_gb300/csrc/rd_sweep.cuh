@@ -1,0 +1,814 @@
+// The three kernels of one G-prox PDHG iteration (arxiv 2305.03945, Section 2.1, Algorithm 1),
+// templated on the arithmetic type T and on the equation K so that each instantiation holds only
+// its own physics.  T = float is the inner solve of FP64 defect correction (the unknown is the
+// correction d of u + d); T = double is the plain FP64 method.
+//
+//   k_res  (row bands)      W = F(U_n) (eq. F(U) rd equation / F(U) CH / Section 3.4.1), the
+//                           per-band partial sums of ||W_c||^2, the forward row transform of W
+//                           along x, and (last block to finish) the stopping decision
+//                           ||Res(U_n)||_2 <= delta of Section 2.1;
+//   k_col  (column blocks)  forward column transform along y, multiplication by 1/g_hat (the
+//                           spectral inverse of G = A_lin^2), inverse column transform;
+//   k_upd  (row bands)      inverse row transform of Y = G^{-1} W, the dual update
+//                           P_{n+1} = P_n + tau_p Y, the extrapolation P~ = P_n + (1+omega) tau_p Y
+//                           (eqs. G-prox ... dynamic 1-2) and the primal update
+//                           U_{n+1} = U_n - tau_u dF(U_n)^T P~ (eq. G-prox ... dynamic 3).
+// The transforms are the separable Hartley transform (periodic) and Makhoul's DCT-II (Neumann),
+// both of which diagonalise the five-point Laplacian with its boundary rule.
+#pragma once
+
+#include "rd_device.cuh"
+#include "rd_launch.h"
+
+namespace rd {
+
+// Equation keys of the sweep templates.
+enum KKey {
+  KK_NONE_LAP = 0, KK_AC = 1, KK_CH_IMPL = 2, KK_CH_SPLIT = 3, KK_GS = 4, KK_SCHNAK = 5,
+  KK_NONE_BIH = 6, KK_PCONLY = 7
+};
+
+__host__ __device__ inline int kind_key(const Desc& d) {
+  if (d.mode == MODE_PRECOND_ONLY) return KK_PCONLY;
+  if (d.kind == RX_NONE) return d.op == OP_BIHARM ? KK_NONE_BIH : KK_NONE_LAP;
+  return d.kind;
+}
+
+template <int K>
+struct KT {
+  static constexpr bool biharm = K == KK_CH_IMPL || K == KK_CH_SPLIT || K == KK_NONE_BIH;
+  static constexpr bool two = K == KK_GS || K == KK_SCHNAK;
+  static constexpr int H = K == KK_PCONLY ? 0 : (biharm ? 2 : 1);
+  static constexpr bool nonlinear = K != KK_NONE_LAP && K != KK_NONE_BIH && K != KK_PCONLY;
+};
+
+__host__ __device__ inline int ilog2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// staged rows in shared memory, row stride nx; columns boundary-mapped only when EDGE
+template <class T, bool EDGE>
+struct Rows {
+  const T* p;
+  int nx, bc;
+  __device__ __forceinline__ T operator()(int lr, int j) const {
+    if constexpr (EDGE) return p[lr * nx + bcmap(j, nx, bc)];
+    else return p[lr * nx + j];
+  }
+};
+
+// P~ in the complex transform buffer: two rows per line (row a in .x, row b in .y)
+template <class T, bool EDGE>
+struct Pairs {
+  const cx<T>* buf;
+  int ls, nx, bc, line0;
+  __device__ __forceinline__ T operator()(int lr, int j) const {
+    const int jj = EDGE ? bcmap(j, nx, bc) : j;
+    const cx<T> v = buf[(line0 + (lr >> 1)) * ls + pidx(jj)];
+    return (lr & 1) ? v.y : v.x;
+  }
+};
+
+// W_c = F_c(X) at one point for every component (see residual map definitions in rd_pdhg.h).
+//   plain (DC = false): X = U, r = rhs of the step (U^k plus the explicit / constant terms)
+//   DC    (DC = true) : X = d, B = u, r = F(u); returns F(u + d) = F(u) + A_lin d + N(u + d) - N(u)
+//                       with the nonlinear increment expanded so that no large terms cancel.
+template <class T, int K, bool DC, class A>
+__device__ __forceinline__ void residual_pt(const Desc& d, const A& x0, const A& x1, const A& b0, const A& b1,
+                                            int i, int j, T r0, T r1, T* w) {
+  const T hx2 = T(d.hx2), hy2 = T(d.hy2), dt = T(d.dt), a = T(d.a), b = T(d.b);
+  const T c0 = x0(i, j);
+  if constexpr (K == KK_NONE_LAP || K == KK_NONE_BIH) {
+    const T lin = K == KK_NONE_LAP ? c0 - dt * a * lap5(x0, i, j, c0, hx2, hy2)
+                                   : c0 + dt * a * lap13(x0, i, j, c0, hx2, hy2);
+    w[0] = DC ? r0 + lin : lin - r0;
+  } else if constexpr (K == KK_AC) {
+    const T lin = c0 - dt * a * lap5(x0, i, j, c0, hx2, hy2);
+    if constexpr (!DC) {
+      w[0] = lin - r0 + dt * b * (c0 * c0 * c0 - c0);
+    } else {
+      const T u = b0(i, j);
+      w[0] = r0 + lin + dt * b * (c0 * (T(3) * u * u - T(1)) + c0 * c0 * (T(3) * u + c0));
+    }
+  } else if constexpr (K == KK_CH_IMPL || K == KK_CH_SPLIT) {
+    const T lin = c0 + dt * a * lap13(x0, i, j, c0, hx2, hy2);
+    constexpr T sh = K == KK_CH_IMPL ? T(1) : T(0);
+    auto q = [&](int ii, int jj) -> T {
+      const T xv = x0(ii, jj);
+      if constexpr (!DC) {
+        return xv * xv * xv - sh * xv;
+      } else {
+        const T u = b0(ii, jj);
+        return xv * (T(3) * u * u - sh) + xv * xv * (T(3) * u + xv);
+      }
+    };
+    const T qc = q(i, j);
+    const T lq = (q(i, j + 1) + q(i, j - 1) - T(2) * qc) * hx2 + (q(i + 1, j) + q(i - 1, j) - T(2) * qc) * hy2;
+    w[0] = DC ? r0 + lin - dt * b * lq : lin - r0 - dt * b * lq;
+  } else if constexpr (K == KK_GS) {
+    const T Du = T(d.p[0]), Dv = T(d.p[1]), Ff = T(d.p[2]), kk = T(d.p[3]);
+    const T u0 = c0, v0 = x1(i, j);
+    const T lu = lap5(x0, i, j, u0, hx2, hy2), lv = lap5(x1, i, j, v0, hx2, hy2);
+    if constexpr (!DC) {
+      const T uvv = u0 * v0 * v0;
+      w[0] = u0 - r0 - dt * Du * lu + dt * uvv + dt * Ff * u0;
+      w[1] = v0 - r1 - dt * Dv * lv - dt * uvv + dt * (Ff + kk) * v0;
+    } else {
+      const T U = b0(i, j), V = b1(i, j);
+      const T inc = u0 * V * V + T(2) * U * V * v0 + T(2) * u0 * V * v0 + U * v0 * v0 + u0 * v0 * v0;
+      w[0] = r0 + u0 - dt * Du * lu + dt * inc + dt * Ff * u0;
+      w[1] = r1 + v0 - dt * Dv * lv - dt * inc + dt * (Ff + kk) * v0;
+    }
+  } else if constexpr (K == KK_SCHNAK) {
+    const T D1 = T(d.p[0]), D2 = T(d.p[1]), kap = T(d.p[2]);
+    const T u0 = c0, v0 = x1(i, j);
+    const T lu = lap5(x0, i, j, u0, hx2, hy2), lv = lap5(x1, i, j, v0, hx2, hy2);
+    if constexpr (!DC) {
+      const T u2v = u0 * u0 * v0;
+      w[0] = u0 - r0 - dt * D1 * lu + dt * kap * u0 - dt * kap * u2v;
+      w[1] = v0 - r1 - dt * D2 * lv + dt * kap * u2v;
+    } else {
+      const T U = b0(i, j), V = b1(i, j);
+      const T inc = T(2) * U * u0 * V + u0 * u0 * V + U * U * v0 + T(2) * U * u0 * v0 + u0 * u0 * v0;
+      w[0] = r0 + u0 - dt * D1 * lu + dt * kap * u0 - dt * kap * inc;
+      w[1] = r1 + v0 - dt * D2 * lv + dt * kap * inc;
+    }
+  }
+}
+
+// g = dF(x)^T P~ at local row lr, column j; x0, x1 are the components of the current state.
+template <class T, int K, class SF>
+__device__ __forceinline__ void gradT_pt(const Desc& d, const SF& p0, const SF& p1, T x0, T x1, int lr, int j,
+                                         T* g) {
+  const T hx2 = T(d.hx2), hy2 = T(d.hy2), dt = T(d.dt), a = T(d.a), b = T(d.b);
+  const T P = p0(lr, j);
+  if constexpr (K == KK_NONE_LAP) {
+    g[0] = P - dt * a * lap5(p0, lr, j, P, hx2, hy2);
+  } else if constexpr (K == KK_NONE_BIH) {
+    g[0] = P + dt * a * lap13(p0, lr, j, P, hx2, hy2);
+  } else if constexpr (K == KK_AC) {
+    g[0] = P - dt * a * lap5(p0, lr, j, P, hx2, hy2) + dt * b * (T(3) * x0 * x0 - T(1)) * P;
+  } else if constexpr (K == KK_CH_IMPL || K == KK_CH_SPLIT) {
+    constexpr T sh = K == KK_CH_IMPL ? T(1) : T(0);
+    g[0] = P + dt * a * lap13(p0, lr, j, P, hx2, hy2) - dt * b * (T(3) * x0 * x0 - sh) * lap5(p0, lr, j, P, hx2, hy2);
+  } else if constexpr (K == KK_GS) {
+    const T Du = T(d.p[0]), Dv = T(d.p[1]), Ff = T(d.p[2]), kk = T(d.p[3]);
+    const T Q = p1(lr, j);
+    const T u = x0, v = x1;
+    g[0] = P - dt * Du * lap5(p0, lr, j, P, hx2, hy2) + dt * (v * v + Ff) * P - dt * v * v * Q;
+    g[1] = Q - dt * Dv * lap5(p1, lr, j, Q, hx2, hy2) + T(2) * dt * u * v * P - dt * (T(2) * u * v - (Ff + kk)) * Q;
+  } else if constexpr (K == KK_SCHNAK) {
+    const T D1 = T(d.p[0]), D2 = T(d.p[1]), kap = T(d.p[2]);
+    const T Q = p1(lr, j);
+    const T u = x0, v = x1;
+    g[0] = P - dt * (D1 * lap5(p0, lr, j, P, hx2, hy2) + kap * (-P + T(2) * u * v * (P - Q)));
+    g[1] = Q - dt * (D2 * lap5(p1, lr, j, Q, hx2, hy2) + kap * (u * u * (P - Q)));
+  }
+}
+
+// Ticket: returns true in every thread of the last block of the launch to arrive.
+__device__ __forceinline__ bool last_block(State* st, int nblocks) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&st->ticket, 1u);
+    s_last = (t == (unsigned)nblocks - 1u);
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// Sum of n partials with a fixed thread partition and a fixed tree (the result depends only on
+// n and blockDim).  Called by every thread of the block; valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double* p, int n, double* red) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) s += __ldcg(p + k);
+  return block_sum(s, red);
+}
+
+// Stopping decision of one PDHG solve from the per-band partial sums (all threads of the last
+// block call it): r <= threshold -> converged; non-finite or 1e8-fold growth -> diverged;
+// max_iter updates done -> not converged; otherwise count the coming update.
+__device__ inline void finalize_measure(const Desc& d, State* st, double* red) {
+  __threadfence();
+  double tot = 0.0;
+  for (int c = 0; c < d.ncomp; ++c) tot += sqrt(sum_partials(d.partials + c * d.nbands, d.nbands, red));
+  if (threadIdx.x != 0) return;
+  const double meas = d.meas_div_dt ? tot / d.dt : tot;
+  st->ticket = 0u;
+  st->r = meas;
+  const int n = st->n;
+  if (n == 0) {
+    st->r0 = meas;
+    st->best = meas;
+    st->best_n = 0;
+  } else if (meas < 0.5 * st->best) {
+    st->best = meas;
+    st->best_n = n;
+  }
+  const double r0 = n == 0 ? meas : st->r0;
+  if (meas <= st->thresh) {
+    st->status = ST_CONVERGED;
+  } else if (!isfinite(meas) || meas > kDivergeFactor * r0) {
+    st->status = ST_DIVERGED;
+  } else if (d.stall_window > 0 && n - st->best_n >= d.stall_window) {
+    st->status = ST_CONVERGED;  // stalled at the rounding floor of this precision
+  } else if (n >= st->max_iter) {
+    st->status = ST_NOT_CONVERGED;
+  } else {
+    st->n = n + 1;
+  }
+}
+
+// 16-byte vectors
+template <class T> struct V16;
+template <> struct V16<float> { using t = float4; static constexpr int n = 4; };
+template <> struct V16<double> { using t = double2; static constexpr int n = 2; };
+
+template <class T, int W>
+__device__ __forceinline__ void vld(const T* __restrict__ p, T* v) {
+  if constexpr (W == V16<T>::n) {
+    const typename V16<T>::t q = *reinterpret_cast<const typename V16<T>::t*>(p);
+    const T* e = reinterpret_cast<const T*>(&q);
+#pragma unroll
+    for (int k = 0; k < W; ++k) v[k] = e[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; ++k) v[k] = p[k];
+  }
+}
+template <class T, int W>
+__device__ __forceinline__ void vst(T* __restrict__ p, const T* v) {
+  if constexpr (W == V16<T>::n) {
+    typename V16<T>::t q;
+    T* e = reinterpret_cast<T*>(&q);
+#pragma unroll
+    for (int k = 0; k < W; ++k) e[k] = v[k];
+    *reinterpret_cast<typename V16<T>::t*>(p) = q;
+  } else {
+#pragma unroll
+    for (int k = 0; k < W; ++k) p[k] = v[k];
+  }
+}
+
+// Copy rows g0 .. g0+nrows-1 (boundary-mapped) of a plane into shared memory (row stride nx).
+template <class T, int W>
+__device__ __forceinline__ void stage_rows_w(T* dst, const T* __restrict__ src, int nx, int lognx, int ny, int bc,
+                                             int g0, int nrows) {
+  const int lw = W == 4 ? 2 : (W == 2 ? 1 : 0);
+  const int lv = lognx - lw;  // log2 vectors per row
+  const int total = nrows << lv;
+#pragma unroll 4
+  for (int v = threadIdx.x; v < total; v += blockDim.x) {
+    const int r = v >> lv, c = v & ((1 << lv) - 1);
+    const int g = bcmap(g0 + r, ny, bc);
+    T e[W];
+    vld<T, W>(src + (size_t)g * nx + c * W, e);
+    vst<T, W>(dst + r * nx + c * W, e);
+  }
+}
+template <class T>
+__device__ __forceinline__ void stage_rows(T* dst, const T* __restrict__ src, int nx, int lognx, int ny, int bc,
+                                           int g0, int nrows) {
+  constexpr int W = V16<T>::n;
+  if (nx >= W) stage_rows_w<T, W>(dst, src, nx, lognx, ny, bc, g0, nrows);
+  else stage_rows_w<T, 1>(dst, src, nx, lognx, ny, bc, g0, nrows);
+}
+
+// In-place forward epilogue over all lines (slot k <- real coefficients of both lines).
+template <class T>
+__device__ __forceinline__ void post_inplace(cx<T>* buf, int nlines, int logN, int ls, int bc,
+                                             const cx<T>* __restrict__ dc) {
+  const int N = 1 << logN, hn = N >> 1, lh = logN - 1;
+  for (int g = threadIdx.x; g < (nlines << lh); g += blockDim.x) {
+    const int line = g >> lh, k = g & (hn - 1);
+    cx<T>* L = buf + line * ls;
+    cx<T> ok, okp;
+    fwd_post(L, N, bc, dc, k, ok, okp);
+    if (k == 0) {
+      cx<T> mk, mkp;
+      fwd_post(L, N, bc, dc, hn, mk, mkp);
+      L[pidx(0)] = ok;
+      L[pidx(hn)] = mk;
+    } else {
+      L[pidx(k)] = ok;
+      L[pidx(N - k)] = okp;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// k_res
+// ---------------------------------------------------------------------------------------
+template <class T, int K, bool EDGE, int W>
+__device__ __forceinline__ void res_group(const Desc& d, cx<T>* buf, const T* xs, const T* bs, int srows, int r,
+                                          int j0, const T* rr0, const T* rr1, int lpc, int ls, T* w0, T* w1) {
+  constexpr bool PC = K == KK_PCONLY;
+  constexpr bool DC = !PC && sizeof(T) == 4;
+  constexpr int H = KT<K>::H;
+  const Rows<T, EDGE> x0{xs, d.nx, d.bc}, x1{xs + srows * d.nx, d.nx, d.bc};
+  const Rows<T, EDGE> b0{bs, d.nx, d.bc}, b1{bs + srows * d.nx, d.nx, d.bc};
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    T w[2] = {T(0), T(0)};
+    if constexpr (PC) {
+      w[0] = x0(r, j0 + q);
+      if (d.ncomp > 1) w[1] = x1(r, j0 + q);
+    } else {
+      residual_pt<T, K, DC>(d, x0, x1, b0, b1, H + r, j0 + q, rr0[q], KT<K>::two ? rr1[q] : T(0), w);
+    }
+    w0[q] = w[0];
+    w1[q] = w[1];
+  }
+}
+
+template <class T, int K, int W>
+__device__ __forceinline__ void res_points(const Desc& d, cx<T>* buf, const T* xs, const T* bs, int y0, int rows,
+                                           int ls, T& acc0, T& acc1) {
+  constexpr bool PC = K == KK_PCONLY;
+  constexpr int H = KT<K>::H;
+  const int nx = d.nx, bc = d.bc;
+  const int nc = PC ? d.ncomp : (KT<K>::two ? 2 : 1);
+  const size_t plane = (size_t)nx * d.ny;
+  const int srows = rows + 2 * H;
+  const int lpc = rows >> 1;
+  const T* R = static_cast<const T*>(d.rhs);
+  T* WY = static_cast<T*>(d.WY);
+  const bool transform = d.precond != 0;
+  const int lw = W == 4 ? 2 : (W == 2 ? 1 : 0);
+  const int lv = d.lognx - lw;
+  for (int v = threadIdx.x; v < (rows << lv); v += blockDim.x) {
+    const int r = v >> lv, j0 = (v & ((1 << lv) - 1)) * W;
+    const size_t o = (size_t)(y0 + r) * nx + j0;
+    T rr0[W], rr1[W];
+    if constexpr (!PC) {
+      vld<T, W>(R + o, rr0);
+      if constexpr (KT<K>::two) vld<T, W>(R + plane + o, rr1);
+    }
+    T w0[W], w1[W];
+    if (j0 >= 2 && j0 + W + 2 <= nx)
+      res_group<T, K, false, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, lpc, ls, w0, w1);
+    else
+      res_group<T, K, true, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, lpc, ls, w0, w1);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      acc0 += w0[q] * w0[q];
+      acc1 += w1[q] * w1[q];
+    }
+    if (transform) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        const int j = j0 + q;
+        const int slot = bc == BC_PERIODIC ? j : mk_slot(j, nx);
+        T* e0 = reinterpret_cast<T*>(buf + (r >> 1) * ls + pidx(slot));
+        e0[r & 1] = w0[q];
+        if (nc > 1) {
+          T* e1 = reinterpret_cast<T*>(buf + (lpc + (r >> 1)) * ls + pidx(slot));
+          e1[r & 1] = w1[q];
+        }
+      }
+    } else {
+      vst<T, W>(WY + o, w0);
+      if (nc > 1) vst<T, W>(WY + plane + o, w1);
+    }
+  }
+}
+
+template <class T, int K>
+__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_res(const __grid_constant__ Desc d, State* __restrict__ st) {
+  constexpr bool PC = K == KK_PCONLY;
+  constexpr bool DC = !PC && sizeof(T) == 4;
+  constexpr int H = KT<K>::H;
+  const int band = blockIdx.x;
+  if (band >= d.nbands) return;
+  if (!PC && *((volatile const int*)&st->status) != ST_ACTIVE) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nx = d.nx, ny = d.ny, bc = d.bc, lognx = d.lognx;
+  const int nc = PC ? d.ncomp : (KT<K>::two ? 2 : 1);
+  const size_t plane = (size_t)nx * ny;
+  const int y0 = band * d.band_rows;
+  const int rows = min(d.band_rows, ny - y0);
+  const int lpc = rows >> 1;
+  const int ls = padded_len(nx);
+  const int srows = rows + 2 * H;
+  T* WY = static_cast<T*>(d.WY);
+
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  T* xs = reinterpret_cast<T*>(buf + nc * lpc * ls);
+  T* bs = xs + nc * srows * nx;
+
+  // 1. stage the unknown (and the defect-correction base state) rows with halo
+  const T* X = static_cast<const T*>(d.X);
+  for (int c = 0; c < nc; ++c) stage_rows<T>(xs + c * srows * nx, X + c * plane, nx, lognx, ny, bc, y0 - H, srows);
+  if constexpr (DC && KT<K>::nonlinear) {
+    const T* Bg = static_cast<const T*>(d.base);
+    for (int c = 0; c < nc; ++c) stage_rows<T>(bs + c * srows * nx, Bg + c * plane, nx, lognx, ny, bc, y0 - H, srows);
+  }
+  __syncthreads();
+
+  // 2. W = F(U_n) on the band rows, written packed into the transform buffer
+  T acc0 = T(0), acc1 = T(0);
+  if (nx >= V16<T>::n) res_points<T, K, V16<T>::n>(d, buf, xs, bs, y0, rows, ls, acc0, acc1);
+  else res_points<T, K, 1>(d, buf, xs, bs, y0, rows, ls, acc0, acc1);
+
+  // 3. forward row transform and its epilogue straight to global memory
+  if (d.precond != 0) {
+    __syncthreads();
+    block_fft<T, -1>(buf, nc * lpc, lognx, ls, static_cast<const cx<T>*>(d.twx), tid, nt);
+    const int hn = nx >> 1, lh = lognx - 1;
+    const cx<T>* dcx = static_cast<const cx<T>*>(d.dcx);
+    for (int g = tid; g < ((nc * lpc) << lh); g += nt) {
+      const int line = g >> lh, k = g & (hn - 1);
+      const int c = line / lpc, m = line - c * lpc;
+      const cx<T>* L = buf + line * ls;
+      T* Wa = WY + c * plane + (size_t)(y0 + 2 * m) * nx;
+      T* Wb = Wa + nx;
+      cx<T> ok, okp;
+      fwd_post(L, nx, bc, dcx, k, ok, okp);
+      Wa[k] = ok.x;
+      Wb[k] = ok.y;
+      if (k != 0) {
+        Wa[nx - k] = okp.x;
+        Wb[nx - k] = okp.y;
+      } else {
+        fwd_post(L, nx, bc, dcx, hn, ok, okp);
+        Wa[hn] = ok.x;
+        Wb[hn] = ok.y;
+      }
+    }
+  }
+
+  if constexpr (PC) return;
+  // 4. partial norms, ticket, stopping decision in the last block
+  const double s0 = block_sum((double)acc0, red);
+  const double s1 = KT<K>::two ? block_sum((double)acc1, red) : 0.0;
+  if (tid == 0) {
+    d.partials[band] = s0;
+    if (KT<K>::two) d.partials[d.nbands + band] = s1;
+  }
+  if (last_block(st, d.nbands)) finalize_measure(d, st, red);
+}
+
+// ---------------------------------------------------------------------------------------
+// k_col
+// ---------------------------------------------------------------------------------------
+template <class T, bool PC>
+__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_col(const __grid_constant__ Desc d, State* __restrict__ st) {
+  if ((int)blockIdx.x >= d.ncomp * d.ncolblk) return;
+  if (!PC && *((volatile const int*)&st->status) != ST_ACTIVE) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nx = d.nx, ny = d.ny, logny = d.logny;
+  const size_t plane = (size_t)nx * ny;
+  const int c = blockIdx.x / d.ncolblk, cb = blockIdx.x - c * d.ncolblk;
+  const int x0 = cb * d.col_width;
+  const int nl = d.col_width >> 1;
+  const int lnl = ilog2i(nl);
+  const int ls = padded_len(ny);
+  T* WY = static_cast<T*>(d.WY) + c * plane;
+  const T* S = static_cast<const T*>(d.scale) + c * plane;
+  const cx<T>* twy = static_cast<const cx<T>*>(d.twy);
+  const cx<T>* dcy = static_cast<const cx<T>*>(d.dcy);
+  const bool per = d.bc == BC_PERIODIC;
+  const int hn = ny >> 1, lh = logny - 1;
+
+#pragma unroll 4
+  for (int g = tid; g < (ny << lnl); g += nt) {
+    const int row = g >> lnl, m = g & (nl - 1);
+    const cx<T> v = *reinterpret_cast<const cx<T>*>(WY + (size_t)row * nx + x0 + 2 * m);
+    const int slot = per ? row : mk_slot(row, ny);
+    buf[m * ls + pidx(slot)] = v;
+  }
+  __syncthreads();
+  block_fft<T, -1>(buf, nl, logny, ls, twy, tid, nt);
+  // forward epilogue and the spectral scaling 1 / (g_hat nx ny), in place
+  for (int g = tid; g < (nl << lh); g += nt) {
+    const int m = g >> lh, k = g & (hn - 1);
+    cx<T>* L = buf + m * ls;
+    const int col = x0 + 2 * m;
+    cx<T> ok, okp;
+    fwd_post(L, ny, d.bc, dcy, k, ok, okp);
+    const int k2 = k == 0 ? hn : ny - k;
+    if (k == 0) {
+      cx<T> t;
+      fwd_post(L, ny, d.bc, dcy, hn, okp, t);
+    }
+    const cx<T> s1 = *reinterpret_cast<const cx<T>*>(S + (size_t)k * nx + col);
+    const cx<T> s2 = *reinterpret_cast<const cx<T>*>(S + (size_t)k2 * nx + col);
+    L[pidx(k)] = cx<T>{ok.x * s1.x, ok.y * s1.y};
+    L[pidx(k2)] = cx<T>{okp.x * s2.x, okp.y * s2.y};
+  }
+  __syncthreads();
+  if (per) {
+    block_fft<T, -1>(buf, nl, logny, ls, twy, tid, nt);
+    post_inplace(buf, nl, logny, ls, d.bc, dcy);
+    __syncthreads();
+#pragma unroll 4
+    for (int g = tid; g < (ny << lnl); g += nt) {
+      const int row = g >> lnl, m = g & (nl - 1);
+      *reinterpret_cast<cx<T>*>(WY + (size_t)row * nx + x0 + 2 * m) = buf[m * ls + pidx(row)];
+    }
+  } else {
+    for (int g = tid; g < (nl << lh); g += nt) {
+      const int m = g >> lh, k = g & (hn - 1);
+      cx<T>* L = buf + m * ls;
+      const cx<T> w = ldg(dcy + k);
+      cx<T> zk, zkp;
+      if (k == 0) {
+        // k = 0 (partner X_N = 0) and the self-paired middle frequency N/2
+        dct_inv_pre(L[pidx(0)], cx<T>{T(0), T(0)}, w.x, w.y, zk, zkp);
+        const cx<T> Xm = L[pidx(hn)];
+        const cx<T> wm = ldg(dcy + hn);
+        cx<T> zm, zmp;
+        dct_inv_pre(Xm, Xm, wm.x, wm.y, zm, zmp);
+        L[pidx(0)] = zk;
+        L[pidx(hn)] = zm;
+      } else {
+        dct_inv_pre(L[pidx(k)], L[pidx(ny - k)], w.x, w.y, zk, zkp);
+        L[pidx(k)] = zk;
+        L[pidx(ny - k)] = zkp;
+      }
+    }
+    __syncthreads();
+    block_fft<T, 1>(buf, nl, logny, ls, twy, tid, nt);
+#pragma unroll 4
+    for (int g = tid; g < (ny << lnl); g += nt) {
+      const int n = g >> lnl, m = g & (nl - 1);
+      *reinterpret_cast<cx<T>*>(WY + (size_t)mk_perm(n, ny) * nx + x0 + 2 * m) = buf[m * ls + pidx(n)];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// k_upd
+// ---------------------------------------------------------------------------------------
+template <class T, int K, bool EDGE, int W>
+__device__ __forceinline__ void upd_group(const Desc& d, const cx<T>* buf, int ls, int lpc, int lr, int j0,
+                                          T* xa, T* xb, const T* sa, const T* sb) {
+  constexpr bool DC = sizeof(T) == 4;
+  const T tu = T(d.tau_u);
+  const Pairs<T, EDGE> p0{buf, ls, d.nx, d.bc, 0};
+  const Pairs<T, EDGE> p1{buf, ls, d.nx, d.bc, lpc};
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    T s0 = xa[q], s1 = KT<K>::two ? xb[q] : T(0);
+    if constexpr (DC && KT<K>::nonlinear) {
+      s0 += sa[q];
+      if constexpr (KT<K>::two) s1 += sb[q];
+    }
+    T g[2] = {T(0), T(0)};
+    gradT_pt<T, K>(d, p0, p1, s0, s1, lr, j0 + q, g);
+    xa[q] -= tu * g[0];
+    if constexpr (KT<K>::two) xb[q] -= tu * g[1];
+  }
+}
+
+template <class T, int K, int W>
+__device__ __forceinline__ void upd_points(const Desc& d, const cx<T>* buf, int y0, int rows, int ls, int lpc) {
+  constexpr bool DC = sizeof(T) == 4;
+  constexpr int H = KT<K>::H;
+  const int nx = d.nx;
+  const size_t plane = (size_t)nx * d.ny;
+  T* X = static_cast<T*>(d.X);
+  const T* Bs = static_cast<const T*>(d.base);
+  const int lw = W == 4 ? 2 : (W == 2 ? 1 : 0);
+  const int lv = d.lognx - lw;
+  for (int v = threadIdx.x; v < (rows << lv); v += blockDim.x) {
+    const int r = v >> lv, j0 = (v & ((1 << lv) - 1)) * W;
+    const size_t o = (size_t)(y0 + r) * nx + j0;
+    T xa[W], xb[W], sa[W], sb[W];
+    vld<T, W>(X + o, xa);
+    if constexpr (KT<K>::two) vld<T, W>(X + plane + o, xb);
+    if constexpr (DC && KT<K>::nonlinear) {
+      vld<T, W>(Bs + o, sa);
+      if constexpr (KT<K>::two) vld<T, W>(Bs + plane + o, sb);
+    }
+    if (j0 >= 2 && j0 + W + 2 <= nx) upd_group<T, K, false, W>(d, buf, ls, lpc, H + r, j0, xa, xb, sa, sb);
+    else upd_group<T, K, true, W>(d, buf, ls, lpc, H + r, j0, xa, xb, sa, sb);
+    vst<T, W>(X + o, xa);
+    if constexpr (KT<K>::two) vst<T, W>(X + plane + o, xb);
+  }
+}
+
+template <class T, int K>
+__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_upd(const __grid_constant__ Desc d, State* __restrict__ st) {
+  constexpr bool PC = K == KK_PCONLY;
+  constexpr int H = KT<K>::H;
+  const int band = blockIdx.x;
+  if (band >= d.nbands) return;
+  if (!PC && *((volatile const int*)&st->status) != ST_ACTIVE) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nx = d.nx, ny = d.ny, bc = d.bc, lognx = d.lognx;
+  const int nc = PC ? d.ncomp : (KT<K>::two ? 2 : 1);
+  const size_t plane = (size_t)nx * ny;
+  const int y0 = band * d.band_rows;
+  const int rows = min(d.band_rows, ny - y0);
+  const int lrows = rows + 2 * H;
+  const int lpc = lrows >> 1;
+  const int nl = nc * lpc;
+  const int ls = padded_len(nx);
+  const T* WY = static_cast<const T*>(d.WY);
+  const cx<T>* twx = static_cast<const cx<T>*>(d.twx);
+  const cx<T>* dcx = static_cast<const cx<T>*>(d.dcx);
+  const int hn = nx >> 1, lh = lognx - 1;
+
+  // 1. Y on rows y0-H .. y0+rows+H-1 (boundary-mapped) into buf, two rows per line
+  if (d.precond == 0 || bc == BC_PERIODIC) {
+#pragma unroll 2
+    for (int g = tid; g < (nl << lh); g += nt) {
+      const int line = g >> lh, j = 2 * (g & (hn - 1));
+      const int c = line / lpc, m = line - c * lpc;
+      const int ga = bcmap(y0 - H + 2 * m, ny, bc), gb = bcmap(y0 - H + 2 * m + 1, ny, bc);
+      const T* Wc = WY + c * plane;
+      const cx<T> a = *reinterpret_cast<const cx<T>*>(Wc + (size_t)ga * nx + j);
+      const cx<T> b = *reinterpret_cast<const cx<T>*>(Wc + (size_t)gb * nx + j);
+      buf[line * ls + pidx(j)] = cx<T>{a.x, b.x};
+      buf[line * ls + pidx(j + 1)] = cx<T>{a.y, b.y};
+    }
+    __syncthreads();
+    if (d.precond != 0) {
+      block_fft<T, -1>(buf, nl, lognx, ls, twx, tid, nt);
+      post_inplace(buf, nl, lognx, ls, bc, dcx);
+      __syncthreads();
+    }
+  } else {
+    for (int g = tid; g < (nl << lh); g += nt) {
+      const int line = g >> lh, k = g & (hn - 1);
+      const int c = line / lpc, m = line - c * lpc;
+      const int ga = bcmap(y0 - H + 2 * m, ny, bc), gb = bcmap(y0 - H + 2 * m + 1, ny, bc);
+      const T* Wa = WY + c * plane + (size_t)ga * nx;
+      const T* Wb = WY + c * plane + (size_t)gb * nx;
+      cx<T>* L = buf + line * ls;
+      const cx<T> w = ldg(dcx + k);
+      cx<T> zk, zkp;
+      if (k == 0) {
+        dct_inv_pre(cx<T>{Wa[0], Wb[0]}, cx<T>{T(0), T(0)}, w.x, w.y, zk, zkp);
+        const cx<T> Xm{Wa[hn], Wb[hn]};
+        const cx<T> wm = ldg(dcx + hn);
+        cx<T> zm, zmp;
+        dct_inv_pre(Xm, Xm, wm.x, wm.y, zm, zmp);
+        L[pidx(0)] = zk;
+        L[pidx(hn)] = zm;
+      } else {
+        dct_inv_pre(cx<T>{Wa[k], Wb[k]}, cx<T>{Wa[nx - k], Wb[nx - k]}, w.x, w.y, zk, zkp);
+        L[pidx(k)] = zk;
+        L[pidx(nx - k)] = zkp;
+      }
+    }
+    __syncthreads();
+    block_fft<T, 1>(buf, nl, lognx, ls, twx, tid, nt);
+    // undo the Makhoul reordering in place (slot n holds column mk_perm(n)), in chunks of lines
+    // so that each thread holds at most 16 values between the two barriers
+    {
+      constexpr int MAXV = 16;
+      int chunk = (nt * MAXV) >> lognx;
+      if (chunk < 1) chunk = 1;
+      for (int l0 = 0; l0 < nl; l0 += chunk) {
+        const int cl = nl - l0 < chunk ? nl - l0 : chunk;
+        const int total = cl << lognx;
+        const int nthr = (total + MAXV - 1) / MAXV;
+        cx<T> v[MAXV];
+#pragma unroll
+        for (int s = 0; s < MAXV; ++s) {
+          const int g = tid + s * nthr;
+          if (tid < nthr && g < total) v[s] = buf[(l0 + (g >> lognx)) * ls + pidx(g & (nx - 1))];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < MAXV; ++s) {
+          const int g = tid + s * nthr;
+          if (tid < nthr && g < total)
+            buf[(l0 + (g >> lognx)) * ls + pidx(mk_perm(g & (nx - 1), nx))] = v[s];
+        }
+        __syncthreads();
+      }
+    }
+  }
+
+  if constexpr (PC) {
+    T* X = static_cast<T*>(d.X);
+    const int rl = rows >> 1;
+    for (int g = tid; g < ((nc * rl) << lh); g += nt) {
+      const int line = g >> lh, j = 2 * (g & (hn - 1));
+      const int c = line / rl, m = line - c * rl;
+      const cx<T> e0 = buf[(c * lpc + m) * ls + pidx(j)], e1 = buf[(c * lpc + m) * ls + pidx(j + 1)];
+      T* Xa = X + c * plane + (size_t)(y0 + 2 * m) * nx + j;
+      *reinterpret_cast<cx<T>*>(Xa) = cx<T>{e0.x, e1.x};
+      *reinterpret_cast<cx<T>*>(Xa + nx) = cx<T>{e0.y, e1.y};
+    }
+    return;
+  } else {
+    // 2. P~ = P_n + (1 + omega) tau_p Y on all local rows (in place in buf);
+    //    P_{n+1} = P_n + tau_p Y on the band rows.  Each thread owns two slots of a line.
+    const int n = st->n;  // already counts this update
+    const T* Pin = static_cast<const T*>(d.P[(n - 1) & 1]);
+    T* Pout = static_cast<T*>(d.P[n & 1]);
+    const T tp = T(d.tau_p), tpe = T((1.0 + d.omega) * d.tau_p);
+#pragma unroll 2
+    for (int g = tid; g < (nl << lh); g += nt) {
+      const int line = g >> lh, j = 2 * (g & (hn - 1));
+      const int c = line / lpc, m = line - c * lpc;
+      const int la = 2 * m, lb = 2 * m + 1;
+      const size_t oa = c * plane + (size_t)bcmap(y0 - H + la, ny, bc) * nx + j;
+      const size_t ob = c * plane + (size_t)bcmap(y0 - H + lb, ny, bc) * nx + j;
+      const cx<T> pa = *reinterpret_cast<const cx<T>*>(Pin + oa);
+      const cx<T> pb = *reinterpret_cast<const cx<T>*>(Pin + ob);
+      cx<T>* s0 = buf + line * ls + pidx(j);
+      cx<T>* s1 = buf + line * ls + pidx(j + 1);
+      const cx<T> y0v = *s0, y1v = *s1;  // (row a, row b) at columns j, j+1
+      *s0 = cx<T>{pa.x + tpe * y0v.x, pb.x + tpe * y0v.y};
+      *s1 = cx<T>{pa.y + tpe * y1v.x, pb.y + tpe * y1v.y};
+      if (la >= H && la < H + rows) *reinterpret_cast<cx<T>*>(Pout + oa) = cx<T>{pa.x + tp * y0v.x, pa.y + tp * y1v.x};
+      if (lb >= H && lb < H + rows) *reinterpret_cast<cx<T>*>(Pout + ob) = cx<T>{pb.x + tp * y0v.y, pb.y + tp * y1v.y};
+    }
+    __syncthreads();
+
+    // 3. U_{n+1} = U_n - tau_u dF(U_n)^T P~ on band rows
+    if (nx >= V16<T>::n) upd_points<T, K, V16<T>::n>(d, buf, y0, rows, ls, lpc);
+    else upd_points<T, K, 1>(d, buf, y0, rows, ls, lpc);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+template <class K_>
+static cudaError_t allow_smem_k(K_ kernel, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+template <class T, int K>
+static cudaError_t launch_iter_k(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev) {
+  constexpr bool PC = K == KK_PCONLY;
+  if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  k_res<T, K><<<c.grid_bands, c.thr_res, c.smem_res, s>>>(d, st);
+  if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+  if (c.transform) k_col<T, PC><<<c.grid_cols, c.thr_col, c.smem_col, s>>>(d, st);
+  if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
+  k_upd<T, K><<<c.grid_bands, c.thr_upd, c.smem_upd, s>>>(d, st);
+  if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
+  return cudaGetLastError();
+}
+
+template <class T, int K>
+static cudaError_t allow_k(int optin) {
+  cudaError_t e;
+  if ((e = allow_smem_k(k_res<T, K>, optin)) != cudaSuccess) return e;
+  if ((e = allow_smem_k(k_upd<T, K>, optin)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+#define RD_SWEEP_INSTANTIATE(T)                                                                         \
+  template <>                                                                                            \
+  cudaError_t launch_iteration<T>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s,           \
+                                  cudaEvent_t* ev) {                                                     \
+    switch (kind_key(d)) {                                                                               \
+      case KK_NONE_LAP: return launch_iter_k<T, KK_NONE_LAP>(d, st, c, s, ev);                           \
+      case KK_AC: return launch_iter_k<T, KK_AC>(d, st, c, s, ev);                                       \
+      case KK_CH_IMPL: return launch_iter_k<T, KK_CH_IMPL>(d, st, c, s, ev);                             \
+      case KK_CH_SPLIT: return launch_iter_k<T, KK_CH_SPLIT>(d, st, c, s, ev);                           \
+      case KK_GS: return launch_iter_k<T, KK_GS>(d, st, c, s, ev);                                       \
+      case KK_SCHNAK: return launch_iter_k<T, KK_SCHNAK>(d, st, c, s, ev);                               \
+      case KK_NONE_BIH: return launch_iter_k<T, KK_NONE_BIH>(d, st, c, s, ev);                           \
+      default: return launch_iter_k<T, KK_PCONLY>(d, st, c, s, ev);                                     \
+    }                                                                                                    \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t set_kernel_smem_limits<T>(int* usable) {                                                   \
+    int dev = 0, optin = 0;                                                                              \
+    cudaError_t e;                                                                                       \
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;                                              \
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) \
+      return e;                                                                                          \
+    if ((e = allow_k<T, KK_NONE_LAP>(optin)) != cudaSuccess) return e;                                   \
+    if ((e = allow_k<T, KK_AC>(optin)) != cudaSuccess) return e;                                         \
+    if ((e = allow_k<T, KK_CH_IMPL>(optin)) != cudaSuccess) return e;                                    \
+    if ((e = allow_k<T, KK_CH_SPLIT>(optin)) != cudaSuccess) return e;                                   \
+    if ((e = allow_k<T, KK_GS>(optin)) != cudaSuccess) return e;                                         \
+    if ((e = allow_k<T, KK_SCHNAK>(optin)) != cudaSuccess) return e;                                     \
+    if ((e = allow_k<T, KK_NONE_BIH>(optin)) != cudaSuccess) return e;                                   \
+    if ((e = allow_k<T, KK_PCONLY>(optin)) != cudaSuccess) return e;                                     \
+    if ((e = allow_smem_k(k_col<T, false>, optin)) != cudaSuccess) return e;                             \
+    if ((e = allow_smem_k(k_col<T, true>, optin)) != cudaSuccess) return e;                              \
+    if (usable) *usable = optin - 1024;                                                                  \
+    return cudaSuccess;                                                                                  \
+  }
+
+}  // namespace rd
