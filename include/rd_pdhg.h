@@ -198,6 +198,27 @@ RD_API rd_status rd_pdhg_reset_stats(rd_pdhg *h);
 
 RD_API void rd_pdhg_destroy(rd_pdhg *h);
 
+/* Y <- G^{-1} W without any device allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need the operator -- code
+ * running inside a fixed memory budget it does not own, latency-critical loops that must not
+ * pay the device-wide synchronisation of cudaMalloc / cudaFree, or callers holding no solver
+ * handle.  It computes the same G = A_lin^2 solve as rd_pdhg_apply_precond for the equation
+ * described by (grid, bc, op, reaction, dt), with its scratch (transform buffer, twiddle and
+ * spectral-scale tables) in one static device array of 2.5 MiB that every device loading the
+ * library holds until process exit.
+ *   w, y: device arrays of ncomp*ny*nx doubles (caller-owned; y may alias w).
+ *   cuda_stream: cudaStream_t to issue the work on (NULL = legacy default); returns after the
+ *   stream is synchronised.
+ *   Limits: ncomp*nx*ny <= 131072 points and sides <= 2048, else RD_ERR_UNSUPPORTED.
+ *   The first call on a device does a one-time set-up for that device (looks up the scratch
+ *   array's device address, raises the kernels' shared-memory limit); make it before any stream
+ *   capture.  All calls share the scratch array and it keeps the last call's contents (every
+ *   entry is rewritten before it is read); calls that overlap on the GPU race on it, so order
+ *   them on one stream. */
+RD_API rd_status rd_apply_precond_static(const rd_grid *grid, rd_bc bc, rd_operator op,
+                                         const rd_reaction *reaction, double dt, const double *w,
+                                         double *y, void *cuda_stream);
+
 RD_API const char *rd_status_string(rd_status s);
 RD_API const char *rd_last_error(void);   /* detail of the last failing call on this thread */
 

@@ -138,6 +138,8 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
 
 }  // namespace
 
+void rd::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 struct rd_pdhg {
   int nx = 0, ny = 0, nc = 1;
   size_t npts = 0;  // nc * nx * ny

@@ -30,6 +30,9 @@ cudaError_t launch_resid64(const Desc& hd, const Desc* d64, State* outer, State*
                            const double* rhs, double* w64, float* r32, float* u32, float* z0, float* z1, int decide,
                            double rtol, int nbands, cudaStream_t s);
 
+// Set the thread-local detail string returned by rd_last_error().
+void set_last_error(const char* msg);
+
 cudaError_t launch_axpy_dc(double* u, const float* dlt, size_t n, cudaStream_t s);
 cudaError_t launch_mass(const Desc* d64, State* st, const double* u, int nbands, cudaStream_t s);
 

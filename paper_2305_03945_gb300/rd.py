@@ -25,7 +25,7 @@ PREC = {"fp64": 0, "fp32_dc": 1}
 
 EXPORTS = ("rd_opts_default", "rd_pdhg_create", "rd_pdhg_step", "rd_pdhg_solve", "rd_pdhg_solve_host",
            "rd_pdhg_residual", "rd_pdhg_apply_precond", "rd_pdhg_get_stats", "rd_pdhg_reset_stats",
-           "rd_pdhg_destroy", "rd_status_string", "rd_last_error")
+           "rd_pdhg_destroy", "rd_status_string", "rd_last_error", "rd_apply_precond_static")
 
 
 class rd_grid(ctypes.Structure):
@@ -105,6 +105,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rd_pdhg_reset_stats.restype = ctypes.c_int
     lib.rd_pdhg_destroy.argtypes = [vp]
     lib.rd_pdhg_destroy.restype = None
+    lib.rd_apply_precond_static.argtypes = [P(rd_grid), ctypes.c_int, ctypes.c_int, P(rd_reaction),
+                                            ctypes.c_double, vp, vp, vp]
+    lib.rd_apply_precond_static.restype = ctypes.c_int
     lib.rd_status_string.argtypes = [ctypes.c_int]
     lib.rd_status_string.restype = ctypes.c_char_p
     lib.rd_last_error.argtypes = []
