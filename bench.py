@@ -233,7 +233,8 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- chosen form: FP32 sweeps + FP64 defect correction ----
     u = torch.from_numpy(w.u0.copy()).to(dev)
-    sv = rd.Solver(pb, precision=args.precision, profile=1)
+    tune = dict(band_rows=args.band_rows, col_width=args.col_width, graph_k=args.graph_k)
+    sv = rd.Solver(pb, precision=args.precision, profile=1, **tune)
     with ClockSampler(local_rank) as clk:
         tot_ms, its, infos = timed_steps(sv, u, args.steps, args.warmup)
     st = sv.stats()
@@ -272,7 +273,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:
         uh = torch.from_numpy(w.u0.copy()).pin_memory()
         uh_np = uh.numpy()
-        sv_e = rd.Solver(pb, precision=args.precision)
+        sv_e = rd.Solver(pb, precision=args.precision, **tune)
         for _ in range(args.warmup):
             sv_e.solve_host(uh_np, 1)
         barrier()
@@ -344,7 +345,8 @@ def run_ours(args, rank, world, local_rank):
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "iterations_per_step": its / args.steps,
-                   "residual_passes_per_step": st["residual_passes"] / args.steps},
+                   "residual_passes_per_step": st["residual_passes"] / args.steps,
+                   "band_rows": args.band_rows, "col_width": args.col_width, "graph_k": args.graph_k},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "parity_full_size": parity, "fp64_plain": fp64,
         "gpu_launches": st["kernel_launches"], "clocks": clk.summary(), "source_hash": shash,
     }
@@ -365,6 +367,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--band-rows", type=int, default=0, help="rows per CTA of the band kernels (0 = planner)")
+    ap.add_argument("--col-width", type=int, default=0, help="columns per CTA of the column kernel (0 = planner)")
+    ap.add_argument("--graph-k", type=int, default=8, help="PDHG iterations per captured CUDA graph")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

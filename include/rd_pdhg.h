@@ -198,13 +198,78 @@ RD_API rd_status rd_pdhg_reset_stats(rd_pdhg *h);
 
 RD_API void rd_pdhg_destroy(rd_pdhg *h);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched, continuously served solves (no counterpart in the paper: a serving layer over the
+ * same method).  Every request is an independent run of nsteps implicit steps of one scalar
+ * equation (RD_RX_NONE, Allen-Cahn or Cahn-Hilliard; 2-D, sides powers of two in [4, 1024],
+ * either boundary condition) solved with FP32 PDHG sweeps inside FP64 defect correction to the
+ * request's tolerance.  The batch owns one device arena of hbm_budget_bytes; a request is
+ * admitted when a slot is free and its workspace (about 48 bytes per grid point) fits the
+ * arena, its state then stays resident on the GPU across all its steps, and all admitted
+ * requests advance together in shared launches (one per equation kind and sweep kernel, over
+ * every admitted grid size) of a CUDA graph that a library thread relaunches until the slot
+ * finishes.  Requests submitted while others run are admitted as slots and memory free up.
+ * --------------------------------------------------------------------------------------- */
+typedef struct rd_batch rd_batch;
+
+typedef struct {
+    rd_grid grid;
+    int bc;                /* rd_bc                                                             */
+    int op;                /* rd_operator (must match the kind, as for rd_pdhg_create)          */
+    rd_reaction reaction;
+    double dt;             /* h_t                                                               */
+    double tau, sigma;     /* PDHG primal / dual steps                                          */
+    double tol;            /* stopping threshold of every step (FP64 residual)                  */
+    int tol_kind;          /* rd_tol_kind                                                       */
+    int nsteps;            /* implicit steps to take (>= 1)                                     */
+    const double *u0_host; /* host, ncomp*ny*nx doubles; copied by rd_batch_submit              */
+    uint64_t tag;          /* caller's label, echoed in the result                              */
+} rd_request;
+
+typedef struct {
+    uint64_t id, tag;
+    int status;            /* rd_status of the run                                              */
+    int steps;             /* steps completed                                                   */
+    long long iterations;  /* FP32 PDHG updates over all steps                                  */
+    int outer_rounds;      /* FP64 residual evaluations over all steps                          */
+    double residual;       /* last stopping measure                                             */
+    double t_submit, t_admit, t_done;  /* host steady-clock seconds                             */
+} rd_result;
+
+typedef struct {
+    long long submitted, admitted, completed, graph_launches, queued, arena_free_bytes;
+} rd_batch_stats;
+
+/* Create a batch: arena of hbm_budget_bytes (allocated here, once), at most max_slots requests
+ * resident at a time, solver options (graph_k, max_iter, dc_inner_rtol, dc_max_outer, omega;
+ * NULL = defaults), work issued on cuda_stream.  Starts the library's scheduling thread. */
+RD_API rd_status rd_batch_create(rd_batch **out, size_t hbm_budget_bytes, int max_slots,
+                                 const rd_opts *opts, void *cuda_stream);
+
+/* Queue one request (u0 copied now).  When it finishes, its final state is copied to
+ * u_out_host (host, ncomp*ny*nx doubles, must stay valid until then; may be NULL) and a result
+ * becomes available to rd_batch_poll.  RD_ERR_BUSY: larger than the whole budget. */
+RD_API rd_status rd_batch_submit(rd_batch *b, const rd_request *req, double *u_out_host,
+                                 uint64_t *id);
+
+/* Move up to cap finished results into done (host array); waits up to timeout_s seconds for
+ * the first one when none is ready. */
+RD_API rd_status rd_batch_poll(rd_batch *b, rd_result *done, int cap, int *n_done,
+                               double timeout_s);
+
+RD_API rd_status rd_batch_get_stats(rd_batch *b, rd_batch_stats *out);
+
+/* Stop the scheduling thread (queued requests are dropped, running ones abandoned) and free
+ * everything. */
+RD_API void rd_batch_destroy(rd_batch *b);
+
 /* Y <- G^{-1} W without any device allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they need the operator -- code
  * running inside a fixed memory budget it does not own, latency-critical loops that must not
  * pay the device-wide synchronisation of cudaMalloc / cudaFree, or callers holding no solver
  * handle.  It computes the same G = A_lin^2 solve as rd_pdhg_apply_precond for the equation
  * described by (grid, bc, op, reaction, dt), with its scratch (transform buffer, twiddle and
- * spectral-scale tables) in one static device array of 2.5 MiB that every device loading the
+ * eigenvalue tables) in one static device array of 2.5 MiB that every device loading the
  * library holds until process exit.
  *   w, y: device arrays of ncomp*ny*nx doubles (caller-owned; y may alias w).
  *   cuda_stream: cudaStream_t to issue the work on (NULL = legacy default); returns after the

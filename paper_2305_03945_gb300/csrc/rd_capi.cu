@@ -83,7 +83,7 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     for (int cand = 16; cand >= 2; cand /= 2) {
       if (cand > ny) continue;
       const int nb = (ny + cand - 1) / cand;
-      const int sm = std::max(smem_lines<T>(nc * ((cand + 2 * H) / 2), nx), res_smem_bytes<T>(nc, cand, H, nx, dc));
+      const int sm = std::max(lines_smem_bytes<T>(nc * ((cand + 2 * H) / 2), nx), res_smem_bytes<T>(nc, cand, H, nx, dc));
       if (sm > kSmemLimit) continue;
       if (nb >= kTargetBlocks || cand == 2) {
         B = cand;
@@ -93,7 +93,7 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     if (B == 0) B = 2;
   }
   const int smem_res = res_smem_bytes<T>(nc, B, H, nx, dc);
-  const int smem_upd = smem_lines<T>(nc * ((B + 2 * H) / 2), nx);
+  const int smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx);
   if (smem_upd > kSmemLimit || smem_res > kSmemLimit) {
     why = "row band does not fit in shared memory";
     return false;
@@ -110,12 +110,12 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     C = cmin;
     for (int cand = cmin * 2; cand <= nx; cand *= 2) {
       if (nc * (nx / cand) < 2 * kTargetBlocks) break;
-      if (smem_lines<T>(cand / 2, ny) > kSmemLimit / 2) break;
+      if (lines_smem_bytes<T>(cand / 2, ny) > kSmemLimit / 2) break;
 
       C = cand;
     }
   }
-  const int smem_col = smem_lines<T>(C / 2, ny);
+  const int smem_col = lines_smem_bytes<T>(C / 2, ny);
   if (smem_col > kSmemLimit) {
     why = "column block does not fit in shared memory";
     return false;
@@ -155,13 +155,13 @@ struct rd_pdhg {
   double* rhs64 = nullptr;
   double* P64[2] = {nullptr, nullptr};
   double* WY64 = nullptr;
-  double* scale64 = nullptr;
+  double* mu64[2] = {nullptr, nullptr};  // mu_x, mu_y
   cx<double>* tw64[4] = {nullptr, nullptr, nullptr, nullptr};  // twx, twy, dcx, dcy
   // FP32 defect-correction workspaces
   float* D32 = nullptr;
   float* P32[2] = {nullptr, nullptr};
   float* WY32 = nullptr;
-  float* scale32 = nullptr;
+  float* mu32[2] = {nullptr, nullptr};
   float* r32 = nullptr;
   float* u32 = nullptr;
   cx<float>* tw32[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -215,37 +215,37 @@ void host_twiddles(int n, std::vector<double>& tw, std::vector<double>& dc) {
   }
 }
 
-// 1 / (g_hat nx ny) on the transform grid, g_hat = (1 + D dt mu)^2 or (1 + a dt mu^2)^2
-void host_scale(const rd_pdhg* h, std::vector<double>& s) {
-  const int nx = h->nx, ny = h->ny;
-  s.assign((size_t)h->nc * nx * ny, 0.0);
+// Eigenvalues of -Lap along each axis, mu(k) = 4/h^2 sin^2(pi k / (d n)) (d = 1 periodic,
+// 2 Neumann), evaluated in long double; the preconditioner symbol is
+// g_hat(kx, ky) = (1 + gc1 mu + gc2 mu^2)^2 with mu = mu_x(kx) + mu_y(ky).
+void host_mu(const rd_pdhg* h, std::vector<double>& mx, std::vector<double>& my) {
   const long double pi = 3.141592653589793238462643383279502884L;
   const long double dd = h->bc == RD_BC_PERIODIC ? 1.0L : 2.0L;
-  std::vector<long double> mx(nx), my(ny);
-  for (int k = 0; k < nx; ++k) {
-    const long double sn = sinl(pi * k / (dd * nx));
-    mx[k] = 4.0L / ((long double)h->hx * h->hx) * sn * sn;
+  mx.resize(h->nx);
+  my.resize(h->ny);
+  for (int k = 0; k < h->nx; ++k) {
+    const long double sn = sinl(pi * k / (dd * h->nx));
+    mx[k] = (double)(4.0L / ((long double)h->hx * h->hx) * sn * sn);
   }
-  for (int k = 0; k < ny; ++k) {
-    const long double sn = sinl(pi * k / (dd * ny));
-    my[k] = 4.0L / ((long double)h->hy * h->hy) * sn * sn;
+  for (int k = 0; k < h->ny; ++k) {
+    const long double sn = sinl(pi * k / (dd * h->ny));
+    my[k] = (double)(4.0L / ((long double)h->hy * h->hy) * sn * sn);
   }
-  for (int c = 0; c < h->nc; ++c) {
-    long double D = h->rx.a;
-    if (h->kind == RD_RX_GRAY_SCOTT || h->kind == RD_RX_SCHNAKENBERG) D = h->rx.p[c];
-    for (int ky = 0; ky < ny; ++ky)
-      for (int kx = 0; kx < nx; ++kx) {
-        const long double mu = mx[kx] + my[ky];
-        long double g;
-        if (h->op == RD_OP_LAPLACIAN) {
-          g = 1.0L + D * h->dt * mu;
-        } else {
-          g = 1.0L + (long double)h->rx.a * h->dt * mu * mu;
-        }
-        g = g * g;
-        s[((size_t)c * ny + ky) * nx + kx] = (double)(1.0L / (g * nx * ny));
-      }
+}
+
+void symbol_coefficients(const rd_pdhg* h, Desc& d) {
+  for (int c = 0; c < 2; ++c) {
+    double D = h->rx.a;
+    if (h->kind == RD_RX_GRAY_SCOTT || h->kind == RD_RX_SCHNAKENBERG) D = h->rx.p[c < h->nc ? c : 0];
+    if (h->op == RD_OP_LAPLACIAN) {
+      d.gc1[c] = D * h->dt;
+      d.gc2[c] = 0.0;
+    } else {
+      d.gc1[c] = 0.0;
+      d.gc2[c] = h->rx.a * h->dt;
+    }
   }
+  d.inv_nn = 1.0 / ((double)h->nx * (double)h->ny);
 }
 
 rd_status status_of(int st) {
@@ -387,10 +387,10 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   RD_TRY(dalloc(h, &h->d_state, 3 * sizeof(State)));
   RD_CUDA(cudaMallocHost(&h->h_state, 3 * sizeof(State)));
 
-  std::vector<double> twx, dcx, twy, dcy, sc;
+  std::vector<double> twx, dcx, twy, dcy, mx, my;
   host_twiddles(h->nx, twx, dcx);
   host_twiddles(h->ny, twy, dcy);
-  if (transform) host_scale(h, sc);
+  host_mu(h, mx, my);
 
   if (!h->dc) {
     RD_TRY(dalloc(h, &h->P64[0], n * sizeof(double)));
@@ -404,10 +404,10 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
     RD_CUDA(cudaMemcpy(h->tw64[1], twy.data(), twy.size() * sizeof(double), cudaMemcpyHostToDevice));
     RD_CUDA(cudaMemcpy(h->tw64[2], dcx.data(), dcx.size() * sizeof(double), cudaMemcpyHostToDevice));
     RD_CUDA(cudaMemcpy(h->tw64[3], dcy.data(), dcy.size() * sizeof(double), cudaMemcpyHostToDevice));
-    if (transform) {
-      RD_TRY(dalloc(h, &h->scale64, n * sizeof(double)));
-      RD_CUDA(cudaMemcpy(h->scale64, sc.data(), n * sizeof(double), cudaMemcpyHostToDevice));
-    }
+    RD_TRY(dalloc(h, &h->mu64[0], (size_t)h->nx * sizeof(double)));
+    RD_TRY(dalloc(h, &h->mu64[1], (size_t)h->ny * sizeof(double)));
+    RD_CUDA(cudaMemcpy(h->mu64[0], mx.data(), mx.size() * sizeof(double), cudaMemcpyHostToDevice));
+    RD_CUDA(cudaMemcpy(h->mu64[1], my.data(), my.size() * sizeof(double), cudaMemcpyHostToDevice));
   } else {
     RD_TRY(dalloc(h, &h->D32, n * sizeof(float)));
     RD_TRY(dalloc(h, &h->P32[0], n * sizeof(float)));
@@ -426,11 +426,12 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
     RD_TRY(up32(&h->tw32[1], twy, h->ny));
     RD_TRY(up32(&h->tw32[2], dcx, h->nx));
     RD_TRY(up32(&h->tw32[3], dcy, h->ny));
-    if (transform) {
-      RD_TRY(dalloc(h, &h->scale32, n * sizeof(float)));
-      f.assign(sc.begin(), sc.end());
-      RD_CUDA(cudaMemcpy(h->scale32, f.data(), n * sizeof(float), cudaMemcpyHostToDevice));
-    }
+    RD_TRY(dalloc(h, &h->mu32[0], (size_t)h->nx * sizeof(float)));
+    RD_TRY(dalloc(h, &h->mu32[1], (size_t)h->ny * sizeof(float)));
+    f.assign(mx.begin(), mx.end());
+    RD_CUDA(cudaMemcpy(h->mu32[0], f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    f.assign(my.begin(), my.end());
+    RD_CUDA(cudaMemcpy(h->mu32[1], f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
 
   // descriptors
@@ -443,7 +444,10 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   d64.P[0] = h->P64[0];
   d64.P[1] = h->P64[1];
   d64.WY = h->WY64;
-  d64.scale = h->scale64;
+  d64.scale = nullptr;
+  d64.mux = h->mu64[0];
+  d64.muy = h->mu64[1];
+  symbol_coefficients(h, d64);
   d64.twx = h->tw64[0];
   d64.twy = h->tw64[1];
   d64.dcx = h->tw64[2];
@@ -460,7 +464,10 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   d32.P[0] = h->P32[0];
   d32.P[1] = h->P32[1];
   d32.WY = h->WY32;
-  d32.scale = h->scale32;
+  d32.scale = nullptr;
+  d32.mux = h->mu32[0];
+  d32.muy = h->mu32[1];
+  symbol_coefficients(h, d32);
   d32.twx = h->tw32[0];
   d32.twy = h->tw32[1];
   d32.dcx = h->tw32[2];

@@ -115,22 +115,22 @@ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
 }
 
 // Twiddles w^r, r = 1..R-1, of one Stockham job from the table entries w^1, w^2, w^4, w^8
-// (w = exp(-2 pi i step / N)) and products of them.
+// (w = exp(-2 pi i step / N)) and products of them.  The table lives in shared memory.
 template <class T, int R>
 __device__ __forceinline__ void job_twiddles(const cx<T>* __restrict__ tw, int step, cx<T>* w) {
-  w[1] = ldg(tw + step);
+  w[1] = tw[step];
   if constexpr (R > 2) {
-    w[2] = ldg(tw + 2 * step);
+    w[2] = tw[2 * step];
     w[3] = cmul(w[1], w[2]);
   }
   if constexpr (R > 4) {
-    w[4] = ldg(tw + 4 * step);
+    w[4] = tw[4 * step];
     w[5] = cmul(w[1], w[4]);
     w[6] = cmul(w[2], w[4]);
     w[7] = cmul(w[3], w[4]);
   }
   if constexpr (R > 8) {
-    w[8] = ldg(tw + 8 * step);
+    w[8] = tw[8 * step];
 #pragma unroll
     for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
   }
@@ -241,7 +241,7 @@ __device__ __forceinline__ void fwd_post(const cx<T>* L, int N, int bc, const cx
     okp.x = T(0.5) * (zp.x + z.x - zp.y + z.y);
     okp.y = T(0.5) * (zp.x - z.x + zp.y + z.y);
   } else {
-    const cx<T> w = ldg(dc + k);  // (cos, sin)(pi k / 2N)
+    const cx<T> w = dc[k];  // (cos, sin)(pi k / 2N)
     const T c = w.x, s = w.y;
     ok.x = T(0.5) * (c * (z.x + zp.x) + s * (z.y - zp.y));
     ok.y = T(0.5) * (c * (z.y + zp.y) - s * (z.x - zp.x));
@@ -318,12 +318,50 @@ __device__ __forceinline__ T lap13(const F& f, int i, int j, T c, T hx2, T hy2) 
 // Shared-memory bytes of the residual band kernel: the complex transform buffer first, then
 // the staged real rows of the unknown (and of the defect-correction base state); every region
 // starts 16-byte aligned.
+// FP32 sweeps keep their twiddle / DCT rotation tables in shared memory; FP64 sweeps (which
+// need twice the bytes per line) read them from global memory.
+template <class T> struct SmemTables { static constexpr bool value = sizeof(T) == 4; };
+
 template <class T>
 __host__ __device__ inline int res_smem_bytes(int nc, int rows, int H, int nx, int dc) {
   const int ls = padded_len(nx);
+  const int tabs = SmemTables<T>::value ? 2 * nx * (int)sizeof(cx<T>) : 0;
   const int buf = nc * (rows >> 1) * ls * (int)sizeof(cx<T>);
   const int stg = nc * (rows + 2 * H) * nx * (int)sizeof(T);
-  return buf + stg * (dc ? 2 : 1);
+  return tabs + buf + stg * (dc ? 2 : 1);
+}
+
+// Shared-memory bytes of a kernel holding `nlines` transform lines of length n plus the
+// twiddle and DCT rotation tables of that length.
+template <class T>
+__host__ __device__ inline int lines_smem_bytes(int nlines, int n) {
+  return ((SmemTables<T>::value ? 2 * n : 0) + nlines * padded_len(n)) * (int)sizeof(cx<T>);
+}
+
+// Copy n entries of a complex table from global to shared memory (called by the whole block).
+template <class T>
+__device__ __forceinline__ void load_table(cx<T>* dst, const cx<T>* __restrict__ src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = ldg(src + k);
+}
+
+// The twiddle / rotation tables a sweep reads: staged into shared memory at `smem` (FP32) or
+// the global tables themselves (FP64).  Returns the first shared-memory byte after the tables.
+template <class T>
+__device__ __forceinline__ unsigned char* place_tables(unsigned char* smem, const void* tw_g, const void* dc_g, int n,
+                                                       bool load_tw, bool load_dc, const cx<T>*& tw,
+                                                       const cx<T>*& dc) {
+  if constexpr (SmemTables<T>::value) {
+    cx<T>* t = reinterpret_cast<cx<T>*>(smem);
+    if (load_tw) load_table(t, static_cast<const cx<T>*>(tw_g), n);
+    if (load_dc) load_table(t + n, static_cast<const cx<T>*>(dc_g), n);
+    tw = t;
+    dc = t + n;
+    return smem + 2 * n * sizeof(cx<T>);
+  } else {
+    tw = static_cast<const cx<T>*>(tw_g);
+    dc = static_cast<const cx<T>*>(dc_g);
+    return smem;
+  }
 }
 
 // block-wide sum of a double, valid in thread 0; sh must hold 32 doubles

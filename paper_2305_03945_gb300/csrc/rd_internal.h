@@ -37,6 +37,8 @@ struct Desc {
   int ncolblk;       // nx / col_width
   int meas_div_dt;   // 1: stopping measure is sum ||F_c|| / dt, else sum ||F_c||
   int stall_window;  // > 0: stop (as converged) when the measure has not halved for this many updates
+  int batched;       // 1: member of a batch (Slot control block, device-side phase machine)
+  int pad_b;
   double hx2, hy2;   // 1/h_x^2, 1/h_y^2
   double dt, a, b;
   double p[6];
@@ -46,12 +48,22 @@ struct Desc {
   const void* rhs;   // plain: rhs of the step (FP64); DC: r = F(u) rounded to FP32
   void* P[2];        // dual variable, ping-pong by iteration parity
   void* WY;          // transform buffer: F(U) row-transformed, then G^{-1}-scaled spectrum
-  const void* scale; // [ncomp][ny][nx] 1 / (g_hat nx ny) in T
+  const void* scale; // unused by the sweeps (kept for layout); see mux / muy
+  const void* mux;   // nx entries of T: 4/h_x^2 sin^2(pi kx / (d nx)), d = 1 periodic, 2 Neumann
+  const void* muy;   // ny entries of T
+  double gc1[2];     // per component: g_hat = (1 + gc1 mu + gc2 mu^2)^2, mu = mux + muy
+  double gc2[2];
+  double inv_nn;     // 1 / (nx ny): normalisation of the unnormalised transform pair
   const void* twx;   // nx complex T: exp(-2 pi i k / nx)
   const void* twy;   // ny complex T
   const void* dcx;   // nx complex T: (cos, sin)(pi k / (2 nx))
   const void* dcy;   // ny complex T
   double* partials;  // [ncomp][nbands] FP64 block partial sums
+  // batch only (FP64 descriptor): the FP32 arrays the outer loop writes or clears
+  float* f32_d;      // correction d
+  float* f32_p0;     // dual P_0 of the inner solve
+  float* f32_r;      // r = F(u) rounded to FP32
+  float* f32_u;      // u rounded to FP32
 };
 
 struct State {
@@ -67,6 +79,32 @@ struct State {
   double best;       // smallest measure at which the measure last halved (stall detection)
   int best_n;        // update count at that point
   unsigned int ticket;
+};
+
+// Phases of one slot of a batch (device-side control of FP64 defect correction and time steps).
+enum Phase {
+  PH_IDLE = 0,    // empty slot
+  PH_BEGIN = 1,   // new step: build rhs from U^k and the outer threshold
+  PH_RESID = 2,   // FP64 residual r = F(u), stopping decision, arm the FP32 inner solve
+  PH_INNER = 3,   // FP32 PDHG iterations on the correction equation
+  PH_AXPY = 4,    // u += d in FP64
+  PH_DONE = 5,    // all steps converged
+  PH_FAILED = 6   // diverged, or the outer loop did not converge
+};
+
+// Control block of one batch slot.
+struct Slot {
+  State outer;            // FP64 defect-correction loop of the current step
+  State inner;            // FP32 PDHG solve of the correction equation
+  int phase;              // Phase
+  int steps_done;
+  int nsteps;
+  int max_outer;          // outer rounds allowed per step
+  double tol;             // stopping threshold (RD_TOL_* of tol_kind)
+  double rtol;            // inner tolerance factor
+  long long inner_total;  // PDHG updates over all steps
+  int outer_total;        // FP64 residual passes over all steps
+  int tol_kind;
 };
 
 }  // namespace rd

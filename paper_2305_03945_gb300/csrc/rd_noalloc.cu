@@ -5,8 +5,8 @@
 // of the device), code paths where the implicit device synchronisation of cudaMalloc/cudaFree is
 // not acceptable (a latency-critical loop sharing the GPU with other work), or callers that hold
 // no solver handle at all and only want this one operator.  For them this file offers a variant
-// of the preconditioner-solve kernels whose scratch space (the intermediate transform array and
-// the twiddle / spectral-scale tables) lives in one statically sized device array instead of
+// of the preconditioner-solve kernels whose scratch space (the intermediate transform array, the
+// twiddle tables and the Laplacian eigenvalue tables) lives in one statically sized device array instead of
 // buffers obtained from cudaMalloc.  The caller still passes the input W and the output Y.
 //
 // Limits and sharing rules:
@@ -59,20 +59,12 @@ __global__ void k_noalloc_twiddles(rd::cx<double>* tw, rd::cx<double>* dc, int n
   }
 }
 
-// 1 / (g_hat nx ny) on the transform grid, g_hat = (1 + D dt mu)^2 or (1 + a dt mu^2)^2.
-__global__ void k_noalloc_scale(double* sc, int nx, int ny, int nc, int neumann, int biharm, double hx, double hy,
-                                double dt, double d0, double d1) {
-  const int npts = nx * ny;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * npts; e += gridDim.x * blockDim.x) {
-    const int c = e / npts, r = e - c * npts;
-    const int ky = r / nx, kx = r - ky * nx;
-    const double den = neumann ? 2.0 : 1.0;
-    const double sx = sinpi(kx / (den * nx)), sy = sinpi(ky / (den * ny));
-    const double mu = 4.0 / (hx * hx) * sx * sx + 4.0 / (hy * hy) * sy * sy;
-    const double D = c == 0 ? d0 : d1;
-    double g = biharm ? 1.0 + D * dt * mu * mu : 1.0 + D * dt * mu;
-    g = g * g;
-    sc[e] = 1.0 / (g * (double)nx * (double)ny);
+// Eigenvalues of -Lap along one axis, mu(k) = 4/h^2 sin^2(pi k / (d n)), d = 1 periodic,
+// 2 Neumann (the preconditioner symbol is built from mu_x(kx) + mu_y(ky) inside the kernels).
+__global__ void k_noalloc_mu(double* mu, int n, int neumann, double h) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const double sn = sinpi(k / ((neumann ? 2.0 : 1.0) * n));
+    mu[k] = 4.0 / (h * h) * sn * sn;
   }
 }
 
@@ -127,11 +119,11 @@ extern "C" RD_API rd_status rd_apply_precond_static(const rd_grid* grid, rd_bc b
   if (npts > kNoAllocMaxPoints)
     return nofail(RD_ERR_UNSUPPORTED, "grid larger than the allocation-free limit of 131072 points (ncomp*nx*ny)");
 
-  // carve the scratch array: transform buffer, scale table, twiddle tables
+  // carve the scratch array: transform buffer, twiddle tables, eigenvalue tables
   const size_t wy_bytes = npts * sizeof(double);
-  const size_t sc_bytes = npts * sizeof(double);
   const size_t tw_bytes = ((size_t)2 * nx + 2 * ny) * sizeof(rd::cx<double>);
-  if (wy_bytes + sc_bytes + tw_bytes > kNoAllocScratchBytes)
+  const size_t mu_bytes = ((size_t)nx + ny) * sizeof(double);
+  if (wy_bytes + tw_bytes + mu_bytes > kNoAllocScratchBytes)
     return nofail(RD_ERR_UNSUPPORTED, "grid does not fit the allocation-free scratch array");
 
   void* base = nullptr;
@@ -139,11 +131,12 @@ extern "C" RD_API rd_status rd_apply_precond_static(const rd_grid* grid, rd_bc b
   if (st != RD_OK) return st;
   unsigned char* p = static_cast<unsigned char*>(base);
   double* wy = reinterpret_cast<double*>(p);
-  double* sc = reinterpret_cast<double*>(p + wy_bytes);
-  rd::cx<double>* twx = reinterpret_cast<rd::cx<double>*>(p + wy_bytes + sc_bytes);
+  rd::cx<double>* twx = reinterpret_cast<rd::cx<double>*>(p + wy_bytes);
   rd::cx<double>* dcx = twx + nx;
   rd::cx<double>* twy = dcx + nx;
   rd::cx<double>* dcy = twy + ny;
+  double* mux = reinterpret_cast<double*>(dcy + ny);
+  double* muy = mux + nx;
 
   const double hx = grid->length[0] / nx, hy = grid->length[1] / ny;
   const double d0 = two ? reaction->p[0] : reaction->a;
@@ -171,7 +164,14 @@ extern "C" RD_API rd_status rd_apply_precond_static(const rd_grid* grid, rd_bc b
   d.dt = dt;
   d.X = y;
   d.WY = wy;
-  d.scale = sc;
+  d.mux = mux;
+  d.muy = muy;
+  for (int c = 0; c < 2; ++c) {
+    const double D = c == 0 ? d0 : d1;
+    d.gc1[c] = op == RD_OP_LAPLACIAN ? D * dt : 0.0;
+    d.gc2[c] = op == RD_OP_LAPLACIAN ? 0.0 : reaction->a * dt;
+  }
+  d.inv_nn = 1.0 / ((double)nx * (double)ny);
   d.twx = twx;
   d.twy = twy;
   d.dcx = dcx;
@@ -192,15 +192,15 @@ extern "C" RD_API rd_status rd_apply_precond_static(const rd_grid* grid, rd_bc b
   cfg.thr_upd = threads(nc, nx);
   cfg.thr_col = threads(1, ny);
   cfg.smem_res = rd::res_smem_bytes<double>(nc, 2, 0, nx, 0);
-  cfg.smem_upd = nc * rd::padded_len(nx) * (int)sizeof(rd::cx<double>);
-  cfg.smem_col = rd::padded_len(ny) * (int)sizeof(rd::cx<double>);
+  cfg.smem_upd = rd::lines_smem_bytes<double>(nc, nx);
+  cfg.smem_col = rd::lines_smem_bytes<double>(1, ny);
   cfg.transform = 1;
 
   cudaError_t e;
   k_noalloc_twiddles<<<(nx + 255) / 256, 256, 0, s>>>(twx, dcx, nx);
   k_noalloc_twiddles<<<(ny + 255) / 256, 256, 0, s>>>(twy, dcy, ny);
-  k_noalloc_scale<<<(int)((npts + 255) / 256), 256, 0, s>>>(sc, nx, ny, nc, bc == RD_BC_NEUMANN,
-                                                            op == RD_OP_NEG_BIHARMONIC, hx, hy, dt, d0, d1);
+  k_noalloc_mu<<<(nx + 255) / 256, 256, 0, s>>>(mux, nx, bc == RD_BC_NEUMANN, hx);
+  k_noalloc_mu<<<(ny + 255) / 256, 256, 0, s>>>(muy, ny, bc == RD_BC_NEUMANN, hy);
   if ((e = cudaGetLastError()) != cudaSuccess) return nofail(RD_ERR_CUDA, cudaGetErrorString(e));
   if (y != w) {
     e = cudaMemcpyAsync(y, w, npts * sizeof(double), cudaMemcpyDeviceToDevice, s);

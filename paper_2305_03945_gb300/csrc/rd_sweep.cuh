@@ -189,10 +189,25 @@ __device__ __forceinline__ double sum_partials(const double* p, int n, double* r
   return block_sum(s, red);
 }
 
+// Is the solve this sweep belongs to running?  Single solves look at their status; batch
+// members (slot != nullptr) at the slot's phase.
+__device__ __forceinline__ bool sweep_active(const State* st, const Slot* slot) {
+  if (slot) return *((volatile const int*)&slot->phase) == PH_INNER;
+  return *((volatile const int*)&st->status) == ST_ACTIVE;
+}
+
+// Cooperative copy of a descriptor into shared memory (batched kernels).
+__device__ __forceinline__ void load_desc(Desc& dst, const Desc* src) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* t = reinterpret_cast<int*>(&dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(Desc) / sizeof(int)); k += blockDim.x) t[k] = s[k];
+}
+
 // Stopping decision of one PDHG solve from the per-band partial sums (all threads of the last
 // block call it): r <= threshold -> converged; non-finite or 1e8-fold growth -> diverged;
-// max_iter updates done -> not converged; otherwise count the coming update.
-__device__ inline void finalize_measure(const Desc& d, State* st, double* red) {
+// max_iter updates done -> not converged; otherwise count the coming update.  A batch member
+// hands control back to its slot's defect-correction loop when the solve stops.
+__device__ inline void finalize_measure(const Desc& d, State* st, double* red, Slot* slot = nullptr) {
   __threadfence();
   double tot = 0.0;
   for (int c = 0; c < d.ncomp; ++c) tot += sqrt(sum_partials(d.partials + c * d.nbands, d.nbands, red));
@@ -220,6 +235,10 @@ __device__ inline void finalize_measure(const Desc& d, State* st, double* red) {
     st->status = ST_NOT_CONVERGED;
   } else {
     st->n = n + 1;
+  }
+  if (slot && st->status != ST_ACTIVE) {
+    slot->inner_total += st->n;
+    slot->phase = st->status == ST_DIVERGED ? PH_FAILED : PH_AXPY;
   }
 }
 
@@ -378,15 +397,14 @@ __device__ __forceinline__ void res_points(const Desc& d, cx<T>* buf, const T* x
 }
 
 template <class T, int K>
-__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_res(const __grid_constant__ Desc d, State* __restrict__ st) {
+__device__ __forceinline__ void res_body(const Desc& d, State* __restrict__ st, Slot* slot, int band,
+                                         unsigned char* smem_raw) {
   constexpr bool PC = K == KK_PCONLY;
   constexpr bool DC = !PC && sizeof(T) == 4;
   constexpr int H = KT<K>::H;
-  const int band = blockIdx.x;
   if (band >= d.nbands) return;
-  if (!PC && *((volatile const int*)&st->status) != ST_ACTIVE) return;
+  if (!PC && !sweep_active(st, slot)) return;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
 
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -400,11 +418,14 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_r
   const int srows = rows + 2 * H;
   T* WY = static_cast<T*>(d.WY);
 
-  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  // 1. stage the unknown (and the defect-correction base state) rows with halo, and the
+  //    transform tables
+  const cx<T>* tws;
+  const cx<T>* dcs;
+  cx<T>* buf = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, d.twx, d.dcx, nx, d.precond != 0,
+                                                        d.precond != 0 && bc == BC_NEUMANN, tws, dcs));
   T* xs = reinterpret_cast<T*>(buf + nc * lpc * ls);
   T* bs = xs + nc * srows * nx;
-
-  // 1. stage the unknown (and the defect-correction base state) rows with halo
   const T* X = static_cast<const T*>(d.X);
   for (int c = 0; c < nc; ++c) stage_rows<T>(xs + c * srows * nx, X + c * plane, nx, lognx, ny, bc, y0 - H, srows);
   if constexpr (DC && KT<K>::nonlinear) {
@@ -421,12 +442,12 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_r
   // 3. forward row transform and its epilogue straight to global memory
   if (d.precond != 0) {
     __syncthreads();
-    block_fft<T, -1>(buf, nc * lpc, lognx, ls, static_cast<const cx<T>*>(d.twx), tid, nt);
+    block_fft<T, -1>(buf, nc * lpc, lognx, ls, tws, tid, nt);
     const int hn = nx >> 1, lh = lognx - 1;
-    const cx<T>* dcx = static_cast<const cx<T>*>(d.dcx);
+    const cx<T>* dcx = dcs;
     for (int g = tid; g < ((nc * lpc) << lh); g += nt) {
       const int line = g >> lh, k = g & (hn - 1);
-      const int c = line / lpc, m = line - c * lpc;
+      const int c = (PC ? nc > 1 : KT<K>::two) ? line / lpc : 0, m = line - c * lpc;
       const cx<T>* L = buf + line * ls;
       T* Wa = WY + c * plane + (size_t)(y0 + 2 * m) * nx;
       T* Wb = Wa + nx;
@@ -453,34 +474,47 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_r
     d.partials[band] = s0;
     if (KT<K>::two) d.partials[d.nbands + band] = s1;
   }
-  if (last_block(st, d.nbands)) finalize_measure(d, st, red);
+  if (last_block(st, d.nbands)) finalize_measure(d, st, red, slot);
+}
+
+template <class T, int K>
+__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_res(const __grid_constant__ Desc d, State* __restrict__ st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  res_body<T, K>(d, st, nullptr, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------
 // k_col
 // ---------------------------------------------------------------------------------------
 template <class T, bool PC>
-__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_col(const __grid_constant__ Desc d, State* __restrict__ st) {
-  if ((int)blockIdx.x >= d.ncomp * d.ncolblk) return;
-  if (!PC && *((volatile const int*)&st->status) != ST_ACTIVE) return;
-
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+__device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, Slot* slot, int blk,
+                                         unsigned char* smem_raw) {
+  if (blk >= d.ncomp * d.ncolblk) return;
+  if (!PC && !sweep_active(st, slot)) return;
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nx = d.nx, ny = d.ny, logny = d.logny;
   const size_t plane = (size_t)nx * ny;
-  const int c = blockIdx.x / d.ncolblk, cb = blockIdx.x - c * d.ncolblk;
+  const int c = blk / d.ncolblk, cb = blk - c * d.ncolblk;
   const int x0 = cb * d.col_width;
   const int nl = d.col_width >> 1;
   const int lnl = ilog2i(nl);
   const int ls = padded_len(ny);
   T* WY = static_cast<T*>(d.WY) + c * plane;
-  const T* S = static_cast<const T*>(d.scale) + c * plane;
-  const cx<T>* twy = static_cast<const cx<T>*>(d.twy);
-  const cx<T>* dcy = static_cast<const cx<T>*>(d.dcy);
   const bool per = d.bc == BC_PERIODIC;
   const int hn = ny >> 1, lh = logny - 1;
+  const cx<T>* twy;
+  const cx<T>* dcy;
+  cx<T>* buf = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, d.twy, d.dcy, ny, true, !per, twy, dcy));
+  // spectral symbol 1 / (g_hat nx ny), g_hat = (1 + c1 mu + c2 mu^2)^2, mu = mu_x(kx) + mu_y(ky)
+  const T* mux = static_cast<const T*>(d.mux);
+  const T* muy = static_cast<const T*>(d.muy);
+  const T c1 = T(d.gc1[c]), c2 = T(d.gc2[c]), inn = T(d.inv_nn);
+  auto sym = [&](T mu) -> T {
+    const T g = T(1) + mu * (c1 + c2 * mu);
+    if constexpr (sizeof(T) == 4) return inn * __frcp_rn(g * g);
+    else return inn / (g * g);
+  };
 
 #pragma unroll 4
   for (int g = tid; g < (ny << lnl); g += nt) {
@@ -503,10 +537,10 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_c
       cx<T> t;
       fwd_post(L, ny, d.bc, dcy, hn, okp, t);
     }
-    const cx<T> s1 = *reinterpret_cast<const cx<T>*>(S + (size_t)k * nx + col);
-    const cx<T> s2 = *reinterpret_cast<const cx<T>*>(S + (size_t)k2 * nx + col);
-    L[pidx(k)] = cx<T>{ok.x * s1.x, ok.y * s1.y};
-    L[pidx(k2)] = cx<T>{okp.x * s2.x, okp.y * s2.y};
+    const T ma = __ldg(mux + col), mb = __ldg(mux + col + 1);
+    const T m1 = __ldg(muy + k), m2 = __ldg(muy + k2);
+    L[pidx(k)] = cx<T>{ok.x * sym(ma + m1), ok.y * sym(mb + m1)};
+    L[pidx(k2)] = cx<T>{okp.x * sym(ma + m2), okp.y * sym(mb + m2)};
   }
   __syncthreads();
   if (per) {
@@ -522,13 +556,13 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_c
     for (int g = tid; g < (nl << lh); g += nt) {
       const int m = g >> lh, k = g & (hn - 1);
       cx<T>* L = buf + m * ls;
-      const cx<T> w = ldg(dcy + k);
+      const cx<T> w = dcy[k];
       cx<T> zk, zkp;
       if (k == 0) {
         // k = 0 (partner X_N = 0) and the self-paired middle frequency N/2
         dct_inv_pre(L[pidx(0)], cx<T>{T(0), T(0)}, w.x, w.y, zk, zkp);
         const cx<T> Xm = L[pidx(hn)];
-        const cx<T> wm = ldg(dcy + hn);
+        const cx<T> wm = dcy[hn];
         cx<T> zm, zmp;
         dct_inv_pre(Xm, Xm, wm.x, wm.y, zm, zmp);
         L[pidx(0)] = zk;
@@ -547,6 +581,12 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_c
       *reinterpret_cast<cx<T>*>(WY + (size_t)mk_perm(n, ny) * nx + x0 + 2 * m) = buf[m * ls + pidx(n)];
     }
   }
+}
+
+template <class T, bool PC>
+__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_col(const __grid_constant__ Desc d, State* __restrict__ st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  col_body<T, PC>(d, st, nullptr, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -601,15 +641,12 @@ __device__ __forceinline__ void upd_points(const Desc& d, const cx<T>* buf, int 
 }
 
 template <class T, int K>
-__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_upd(const __grid_constant__ Desc d, State* __restrict__ st) {
+__device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, Slot* slot, int band,
+                                         unsigned char* smem_raw) {
   constexpr bool PC = K == KK_PCONLY;
   constexpr int H = KT<K>::H;
-  const int band = blockIdx.x;
   if (band >= d.nbands) return;
-  if (!PC && *((volatile const int*)&st->status) != ST_ACTIVE) return;
-
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  if (!PC && !sweep_active(st, slot)) return;
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nx = d.nx, ny = d.ny, bc = d.bc, lognx = d.lognx;
@@ -622,16 +659,19 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_u
   const int nl = nc * lpc;
   const int ls = padded_len(nx);
   const T* WY = static_cast<const T*>(d.WY);
-  const cx<T>* twx = static_cast<const cx<T>*>(d.twx);
-  const cx<T>* dcx = static_cast<const cx<T>*>(d.dcx);
+  const cx<T>* twx;
+  const cx<T>* dcx;
+  cx<T>* buf = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, d.twx, d.dcx, nx, d.precond != 0,
+                                                        d.precond != 0 && bc == BC_NEUMANN, twx, dcx));
   const int hn = nx >> 1, lh = lognx - 1;
+  if (SmemTables<T>::value && d.precond != 0 && bc == BC_NEUMANN) __syncthreads();
 
   // 1. Y on rows y0-H .. y0+rows+H-1 (boundary-mapped) into buf, two rows per line
   if (d.precond == 0 || bc == BC_PERIODIC) {
 #pragma unroll 2
     for (int g = tid; g < (nl << lh); g += nt) {
       const int line = g >> lh, j = 2 * (g & (hn - 1));
-      const int c = line / lpc, m = line - c * lpc;
+      const int c = (PC ? nc > 1 : KT<K>::two) ? line / lpc : 0, m = line - c * lpc;
       const int ga = bcmap(y0 - H + 2 * m, ny, bc), gb = bcmap(y0 - H + 2 * m + 1, ny, bc);
       const T* Wc = WY + c * plane;
       const cx<T> a = *reinterpret_cast<const cx<T>*>(Wc + (size_t)ga * nx + j);
@@ -648,17 +688,17 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_u
   } else {
     for (int g = tid; g < (nl << lh); g += nt) {
       const int line = g >> lh, k = g & (hn - 1);
-      const int c = line / lpc, m = line - c * lpc;
+      const int c = (PC ? nc > 1 : KT<K>::two) ? line / lpc : 0, m = line - c * lpc;
       const int ga = bcmap(y0 - H + 2 * m, ny, bc), gb = bcmap(y0 - H + 2 * m + 1, ny, bc);
       const T* Wa = WY + c * plane + (size_t)ga * nx;
       const T* Wb = WY + c * plane + (size_t)gb * nx;
       cx<T>* L = buf + line * ls;
-      const cx<T> w = ldg(dcx + k);
+      const cx<T> w = dcx[k];
       cx<T> zk, zkp;
       if (k == 0) {
         dct_inv_pre(cx<T>{Wa[0], Wb[0]}, cx<T>{T(0), T(0)}, w.x, w.y, zk, zkp);
         const cx<T> Xm{Wa[hn], Wb[hn]};
-        const cx<T> wm = ldg(dcx + hn);
+        const cx<T> wm = dcx[hn];
         cx<T> zm, zmp;
         dct_inv_pre(Xm, Xm, wm.x, wm.y, zm, zmp);
         L[pidx(0)] = zk;
@@ -721,7 +761,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_u
 #pragma unroll 2
     for (int g = tid; g < (nl << lh); g += nt) {
       const int line = g >> lh, j = 2 * (g & (hn - 1));
-      const int c = line / lpc, m = line - c * lpc;
+      const int c = (PC ? nc > 1 : KT<K>::two) ? line / lpc : 0, m = line - c * lpc;
       const int la = 2 * m, lb = 2 * m + 1;
       const size_t oa = c * plane + (size_t)bcmap(y0 - H + la, ny, bc) * nx + j;
       const size_t ob = c * plane + (size_t)bcmap(y0 - H + lb, ny, bc) * nx + j;
@@ -741,6 +781,12 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_u
     if (nx >= V16<T>::n) upd_points<T, K, V16<T>::n>(d, buf, y0, rows, ls, lpc);
     else upd_points<T, K, 1>(d, buf, y0, rows, ls, lpc);
   }
+}
+
+template <class T, int K>
+__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_upd(const __grid_constant__ Desc d, State* __restrict__ st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  upd_body<T, K>(d, st, nullptr, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -25,7 +25,8 @@ PREC = {"fp64": 0, "fp32_dc": 1}
 
 EXPORTS = ("rd_opts_default", "rd_pdhg_create", "rd_pdhg_step", "rd_pdhg_solve", "rd_pdhg_solve_host",
            "rd_pdhg_residual", "rd_pdhg_apply_precond", "rd_pdhg_get_stats", "rd_pdhg_reset_stats",
-           "rd_pdhg_destroy", "rd_status_string", "rd_last_error", "rd_apply_precond_static")
+           "rd_pdhg_destroy", "rd_status_string", "rd_last_error", "rd_apply_precond_static",
+           "rd_batch_create", "rd_batch_submit", "rd_batch_poll", "rd_batch_get_stats", "rd_batch_destroy")
 
 
 class rd_grid(ctypes.Structure):
@@ -70,6 +71,28 @@ class rd_step_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class rd_request(ctypes.Structure):
+    _fields_ = [("grid", rd_grid), ("bc", ctypes.c_int), ("op", ctypes.c_int), ("reaction", rd_reaction),
+                ("dt", ctypes.c_double), ("tau", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("tol", ctypes.c_double), ("tol_kind", ctypes.c_int), ("nsteps", ctypes.c_int),
+                ("u0_host", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class rd_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("steps", ctypes.c_int), ("iterations", ctypes.c_longlong), ("outer_rounds", ctypes.c_int),
+                ("residual", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rd_batch_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "admitted", "completed", "graph_launches",
+                                                  "queued", "arena_free_bytes")]
+
+
 _lib = None
 
 
@@ -108,6 +131,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rd_apply_precond_static.argtypes = [P(rd_grid), ctypes.c_int, ctypes.c_int, P(rd_reaction),
                                             ctypes.c_double, vp, vp, vp]
     lib.rd_apply_precond_static.restype = ctypes.c_int
+    lib.rd_batch_create.argtypes = [P(vp), ctypes.c_size_t, ctypes.c_int, P(rd_opts), vp]
+    lib.rd_batch_create.restype = ctypes.c_int
+    lib.rd_batch_submit.argtypes = [vp, P(rd_request), vp, P(ctypes.c_uint64)]
+    lib.rd_batch_submit.restype = ctypes.c_int
+    lib.rd_batch_poll.argtypes = [vp, P(rd_result), ctypes.c_int, P(ctypes.c_int), ctypes.c_double]
+    lib.rd_batch_poll.restype = ctypes.c_int
+    lib.rd_batch_get_stats.argtypes = [vp, P(rd_batch_stats)]
+    lib.rd_batch_get_stats.restype = ctypes.c_int
+    lib.rd_batch_destroy.argtypes = [vp]
+    lib.rd_batch_destroy.restype = None
     lib.rd_status_string.argtypes = [ctypes.c_int]
     lib.rd_status_string.restype = ctypes.c_char_p
     lib.rd_last_error.argtypes = []
@@ -233,3 +266,74 @@ class Solver:
 
     def apply_precond(self, w, y):
         _check(load().rd_pdhg_apply_precond(self.h, self._ptr(w), self._ptr(y)))
+
+
+class Batch:
+    """Continuous-batching server of implicit-step runs (rd_batch_*).  Requests are
+    ``workloads.Problem`` records plus a host float64 initial state and a step count; results
+    come back through ``poll``, final states in the host arrays returned by ``submit``."""
+
+    def __init__(self, hbm_budget_bytes, max_slots, graph_k=8, max_iter=10000, dc_inner_rtol=1e-4,
+                 dc_max_outer=12, stream=None):
+        import torch
+        lib = load()
+        o = rd_opts()
+        lib.rd_opts_default(ctypes.byref(o))
+        o.graph_k, o.max_iter, o.dc_inner_rtol, o.dc_max_outer = graph_k, max_iter, dc_inner_rtol, dc_max_outer
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        _check(lib.rd_batch_create(ctypes.byref(h), int(hbm_budget_bytes), int(max_slots), ctypes.byref(o),
+                                   ctypes.c_void_p(stream)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, pb, u0, nsteps, tag=0):
+        """Queue a run; returns (id, out) where out (host float64, the shape of u0) receives the
+        final state when the run finishes."""
+        import numpy as np
+        g, rx, pc, o = make_structs(pb)
+        r = rd_request()
+        r.grid = g
+        r.bc, r.op, r.reaction = BC[pb.bc], OP[pb.op], rx
+        r.dt, r.tau, r.sigma = pb.dt, pb.tau_u, pb.tau_p
+        r.tol, r.tol_kind, r.nsteps = pb.tol, TOL[pb.tol_kind], nsteps
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        out = np.empty_like(u0)
+        r.u0_host = u0.ctypes.data
+        r.tag = tag
+        rid = ctypes.c_uint64()
+        _check(load().rd_batch_submit(self.h, ctypes.byref(r), ctypes.c_void_p(out.ctypes.data), ctypes.byref(rid)))
+        self._keep[rid.value] = out
+        return rid.value, out
+
+    def poll(self, cap=64, timeout=0.0):
+        res = (rd_result * cap)()
+        n = ctypes.c_int()
+        _check(load().rd_batch_poll(self.h, res, cap, ctypes.byref(n), float(timeout)))
+        out = [res[k].as_dict() for k in range(n.value)]
+        for r in out:
+            self._keep.pop(r["id"], None)
+        return out
+
+    def stats(self):
+        st = rd_batch_stats()
+        _check(load().rd_batch_get_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().rd_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

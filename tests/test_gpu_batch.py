@@ -1,0 +1,100 @@
+"""Batched, continuously served runs (rd_batch_*) on the GPU: results against the CPU oracle,
+the same request alone and inside a mix of uneven grid sizes, admission under a small HBM
+budget."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import rd_oracle as O
+from paper_2305_03945_gb300 import workloads as WL
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_03945_gb300 import build
+    build.build()
+
+
+def _requests():
+    """Uneven sizes and both boundary conditions: Allen-Cahn and Cahn-Hilliard."""
+    out = []
+    for k, (kind, op, bc, ny, nx) in enumerate([
+        ("allen_cahn", "laplacian", "periodic", 64, 64),
+        ("allen_cahn", "laplacian", "neumann", 32, 128),
+        ("ch_split", "neg_biharmonic", "periodic", 128, 128),
+        ("ch_implicit", "neg_biharmonic", "neumann", 64, 32),
+        ("allen_cahn", "laplacian", "periodic", 256, 256),
+        ("none", "laplacian", "neumann", 16, 16),
+    ]):
+        ch = op == "neg_biharmonic"
+        pb = WL.Problem(nx=nx, ny=ny, lx=1.0, ly=1.0, bc=bc, op=op, kind=kind,
+                        dt=1e-5 if ch else 2e-3, a=4e-4 if ch else 0.05, b=1.0 if ch else 20.0,
+                        tau_u=1.0, tau_p=1.0, tol=1e-11, tol_kind="f_rel")
+        u0 = WL.uniform_field(50 + k, pb.shape, -0.5, 0.5)
+        out.append((pb, u0, 3 + k % 2))
+    return out
+
+
+def _run(reqs, budget=1 << 30, slots=16):
+    from paper_2305_03945_gb300 import rd
+    results, outs = {}, {}
+    with rd.Batch(budget, slots) as b:
+        ids = []
+        for k, (pb, u0, n) in enumerate(reqs):
+            rid, out = b.submit(pb, u0, n, tag=k)
+            ids.append(rid)
+            outs[rid] = out
+        t0 = time.time()
+        while len(results) < len(ids) and time.time() - t0 < 120:
+            for r in b.poll(timeout=1.0):
+                results[r["id"]] = r
+        stats = b.stats()
+    return ids, results, outs, stats
+
+
+def test_batch_matches_oracle_per_request():
+    reqs = _requests()
+    ids, results, outs, stats = _run(reqs)
+    assert len(results) == len(reqs)
+    for rid, (pb, u0, n) in zip(ids, reqs):
+        r = results[rid]
+        assert r["status"] == 0 and r["steps"] == n, r
+        U_ref, _ = O.solve(pb, u0, n)
+        err = np.linalg.norm(outs[rid] - U_ref) / np.linalg.norm(U_ref)
+        assert err <= 1e-9, (pb.kind, pb.bc, pb.nx, pb.ny, err)
+    assert stats["completed"] == len(reqs)
+
+
+def test_same_result_alone_and_in_the_mix():
+    reqs = _requests()
+    probe = reqs[2]
+    _, res_alone, out_alone, _ = _run([probe])
+    ids, res_mix, out_mix, _ = _run(reqs)
+    a = next(iter(out_alone.values()))
+    m = out_mix[ids[2]]
+    assert np.array_equal(a, m)
+    assert next(iter(res_alone.values()))["iterations"] == res_mix[ids[2]]["iterations"]
+
+
+def test_admission_under_a_small_budget():
+    """A budget that holds only a couple of 128^2 slots still serves every request."""
+    reqs = [r for r in _requests() if r[0].nx <= 128][:4] * 2
+    ids, results, outs, stats = _run(reqs, budget=3 * 128 * 128 * 48 + (8 << 20), slots=8)
+    assert len(results) == len(reqs) and all(r["status"] == 0 for r in results.values())
+    assert stats["admitted"] == len(reqs)
+    assert max(r["t_admit"] - r["t_submit"] for r in results.values()) > 0
+
+
+def test_request_larger_than_budget_is_refused():
+    from paper_2305_03945_gb300 import rd
+    pb, u0, n = _requests()[4]  # 256^2
+    with rd.Batch(2 << 20, 4) as b:
+        with pytest.raises(rd.RDError) as e:
+            b.submit(pb, u0, n)
+        assert e.value.status == rd.RD_ERR_BUSY
