@@ -187,6 +187,85 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------------------------
+# serving: continuous batching of a request mix vs per-request plain FP64
+# --------------------------------------------------------------------------------------------
+def serve(reqs, arrivals, budget, slots):
+    """Run the requests through one rd_batch; arrivals = submit times in seconds (None = all at
+    once).  Returns (wall seconds, per-request results, final states)."""
+    from paper_2305_03945_gb300 import rd
+    results, outs = {}, {}
+    with rd.Batch(budget, slots) as b:
+        t0 = time.perf_counter()
+        pending = list(range(len(reqs)))
+        ids = {}
+        while pending or len(results) < len(reqs):
+            now = time.perf_counter() - t0
+            while pending and (arrivals is None or arrivals[pending[0]] <= now):
+                k = pending.pop(0)
+                pb, u0, n = reqs[k]
+                rid, out = b.submit(pb, u0, n, tag=k)
+                ids[rid] = k
+                outs[k] = out
+            wait = 0.0005 if pending else 0.5
+            for r in b.poll(timeout=wait):
+                results[ids[r["id"]]] = r
+            if time.perf_counter() - t0 > 600:
+                raise RuntimeError("serving run exceeded 600 s")
+        wall = time.perf_counter() - t0
+    return wall, results, outs
+
+
+def serving_leg(n_req, seed, rates, budget, slots, fp64_sample):
+    import numpy as np
+    import torch
+    from paper_2305_03945_gb300 import rd, workloads as WL
+    reqs = WL.serving_requests(n_req, seed)
+    # warm-up (kernel first-use costs, graph capture paths)
+    serve(reqs[:2], None, budget, slots)
+    wall_sat, res_sat, outs_sat = serve(reqs, None, budget, slots)
+    ok = all(r["status"] == 0 for r in res_sat.values())
+    sat = len(reqs) / wall_sat
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res_sat.values()])
+    out = {"requests": n_req, "sides": list(WL.SERVING_SIDES), "kinds": "allen_cahn | ch_split, periodic | neumann",
+           "steps": "10-50", "tol": "f_rel 1e-6", "hbm_budget_gb": budget / 2**30, "max_slots": slots,
+           "saturation": {"solves_per_s": sat, "wall_s": wall_sat, "all_converged": ok,
+                          "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99))},
+           "poisson": []}
+    for f in rates:
+        arr = WL.poisson_arrivals(n_req, f * sat, seed + 17)
+        wall, res, _ = serve(reqs, arr, budget, slots)
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res.values()])
+        out["poisson"].append({"rate_fraction_of_saturation": f, "rate_per_s": f * sat,
+                               "solves_per_s": len(reqs) / wall,
+                               "p50_latency_s": float(np.percentile(lat, 50)),
+                               "p99_latency_s": float(np.percentile(lat, 99)),
+                               "all_converged": all(r["status"] == 0 for r in res.values())})
+    # per-request plain FP64, one request after another (sample), same tolerance
+    idx = list(range(min(fp64_sample, n_req)))
+    t_fp64 = 0.0
+    errs = []
+    for k in idx:
+        pb, u0, n = reqs[k]
+        u = torch.from_numpy(u0.copy()).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with rd.Solver(pb, precision="fp64") as s:
+            s.solve(u, n)
+        torch.cuda.synchronize()
+        t_fp64 += time.perf_counter() - t0
+        ref = u.cpu().numpy()
+        errs.append(float(np.linalg.norm(outs_sat[k] - ref) / np.linalg.norm(ref)))
+    fp64_rate = len(idx) / t_fp64
+    # the batched rate on the same sample, for a like-for-like ratio
+    wall_s, _, _ = serve([reqs[k] for k in idx], None, budget, slots)
+    out["per_request_fp64"] = {"sample": len(idx), "solves_per_s": fp64_rate,
+                               "batched_solves_per_s_same_sample": len(idx) / wall_s,
+                               "speedup_batched_vs_fp64": (len(idx) / wall_s) / fp64_rate,
+                               "max_rel_l2_batched_vs_fp64": max(errs)}
+    return out
+
+
+# --------------------------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
@@ -333,6 +412,10 @@ def run_ours(args, rank, world, local_rank):
                   "max_rel_vs_oracle": float(np.max(np.abs(got - U_ref)) / np.max(np.abs(U_ref)))}
 
     sv.close()
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_leg(args.serving_requests, 5000, args.serving_rates, args.serving_budget_gb * 2**30,
+                              args.serving_slots, args.serving_fp64_sample)
     if rank != 0:
         return 0
     line = {
@@ -348,6 +431,7 @@ def run_ours(args, rank, world, local_rank):
                    "residual_passes_per_step": st["residual_passes"] / args.steps,
                    "band_rows": args.band_rows, "col_width": args.col_width, "graph_k": args.graph_k},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "parity_full_size": parity, "fp64_plain": fp64,
+        "serving": serving,
         "gpu_launches": st["kernel_launches"], "clocks": clk.summary(), "source_hash": shash,
     }
     print(json.dumps(line))
@@ -370,6 +454,12 @@ def main():
     ap.add_argument("--band-rows", type=int, default=0, help="rows per CTA of the band kernels (0 = planner)")
     ap.add_argument("--col-width", type=int, default=0, help="columns per CTA of the column kernel (0 = planner)")
     ap.add_argument("--graph-k", type=int, default=8, help="PDHG iterations per captured CUDA graph")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-rates", type=float, nargs="*", default=[0.5, 1.0])
+    ap.add_argument("--serving-budget-gb", type=float, default=8.0)
+    ap.add_argument("--serving-slots", type=int, default=32)
+    ap.add_argument("--serving-fp64-sample", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

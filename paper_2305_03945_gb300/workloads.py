@@ -286,3 +286,42 @@ def workload_small(name: str, n: int, nsteps: int, seed: int = 7) -> Workload:
     if name == "schnakenberg":
         return config_schnakenberg(n, nsteps)
     raise KeyError(name)
+
+
+# --------------------------------------------------------------------------------------
+# serving mix
+# --------------------------------------------------------------------------------------
+
+SERVING_SIDES = (64, 128, 256, 512, 1024)
+
+
+def serving_requests(n: int, seed: int = 5000, min_steps: int = 10, max_steps: int = 50,
+                     sides=SERVING_SIDES, tol: float = 1e-6):
+    """The serving mix: n seeded requests, each an Allen-Cahn (physics of the 64^2 periodic
+    configuration, domain [0,2pi)^2) or Cahn-Hilliard convex-split (physics of the 512^2
+    configuration, domain [0,1]^2) run of min_steps..max_steps implicit steps on a square grid
+    drawn uniformly from `sides`, periodic or Neumann 50/50, each step solved to
+    ||F||_2 <= tol ||U^k||_2.  Returns a list of (Problem, u0, nsteps)."""
+    r = rng(seed)
+    out = []
+    for k in range(n):
+        side = int(r.choice(sides))
+        bc = "periodic" if r.random() < 0.5 else "neumann"
+        steps = int(r.integers(min_steps, max_steps + 1))
+        if r.random() < 0.5:
+            pb = Problem(nx=side, ny=side, lx=2 * np.pi, ly=2 * np.pi, bc=bc, op="laplacian",
+                         kind="allen_cahn", a=0.1, b=10.0, dt=0.01, tau_u=1.0, tau_p=1.0,
+                         tol=tol, tol_kind="f_rel")
+            u0 = uniform_field(seed + 1 + k, pb.shape, -0.05, 0.05)
+        else:
+            pb = Problem(nx=side, ny=side, lx=1.0, ly=1.0, bc=bc, op="neg_biharmonic",
+                         kind="ch_split", a=4e-4, b=1.0, dt=1e-5, tau_u=1.0, tau_p=1.0,
+                         tol=tol, tol_kind="f_rel")
+            u0 = zero_mean_uniform(seed + 1 + k, pb.shape, 0.1)
+        out.append((pb, u0, steps))
+    return out
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 5999) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson process of the given rate."""
+    return np.cumsum(rng(seed).exponential(1.0 / rate, size=n))
