@@ -312,7 +312,8 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- chosen form: FP32 sweeps + FP64 defect correction ----
     u = torch.from_numpy(w.u0.copy()).to(dev)
-    tune = dict(band_rows=args.band_rows, col_width=args.col_width, graph_k=args.graph_k)
+    tune = dict(band_rows=args.band_rows, col_width=args.col_width, graph_k=args.graph_k,
+                fft_buffers=args.fft_buffers)
     sv = rd.Solver(pb, precision=args.precision, profile=1, **tune)
     with ClockSampler(local_rank) as clk:
         tot_ms, its, infos = timed_steps(sv, u, args.steps, args.warmup)
@@ -429,7 +430,8 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "iterations_per_step": its / args.steps,
                    "residual_passes_per_step": st["residual_passes"] / args.steps,
-                   "band_rows": args.band_rows, "col_width": args.col_width, "graph_k": args.graph_k},
+                   "band_rows": args.band_rows, "col_width": args.col_width, "graph_k": args.graph_k,
+                   "fft_buffers": args.fft_buffers},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "parity_full_size": parity, "fp64_plain": fp64,
         "serving": serving,
         "gpu_launches": st["kernel_launches"], "clocks": clk.summary(), "source_hash": shash,
@@ -453,7 +455,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--band-rows", type=int, default=0, help="rows per CTA of the band kernels (0 = planner)")
     ap.add_argument("--col-width", type=int, default=0, help="columns per CTA of the column kernel (0 = planner)")
-    ap.add_argument("--graph-k", type=int, default=8, help="PDHG iterations per captured CUDA graph")
+    ap.add_argument("--graph-k", type=int, default=2, help="PDHG iterations per trip of the device-side loop")
+    ap.add_argument("--fft-buffers", type=int, default=0, choices=(0, 1, 2),
+                    help="shared-memory transforms: 0 chosen per kernel, 1 in place, 2 two buffers")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-rates", type=float, nargs="*", default=[0.5, 1.0])

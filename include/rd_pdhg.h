@@ -128,11 +128,15 @@ typedef struct {
     int precision;        /* rd_precision, default RD_PREC_FP64                                 */
     double dc_inner_rtol; /* DC inner tolerance factor, default 1e-4                             */
     int dc_max_outer;     /* DC outer rounds per step, default 12                                */
-    int graph_k;          /* PDHG iterations per captured CUDA graph launch, default 8           */
+    int graph_k;          /* PDHG iterations per trip of the device-side loop (a WHILE node of the
+                             step's CUDA graph), default 2                                      */
     int band_rows;        /* rows per CTA of the stencil sweeps; 0 = autotuned                   */
     int col_width;        /* columns per CTA of the column transform; 0 = autotuned              */
     int profile;          /* 1: time the three PDHG kernels of the first iteration of every graph
                              launch with CUDA events (read back by rd_pdhg_get_stats)            */
+    int fft_buffers;      /* shared-memory transforms: 0 = chosen per kernel (two buffers where the
+                             second costs no resident blocks), 1 = in place in one buffer,
+                             2 = two buffers wherever they fit; default 0                       */
 } rd_opts;
 
 typedef struct {
@@ -166,7 +170,10 @@ RD_API void rd_opts_default(rd_opts *o);
  *   precond may be NULL (= RD_PC_LINEAR); opts may be NULL (= rd_opts_default)
  *   cuda_stream: a cudaStream_t (NULL = legacy default stream); all work is issued on it.
  * Allocates every workspace (about 7 arrays of the grid size plus twiddle tables) and captures
- * the CUDA graph of graph_k PDHG iterations.  On error *out is NULL. */
+ * the step graphs: the PDHG iteration loop runs on the device as a WHILE node of a CUDA graph
+ * (graph_k iterations per trip) that the kernels end themselves, so that an FP64 step is one
+ * graph launch and a defect-correction step one launch per outer round.  Needs a GPU and driver
+ * with CUDA-graph conditional nodes.  On error *out is NULL. */
 RD_API rd_status rd_pdhg_create(rd_pdhg **out, const rd_grid *grid, rd_bc bc, rd_operator op,
                          const rd_reaction *reaction, double dt, double tau, double sigma,
                          const rd_precond *precond, const rd_opts *opts, void *cuda_stream);

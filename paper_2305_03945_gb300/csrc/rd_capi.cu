@@ -59,15 +59,32 @@ int band_threads(int nlines, int nx) {
   return t;
 }
 
+// Resident blocks per SM of a sweep kernel with `threads` threads and `smem` bytes of dynamic
+// shared memory: registers per thread as fixed by the kernels' launch bounds, 64 K registers,
+// 2048 threads, 228 KB of shared memory (1 KB reserved per block) and 32 blocks per SM.
 template <class T>
-int smem_lines(int nlines, int n) {
-  return nlines * padded_len(n) * (int)sizeof(cx<T>);
+int blocks_per_sm(int threads, int smem) {
+  const int regs = std::min(255, (65536 / (MaxThreads<T>::value * MinBlocks<T>::value)) & ~7);
+  const int warps = (threads + 31) / 32;
+  const int by_regs = 65536 / (warps * ((regs * 32 + 255) / 256 * 256));
+  const int by_thr = 2048 / (warps * 32);
+  const int by_smem = (228 * 1024) / (smem + 1024);
+  return std::max(0, std::min(std::min(by_regs, by_thr), std::min(by_smem, 32)));
+}
+
+// Transforms ping-pong between two buffers (one barrier per pass instead of two) when the
+// second buffer fits and costs no resident blocks.
+// fft_buffers: 0 = that rule, 1 = never, 2 = whenever the second buffer fits.
+template <class T>
+bool use_pingpong(int fft_buffers, int threads, int smem_inplace, int smem_pp) {
+  if (fft_buffers == 1 || smem_pp > kSmemLimit) return false;
+  return fft_buffers == 2 || blocks_per_sm<T>(threads, smem_pp) >= blocks_per_sm<T>(threads, smem_inplace);
 }
 
 // Launch shape for one precision.  Returns false when the grid does not fit.
 template <class T>
-bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int col_req, int dc, Desc& d,
-                 LaunchCfg& c, std::string& why) {
+bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int col_req, int dc, int fft_buffers,
+                 Desc& d, LaunchCfg& c, std::string& why) {
   if (fft_line_threads<T>(nx) > MaxThreads<T>::value || fft_line_threads<T>(ny) > MaxThreads<T>::value) {
     why = "grid side too long for this precision";
     return false;
@@ -83,7 +100,8 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     for (int cand = 16; cand >= 2; cand /= 2) {
       if (cand > ny) continue;
       const int nb = (ny + cand - 1) / cand;
-      const int sm = std::max(lines_smem_bytes<T>(nc * ((cand + 2 * H) / 2), nx), res_smem_bytes<T>(nc, cand, H, nx, dc));
+      const int sm =
+          std::max(lines_smem_bytes<T>(nc * ((cand + 2 * H) / 2), nx, 0), res_smem_bytes<T>(nc, cand, H, nx, dc, 0));
       if (sm > kSmemLimit) continue;
       if (nb >= kTargetBlocks || cand == 2) {
         B = cand;
@@ -92,8 +110,8 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     }
     if (B == 0) B = 2;
   }
-  const int smem_res = res_smem_bytes<T>(nc, B, H, nx, dc);
-  const int smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx);
+  int smem_res = res_smem_bytes<T>(nc, B, H, nx, dc, 0);
+  int smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 0);
   if (smem_upd > kSmemLimit || smem_res > kSmemLimit) {
     why = "row band does not fit in shared memory";
     return false;
@@ -110,12 +128,12 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     C = cmin;
     for (int cand = cmin * 2; cand <= nx; cand *= 2) {
       if (nc * (nx / cand) < 2 * kTargetBlocks) break;
-      if (lines_smem_bytes<T>(cand / 2, ny) > kSmemLimit / 2) break;
+      if (lines_smem_bytes<T>(cand / 2, ny, 0) > kSmemLimit / 2) break;
 
       C = cand;
     }
   }
-  const int smem_col = lines_smem_bytes<T>(C / 2, ny);
+  int smem_col = lines_smem_bytes<T>(C / 2, ny, 0);
   if (smem_col > kSmemLimit) {
     why = "column block does not fit in shared memory";
     return false;
@@ -129,6 +147,19 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
   c.thr_res = band_threads<T>(nc * (B / 2), nx);
   c.thr_upd = band_threads<T>(nc * ((B + 2 * H) / 2), nx);
   c.thr_col = band_threads<T>(C / 2, ny);
+  d.fft_pp = 0;
+  if (use_pingpong<T>(fft_buffers, c.thr_res, smem_res, res_smem_bytes<T>(nc, B, H, nx, dc, 1))) {
+    d.fft_pp |= 1;
+    smem_res = res_smem_bytes<T>(nc, B, H, nx, dc, 1);
+  }
+  if (use_pingpong<T>(fft_buffers, c.thr_col, smem_col, lines_smem_bytes<T>(C / 2, ny, 1))) {
+    d.fft_pp |= 2;
+    smem_col = lines_smem_bytes<T>(C / 2, ny, 1);
+  }
+  if (use_pingpong<T>(fft_buffers, c.thr_upd, smem_upd, lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 1))) {
+    d.fft_pp |= 4;
+    smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 1);
+  }
   c.smem_res = smem_res;
   c.smem_upd = smem_upd;
   c.smem_col = smem_col;
@@ -149,6 +180,7 @@ struct rd_pdhg {
   rd_opts opts{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t body_stream = nullptr;  // captures the body of the device-side loop
   int dc = 0;
   // FP64 state and plain-path workspaces
   double* U64 = nullptr;
@@ -171,10 +203,12 @@ struct rd_pdhg {
   State* h_state = nullptr; // pinned mirror
   Desc h_desc[3]{};
   LaunchCfg cfg64{}, cfg32{}, cfgpc{};
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  // Step graphs.  FP64: [0] the whole step.  Defect correction: [0] the first outer round of a
+  // step (with the step set-up), [1] every later round.
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // around the first iteration's kernels
-  int kernels_per_graph = 0;
+  int kernels_per_iter = 0;
   rd_stats stats{};
   std::vector<void*> allocs;
 };
@@ -257,27 +291,103 @@ rd_status status_of(int st) {
   }
 }
 
-rd_status capture_graph(rd_pdhg* h) {
+// Capture one step graph.  Layout (FP64 plain, first = true):
+//   k_begin, P_0 = 0, iteration 1, WHILE { graph_k iterations }, k_mass
+// and for defect correction (first adds k_begin and the first FP64 residual in front):
+//   [k_begin, k_resid64], iteration 1, WHILE { graph_k iterations }, k_axpy_dc, k_resid64, k_mass
+// Iteration 1 sits outside the loop so that the profiling events (which a conditional body
+// cannot hold) bracket its three kernels.  The loop's condition starts at 1 on every launch;
+// k_res clears it when the solve is not active (or after max_iter + slack launches), and the
+// last block of k_res clears it when the stopping rule ends the solve.  k_axpy_dc, the second
+// k_resid64 and k_mass act only while (resp. once no longer) the outer loop is active.
+rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraphExec_t* exec) {
   const int K = h->opts.graph_k;
+  cudaStream_t cs = h->cap_stream;
+  const int nb = point_blocks(h->nx, h->ny);
+  const Desc* d64 = h->d_desc + 0;
+  State* st0 = h->d_state + 0;
+  State* st1 = h->d_state + 1;
+  State* sti = h->dc ? st1 : st0;
+  cudaGraph_t g = nullptr;
+  RD_CUDA(cudaGraphCreate(&g, 0));
+  *out = g;
+  cudaGraphConditionalHandle cond = 0;
+  RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  Desc dd = h->dc ? h->h_desc[1] : h->h_desc[0];
+  dd.cond = cond;
+  auto iteration = [&](cudaStream_t st, cudaEvent_t* ev) {
+    return h->dc ? launch_iteration<float>(dd, sti, h->cfg32, st, ev) : launch_iteration<double>(dd, sti, h->cfg64, st, ev);
+  };
+  auto abort_capture = [&](cudaStream_t st, const char* what, cudaError_t e) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(st, &tmp);
+    if (tmp && tmp != g) cudaGraphDestroy(tmp);
+    return fail(RD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  RD_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  if (first) {
+    e = launch_begin(d64, st0, h->U64, h->rhs64, h->opts.tol, h->opts.tol_kind, nb, cs);
+    if (e == cudaSuccess && !h->dc) e = cudaMemsetAsync(h->P64[0], 0, h->npts * sizeof(double), cs);
+    if (e == cudaSuccess && h->dc)
+      e = launch_resid64(h->h_desc[0], d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1,
+                         h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, cs);
+    if (e != cudaSuccess) return abort_capture(cs, "step set-up during capture", e);
+  }
+  if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr)) != cudaSuccess)
+    return abort_capture(cs, "kernel launch during capture", e);
+  // the WHILE node, appended to the capture after the first iteration
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps)) != cudaSuccess)
+    return abort_capture(cs, "cudaStreamGetCaptureInfo", e);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wn = nullptr;
+  if ((e = cudaGraphAddNode(&wn, cg, deps, nullptr, ndeps, &cp)) != cudaSuccess)
+    return abort_capture(cs, "adding the loop node", e);
+  if ((e = cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return abort_capture(cs, "cudaStreamUpdateCaptureDependencies", e);
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return abort_capture(cs, "capturing the loop body", e);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) e = iteration(h->body_stream, nullptr);
+  if (e != cudaSuccess) {
+    abort_capture(h->body_stream, "loop body", e);
+    return abort_capture(cs, "kernel launch during capture", e);
+  }
+  cudaGraph_t body_out = nullptr;
+  if ((e = cudaStreamEndCapture(h->body_stream, &body_out)) != cudaSuccess)
+    return abort_capture(cs, "ending the loop body capture", e);
+  if (h->dc) {
+    e = launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, cs);
+    if (e == cudaSuccess)
+      e = launch_resid64(h->h_desc[0], d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1,
+                         h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, cs);
+    if (e == cudaSuccess) e = launch_mass(d64, h->d_state + 2, h->U64, st0, nb, cs);
+  } else {
+    e = launch_mass(d64, h->d_state + 2, h->U64, nullptr, nb, cs);
+  }
+  if (e != cudaSuccess) return abort_capture(cs, "kernel launch during capture", e);
+  cudaGraph_t g_out = nullptr;
+  RD_CUDA(cudaStreamEndCapture(cs, &g_out));
+  RD_CUDA(cudaGraphInstantiate(exec, g, 0));
+  return RD_OK;
+}
+
+rd_status capture_graphs(rd_pdhg* h) {
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
-  h->kernels_per_graph = K * (lc.transform ? 3 : 2);
+  h->kernels_per_iter = lc.transform ? 3 : 2;
   if (h->opts.profile)
     for (int i = 0; i < 4; ++i) RD_CUDA(cudaEventCreate(&h->ev[i]));
-  RD_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < K; ++k) {
-    cudaError_t e;
-    cudaEvent_t* ev = (k == 0 && h->opts.profile) ? h->ev : nullptr;
-    e = h->dc ? launch_iteration<float>(h->h_desc[1], h->d_state + 1, h->cfg32, h->cap_stream, ev)
-              : launch_iteration<double>(h->h_desc[0], h->d_state + 0, h->cfg64, h->cap_stream, ev);
-    if (e != cudaSuccess) {
-      cudaGraph_t g = nullptr;
-      cudaStreamEndCapture(h->cap_stream, &g);
-      if (g) cudaGraphDestroy(g);
-      return fail(RD_ERR_CUDA, std::string("kernel launch during capture: ") + cudaGetErrorString(e));
-    }
-  }
-  RD_CUDA(cudaStreamEndCapture(h->cap_stream, &h->graph));
-  RD_CUDA(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+  RD_TRY(capture_step_graph(h, true, &h->graph[0], &h->gexec[0]));
+  if (h->dc) RD_TRY(capture_step_graph(h, false, &h->graph[1], &h->gexec[1]));
   return RD_OK;
 }
 
@@ -314,6 +424,7 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
     if (!(o->omega >= 0) || !std::isfinite(o->omega)) return fail(RD_ERR_INVALID_ARG, "omega must be >= 0");
     if (o->precision != RD_PREC_FP64 && o->precision != RD_PREC_FP32_DC) return fail(RD_ERR_INVALID_ARG, "bad precision");
     if (o->graph_k < 1 || o->graph_k > 256) return fail(RD_ERR_INVALID_ARG, "graph_k must be in [1, 256]");
+    if (o->fft_buffers < 0 || o->fft_buffers > 2) return fail(RD_ERR_INVALID_ARG, "fft_buffers must be 0, 1 or 2");
     if (o->precision == RD_PREC_FP32_DC && (!(o->dc_inner_rtol > 0) || o->dc_max_outer < 1))
       return fail(RD_ERR_INVALID_ARG, "bad defect-correction options");
   }
@@ -340,6 +451,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   h->dc = h->opts.precision == RD_PREC_FP32_DC;
   h->stream = static_cast<cudaStream_t>(stream);
   RD_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  RD_CUDA(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
 
   const int H = op == RD_OP_NEG_BIHARMONIC ? 2 : 1;
   const int transform = h->precond != RD_PC_NONE;
@@ -366,11 +478,11 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
 
   std::string why;
   Desc d64 = base, d32 = base;
-  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 0, d64, h->cfg64, why))
+  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 0, h->opts.fft_buffers, d64, h->cfg64, why))
     if (!h->dc) return fail(RD_ERR_UNSUPPORTED, "FP64 path: " + why);
   if (h->dc) {
     // the FP64 kernels of the defect-correction loop only need the band decomposition
-    if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 1, d32, h->cfg32, why))
+    if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 1, h->opts.fft_buffers, d32, h->cfg32, why))
       return fail(RD_ERR_UNSUPPORTED, "FP32 path: " + why);
     d64.band_rows = d32.band_rows;
     d64.nbands = d32.nbands;
@@ -382,7 +494,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   RD_TRY(dalloc(h, &h->U64, n * sizeof(double)));
   RD_TRY(dalloc(h, &h->rhs64, n * sizeof(double)));
   const int nb = std::max(d64.nbands, d32.nbands);
-  RD_TRY(dalloc(h, &h->partials, (size_t)2 * std::max(nb, 1) * sizeof(double)));
+  RD_TRY(dalloc(h, &h->partials, (size_t)2 * std::max(std::max(nb, point_blocks(h->nx, h->ny)), 1) * sizeof(double)));
   RD_TRY(dalloc(h, &h->d_desc, 3 * sizeof(Desc)));
   RD_TRY(dalloc(h, &h->d_state, 3 * sizeof(State)));
   RD_CUDA(cudaMallocHost(&h->h_state, 3 * sizeof(State)));
@@ -495,28 +607,48 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
   if (std::max(lc.smem_res, std::max(lc.smem_col, lc.smem_upd)) > usable)
     return fail(RD_ERR_UNSUPPORTED, "the grid needs more shared memory per block than this device offers");
-  RD_TRY(capture_graph(h));
+  RD_TRY(capture_graphs(h));
   RD_CUDA(cudaDeviceSynchronize());
   return RD_OK;
 }
 
-// Launch the K-iteration graph, read the solve state `which` back and account the launch.
+// Launch step graph `which`, read the three solve states back and account the launch.
 rd_status graph_round(rd_pdhg* h, int which) {
   cudaStream_t s = h->stream;
-  const int n_before = h->h_state[which].n;
-  RD_CUDA(cudaGraphLaunch(h->gexec, s));
-  RD_CUDA(cudaMemcpyAsync(h->h_state + which, h->d_state + which, sizeof(State), cudaMemcpyDeviceToHost, s));
+  // graph 0 starts the step (k_begin resets the counters); graph 1 continues it
+  const bool cont = h->dc && which == 1;
+  const int upd_before = cont ? h->h_state[0].total : 0;
+  const int launches_before = cont ? h->h_state[0].launches : 0;
+  const int outer_before = cont ? h->h_state[0].n : 0;
+  RD_CUDA(cudaGraphLaunch(h->gexec[which], s));
+  RD_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, 3 * sizeof(State), cudaMemcpyDeviceToHost, s));
   RD_CUDA(cudaStreamSynchronize(s));
+  const State& o = h->h_state[0];
   h->stats.graph_launches += 1;
-  h->stats.kernel_launches += h->kernels_per_graph;
   h->stats.host_syncs += 1;
-  h->stats.pdhg_iterations += h->h_state[which].n - n_before;
-  if (h->opts.profile) {
+  int updates, sweeps;
+  if (h->dc) {
+    updates = o.total - upd_before;
+    sweeps = o.launches - launches_before;
+    const int passes = o.n - outer_before;
+    h->stats.residual_passes += passes;
+    // the second k_resid64 and k_axpy_dc are captured in every round graph; k_begin and the
+    // first k_resid64 in the first; k_mass in both
+    h->stats.kernel_launches += (which == 0 ? 2 : 0) + 3;
+  } else {
+    updates = o.n;
+    sweeps = (int)o.trips;
+    h->stats.kernel_launches += 2;  // k_begin, k_mass (the P_0 clear is a memset node)
+  }
+  h->stats.pdhg_iterations += updates;
+  // every k_res launch (active or not) is followed by k_col and k_upd in the graph
+  h->stats.kernel_launches += (long long)sweeps * h->kernels_per_iter;
+  if (h->opts.profile && sweeps > 0) {
     float ms = 0.f;
     RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
     h->stats.kernel_ms[0] += ms;
     h->stats.kernel_samples[0] += 1;
-    if (h->h_state[which].n > n_before) {  // the first iteration updated: k_col and k_upd ran
+    if (updates > 0) {  // the first iteration updated: k_col and k_upd ran
       const int tr = (h->dc ? h->cfg32 : h->cfg64).transform;
       if (tr) {
         RD_CUDA(cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]));
@@ -531,70 +663,27 @@ rd_status graph_round(rd_pdhg* h, int which) {
   return RD_OK;
 }
 
-// One implicit step on the handle's FP64 iterate U64 (already holding U^k); rhs from uk.
-rd_status step_impl(rd_pdhg* h, const double* uk, rd_step_info* info) {
-  cudaStream_t s = h->stream;
-  const Desc* d64 = h->d_desc + 0;
-  State* st0 = h->d_state + 0;
-  State* st1 = h->d_state + 1;
-  const int K = h->opts.graph_k;
-  const int nb = h->h_desc[0].nbands;
+// One implicit step on the handle's FP64 iterate U64 (holding U^k).  FP64: one graph launch
+// runs the whole step.  Defect correction: one graph launch per outer round; the host only
+// reads the outer state between rounds.
+rd_status step_impl(rd_pdhg* h, rd_step_info* info) {
   rd_step_info inf{};
-  int final_status = ST_NOT_CONVERGED;
-  RD_CUDA(launch_begin(d64, st0, uk, h->rhs64, h->opts.tol, h->opts.tol_kind, nb, s));
-  h->h_state[0].n = 0;
-  h->h_state[1].n = 0;
+  int final_status;
+  RD_TRY(graph_round(h, 0));
   if (!h->dc) {
-    RD_CUDA(cudaMemsetAsync(h->P64[0], 0, h->npts * sizeof(double), s));
-    h->stats.kernel_launches += 1;
-    h->h_state[0].n = 0;
-    const int max_launch = h->opts.max_iter / K + 2;
-    for (int it = 0; it <= max_launch; ++it) {
-      RD_TRY(graph_round(h, 0));
-      if (h->h_state[0].status != ST_ACTIVE) break;
-    }
     final_status = h->h_state[0].status;
     inf.iterations = h->h_state[0].n;
     inf.residual = h->h_state[0].r;
     if (final_status == ST_ACTIVE) return fail(RD_ERR_TIMEOUT, "PDHG loop exceeded its launch bound");
   } else {
-    int inner_total = 0;
-    final_status = ST_NOT_CONVERGED;
-    for (int outer = 0; outer <= h->opts.dc_max_outer; ++outer) {
-      RD_CUDA(launch_resid64(h->h_desc[0], d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, h->D32,
-                             h->P32[0], 1, h->opts.dc_inner_rtol, nb, s));
-      RD_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, 2 * sizeof(State), cudaMemcpyDeviceToHost, s));
-      RD_CUDA(cudaStreamSynchronize(s));
-      h->stats.kernel_launches += 1;
-      h->stats.residual_passes += 1;
-      h->stats.host_syncs += 1;
-      if (h->h_state[0].status != ST_ACTIVE) {
-        final_status = h->h_state[0].status;
-        break;
-      }
-      if (outer == h->opts.dc_max_outer) break;
-      const int max_launch = h->opts.max_iter / K + 2;
-      for (int it = 0; it <= max_launch; ++it) {
-        RD_TRY(graph_round(h, 1));
-        if (h->h_state[1].status != ST_ACTIVE) break;
-      }
-      inner_total += h->h_state[1].n;
-      if (h->h_state[1].status == ST_DIVERGED || h->h_state[1].status == ST_ACTIVE) {
-        final_status = ST_DIVERGED;
-        break;
-      }
-      RD_CUDA(launch_axpy_dc(h->U64, h->D32, h->npts, s));
-      h->stats.kernel_launches += 1;
-    }
-    inf.iterations = inner_total;
+    for (int round = 1; h->h_state[0].status == ST_ACTIVE && round <= h->opts.dc_max_outer + 1; ++round)
+      RD_TRY(graph_round(h, 1));
+    final_status = h->h_state[0].status;
+    if (final_status == ST_ACTIVE) return fail(RD_ERR_TIMEOUT, "defect-correction loop exceeded its round bound");
+    inf.iterations = h->h_state[0].total;
     inf.outer_rounds = h->h_state[0].n;
     inf.residual = h->h_state[0].r;
   }
-  RD_CUDA(launch_mass(d64, h->d_state + 2, h->U64, nb, s));
-  h->stats.kernel_launches += 2;  // begin + mass
-  h->stats.host_syncs += 1;
-  RD_CUDA(cudaMemcpyAsync(h->h_state + 2, h->d_state + 2, sizeof(State), cudaMemcpyDeviceToHost, s));
-  RD_CUDA(cudaStreamSynchronize(s));
   inf.mass = h->h_state[2].mass;
   inf.converged = final_status == ST_CONVERGED;
   inf.status = status_of(final_status);
@@ -617,10 +706,11 @@ void rd_opts_default(rd_opts* o) {
   o->precision = RD_PREC_FP64;
   o->dc_inner_rtol = 1e-4;
   o->dc_max_outer = 12;
-  o->graph_k = 8;
+  o->graph_k = 2;
   o->band_rows = 0;
   o->col_width = 0;
   o->profile = 0;
+  o->fft_buffers = 0;
 }
 
 rd_status rd_pdhg_create(rd_pdhg** out, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* reaction,
@@ -648,7 +738,7 @@ rd_status rd_pdhg_step(rd_pdhg* h, const double* u_n, double* u_np1, rd_step_inf
   if (!h || !u_n || !u_np1) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
   const size_t bytes = h->npts * sizeof(double);
   RD_CUDA(cudaMemcpyAsync(h->U64, u_n, bytes, cudaMemcpyDeviceToDevice, h->stream));
-  rd_status s = step_impl(h, h->U64, info);
+  rd_status s = step_impl(h, info);
   if (s == RD_OK || s == RD_ERR_NOT_CONVERGED || s == RD_ERR_DIVERGED) {
     std::string keep = g_last_error;
     RD_CUDA(cudaMemcpyAsync(u_np1, h->U64, bytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -662,7 +752,7 @@ namespace {
 // Algorithm 1's time loop on the handle's iterate U64.
 rd_status solve_u64(rd_pdhg* h, int nsteps, rd_step_info* per_step) {
   for (int k = 0; k < nsteps; ++k) {
-    rd_status s = step_impl(h, h->U64, per_step ? per_step + k : nullptr);
+    rd_status s = step_impl(h, per_step ? per_step + k : nullptr);
     if (s != RD_OK) return s;
   }
   return RD_OK;
@@ -699,10 +789,10 @@ rd_status rd_pdhg_solve_host(rd_pdhg* h, double* u_host, int nsteps, rd_step_inf
 
 rd_status rd_pdhg_residual(rd_pdhg* h, const double* u, const double* u_k, double* w) {
   if (!h || !u || !u_k || !w) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
-  const int nb = h->h_desc[0].nbands;
+  const int nb = point_blocks(h->nx, h->ny);
   RD_CUDA(launch_begin(h->d_desc + 0, h->d_state + 2, u_k, h->rhs64, 0.0, 0, nb, h->stream));
   RD_CUDA(launch_resid64(h->h_desc[0], h->d_desc + 0, h->d_state + 2, h->d_state + 2, u, h->rhs64, w, nullptr,
-                         nullptr, nullptr, nullptr, 0, 0.0, nb, h->stream));
+                         nullptr, nullptr, nullptr, 0, 0.0, 0, nb, h->stream));
   RD_CUDA(cudaStreamSynchronize(h->stream));
   return RD_OK;
 }
@@ -735,11 +825,14 @@ void rd_pdhg_destroy(rd_pdhg* h) {
   for (int i = 0; i < 4; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  if (h->graph) cudaGraphDestroy(h->graph);
+  for (int k = 0; k < 2; ++k) {
+    if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+    if (h->graph[k]) cudaGraphDestroy(h->graph[k]);
+  }
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->body_stream) cudaStreamDestroy(h->body_stream);
   delete h;
 }
 

@@ -136,12 +136,12 @@ __device__ __forceinline__ void job_twiddles(const cx<T>* __restrict__ tw, int s
   }
 }
 
-// One in-place Stockham pass of radix R (Govindaraju et al., SC 2008 formulation): job j of a
-// line reads entries j + r N/R, twiddles them by w^{r (j mod Ns) N/(Ns R)}, applies the radix-R
-// DFT and writes entries (j div Ns) Ns R + (j mod Ns) + r Ns.  All reads happen before the
-// barrier and all writes after it, so one buffer suffices.  Sizes enter as base-2 logarithms.
+// One Stockham pass of radix R (Govindaraju et al., SC 2008 formulation): job j of a line reads
+// entries j + r N/R of src, twiddles them by w^{r (j mod Ns) N/(Ns R)}, applies the radix-R DFT
+// and writes entries (j div Ns) Ns R + (j mod Ns) + r Ns of dst.  With src == dst all reads
+// happen before a barrier and all writes after it.  Sizes enter as base-2 logarithms.
 template <class T, int R, int DIR>
-__device__ __forceinline__ void stockham_pass(cx<T>* buf, int nlines, int logN, int ls, int logNs,
+__device__ __forceinline__ void stockham_pass(const cx<T>* src, cx<T>* dst, int nlines, int logN, int ls, int logNs,
                                               const cx<T>* __restrict__ tw, int tid) {
   constexpr int RM = FftRadix<T>::value;
   constexpr int S = RM / R;
@@ -157,13 +157,13 @@ __device__ __forceinline__ void stockham_pass(cx<T>* buf, int nlines, int logN, 
   for (int s = 0; s < S; ++s) {
     const int g = tid + s * nthr;
     if (tid < nthr && g < total) {
-      const cx<T>* L = buf + (g >> lj) * ls;
+      const cx<T>* L = src + (g >> lj) * ls;
       const int j = g & (jpl - 1);
 #pragma unroll
       for (int r = 0; r < R; ++r) v[s][r] = L[pidx(j + (r << lj))];
     }
   }
-  __syncthreads();
+  if (src == dst) __syncthreads();
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int g = tid + s * nthr;
@@ -177,7 +177,7 @@ __device__ __forceinline__ void stockham_pass(cx<T>* buf, int nlines, int logN, 
         for (int r = 1; r < R; ++r) v[s][r] = cmul_tw<T, DIR>(v[s][r], w[r]);
       }
       dft_reg<T, R, DIR>(v[s]);
-      cx<T>* L = buf + (g >> lj) * ls;
+      cx<T>* L = dst + (g >> lj) * ls;
       const int d = ((j - k) << LR) + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) L[pidx(d + (r << logNs))] = v[s][r];
@@ -186,30 +186,148 @@ __device__ __forceinline__ void stockham_pass(cx<T>* buf, int nlines, int logN, 
   __syncthreads();
 }
 
+// Stockham pass with every size known at compile time.  With the padding pidx(i) = i + i/16,
+// element r of a job sits at a constant offset from element 0 whenever the stride between the
+// elements is a multiple of 16 (or the job's elements are contiguous), so the index arithmetic
+// folds into immediate offsets.
+template <class T, int R, int DIR, int LOGN, int LOGNS>
+__device__ __forceinline__ void stockham_pass_c(const cx<T>* src, cx<T>* dst, int nlines, int ls,
+                                                const cx<T>* __restrict__ tw, int tid) {
+  constexpr int RM = FftRadix<T>::value;
+  constexpr int S = RM / R;
+  constexpr int LR = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4));
+  constexpr int LJ = LOGN - LR;
+  constexpr int JPL = 1 << LJ;
+  constexpr int NS = 1 << LOGNS;
+  constexpr int TWS = LOGN - LOGNS - LR;
+  constexpr bool LD_CONST = (JPL % 16) == 0;
+  constexpr int LD_STRIDE = JPL + JPL / 16;
+  constexpr bool ST_CONST = NS == 1 || (NS % 16) == 0;
+  constexpr int ST_STRIDE = NS == 1 ? 1 : NS + NS / 16;
+  const int total = nlines << LJ;
+  const int nthr = (total + S - 1) / S;
+  cx<T> v[S][R];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int g = tid + s * nthr;
+    if (tid < nthr && g < total) {
+      const cx<T>* L = src + (g >> LJ) * ls;
+      const int j = g & (JPL - 1);
+      if constexpr (LD_CONST) {
+        const cx<T>* p = L + pidx(j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[s][r] = p[r * LD_STRIDE];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[s][r] = L[pidx(j + (r << LJ))];
+      }
+    }
+  }
+  if (src == dst) __syncthreads();
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int g = tid + s * nthr;
+    if (tid < nthr && g < total) {
+      const int j = g & (JPL - 1);
+      const int k = j & (NS - 1);
+      if (NS > 1 && k != 0) {
+        cx<T> w[R];
+        job_twiddles<T, R>(tw, k << TWS, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[s][r] = cmul_tw<T, DIR>(v[s][r], w[r]);
+      }
+      dft_reg<T, R, DIR>(v[s]);
+      cx<T>* L = dst + (g >> LJ) * ls;
+      const int d = ((j - k) << LR) + k;
+      if constexpr (ST_CONST) {
+        cx<T>* p = L + pidx(d);
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r * ST_STRIDE] = v[s][r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) L[pidx(d + (r << LOGNS))] = v[s][r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Radix plan of a length-2^LOGN transform: passes of radix 8 from Ns = 1, the remainder last.
+// Each pass reads `a` and writes `b` (the same buffer when b == a); returns the buffer holding
+// the result.
+template <class T, int DIR, int LOGN, int LOGNS>
+__device__ __forceinline__ cx<T>* fft_passes_c(cx<T>* a, cx<T>* b, int nlines, int ls, const cx<T>* __restrict__ tw,
+                                               int tid) {
+  constexpr int RM = FftRadix<T>::value;
+  constexpr int LRM = RM == 8 ? 3 : 4;
+  constexpr int REM = LOGN - LOGNS;
+  if constexpr (REM > 0) {
+    constexpr int B = REM >= LRM ? LRM : REM;
+    constexpr int R = 1 << B;
+    stockham_pass_c<T, R, DIR, LOGN, LOGNS>(a, b, nlines, ls, tw, tid);
+    return fft_passes_c<T, DIR, LOGN, LOGNS + B>(b, a, nlines, ls, tw, tid);
+  } else {
+    return a;
+  }
+}
+
+template <class T, int DIR, int LOGN>
+__device__ __forceinline__ cx<T>* block_fft_c(cx<T>* buf, cx<T>* scr, int nlines, int ls,
+                                              const cx<T>* __restrict__ tw, int tid, int nthreads) {
+  constexpr int RM = FftRadix<T>::value;
+  int chunk = (nthreads * RM) >> LOGN;
+  if (chunk < 1) chunk = 1;
+  cx<T>* res = buf;
+  for (int l0 = 0; l0 < nlines; l0 += chunk) {
+    const int nl = nlines - l0 < chunk ? nlines - l0 : chunk;
+    res = fft_passes_c<T, DIR, LOGN, 0>(buf + l0 * ls, scr + l0 * ls, nl, ls, tw, tid) - l0 * ls;
+  }
+  return res;
+}
+
 // Unnormalised complex DFT of `nlines` padded lines in shared memory (DIR = -1 forward,
-// +1 inverse), in chunks of as many lines as `nthreads` threads can hold.  Called by every
-// thread of the block (it contains barriers); needs nthreads >= fft_line_threads<T>(N).
+// +1 inverse), in chunks of as many lines as `nthreads` threads can hold, ping-ponging between
+// buf and scr (one barrier per pass), or in place when scr == buf (two barriers per pass, half
+// the shared memory).  Returns the buffer (buf or scr) that holds the result.
+// Called by every thread of the block (it contains barriers); needs nthreads >=
+// fft_line_threads<T>(N).  Lengths 64 .. 2048 run the compile-time specialised passes.
 template <class T, int DIR>
-__device__ void block_fft(cx<T>* buf, int nlines, int logN, int ls, const cx<T>* __restrict__ tw,
-                          int tid, int nthreads) {
+__device__ cx<T>* block_fft(cx<T>* buf, cx<T>* scr, int nlines, int logN, int ls, const cx<T>* __restrict__ tw,
+                            int tid, int nthreads) {
+  switch (logN) {
+    case 6: return block_fft_c<T, DIR, 6>(buf, scr, nlines, ls, tw, tid, nthreads);
+    case 7: return block_fft_c<T, DIR, 7>(buf, scr, nlines, ls, tw, tid, nthreads);
+    case 8: return block_fft_c<T, DIR, 8>(buf, scr, nlines, ls, tw, tid, nthreads);
+    case 9: return block_fft_c<T, DIR, 9>(buf, scr, nlines, ls, tw, tid, nthreads);
+    case 10: return block_fft_c<T, DIR, 10>(buf, scr, nlines, ls, tw, tid, nthreads);
+    case 11: return block_fft_c<T, DIR, 11>(buf, scr, nlines, ls, tw, tid, nthreads);
+    default: break;
+  }
   constexpr int RM = FftRadix<T>::value;
   constexpr int LRM = RM == 8 ? 3 : 4;
   int chunk = (nthreads * RM) >> logN;
   if (chunk < 1) chunk = 1;
+  cx<T>* res = buf;
   for (int l0 = 0; l0 < nlines; l0 += chunk) {
     const int nl = nlines - l0 < chunk ? nlines - l0 : chunk;
-    cx<T>* b0 = buf + l0 * ls;
+    cx<T>* a = buf + l0 * ls;
+    cx<T>* b = scr + l0 * ls;
     int logNs = 0, rem = logN;
     while (rem > 0) {
-      const int b = rem >= LRM ? LRM : rem;
-      if (b == 4) stockham_pass<T, (RM >= 16 ? 16 : RM), DIR>(b0, nl, logN, ls, logNs, tw, tid);
-      else if (b == 3) stockham_pass<T, 8, DIR>(b0, nl, logN, ls, logNs, tw, tid);
-      else if (b == 2) stockham_pass<T, 4, DIR>(b0, nl, logN, ls, logNs, tw, tid);
-      else stockham_pass<T, 2, DIR>(b0, nl, logN, ls, logNs, tw, tid);
-      logNs += b;
-      rem -= b;
+      const int bb = rem >= LRM ? LRM : rem;
+      if (bb == 4) stockham_pass<T, (RM >= 16 ? 16 : RM), DIR>(a, b, nl, logN, ls, logNs, tw, tid);
+      else if (bb == 3) stockham_pass<T, 8, DIR>(a, b, nl, logN, ls, logNs, tw, tid);
+      else if (bb == 2) stockham_pass<T, 4, DIR>(a, b, nl, logN, ls, logNs, tw, tid);
+      else stockham_pass<T, 2, DIR>(a, b, nl, logN, ls, logNs, tw, tid);
+      cx<T>* t = a;
+      a = b;
+      b = t;
+      logNs += bb;
+      rem -= bb;
     }
+    res = a - l0 * ls;
   }
+  return res;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -323,10 +441,10 @@ __device__ __forceinline__ T lap13(const F& f, int i, int j, T c, T hx2, T hy2) 
 template <class T> struct SmemTables { static constexpr bool value = sizeof(T) == 4; };
 
 template <class T>
-__host__ __device__ inline int res_smem_bytes(int nc, int rows, int H, int nx, int dc) {
+__host__ __device__ inline int res_smem_bytes(int nc, int rows, int H, int nx, int dc, int pp) {
   const int ls = padded_len(nx);
   const int tabs = SmemTables<T>::value ? 2 * nx * (int)sizeof(cx<T>) : 0;
-  const int buf = nc * (rows >> 1) * ls * (int)sizeof(cx<T>);
+  const int buf = nc * (rows >> 1) * ls * (int)sizeof(cx<T>) * (pp ? 2 : 1);
   const int stg = nc * (rows + 2 * H) * nx * (int)sizeof(T);
   return tabs + buf + stg * (dc ? 2 : 1);
 }
@@ -334,8 +452,9 @@ __host__ __device__ inline int res_smem_bytes(int nc, int rows, int H, int nx, i
 // Shared-memory bytes of a kernel holding `nlines` transform lines of length n plus the
 // twiddle and DCT rotation tables of that length.
 template <class T>
-__host__ __device__ inline int lines_smem_bytes(int nlines, int n) {
-  return ((SmemTables<T>::value ? 2 * n : 0) + nlines * padded_len(n)) * (int)sizeof(cx<T>);
+__host__ __device__ inline int lines_smem_bytes(int nlines, int n, int pp) {
+  return ((SmemTables<T>::value ? 2 * n : 0) + nlines * padded_len(n) * (pp ? 2 : 1)) *
+         (int)sizeof(cx<T>);
 }
 
 // Copy n entries of a complex table from global to shared memory (called by the whole block).

@@ -38,7 +38,7 @@ struct Desc {
   int meas_div_dt;   // 1: stopping measure is sum ||F_c|| / dt, else sum ||F_c||
   int stall_window;  // > 0: stop (as converged) when the measure has not halved for this many updates
   int batched;       // 1: member of a batch (Slot control block, device-side phase machine)
-  int pad_b;
+  int fft_pp;        // bit 0 k_res, bit 1 k_col, bit 2 k_upd: transforms ping-pong between two buffers
   double hx2, hy2;   // 1/h_x^2, 1/h_y^2
   double dt, a, b;
   double p[6];
@@ -64,13 +64,14 @@ struct Desc {
   float* f32_p0;     // dual P_0 of the inner solve
   float* f32_r;      // r = F(u) rounded to FP32
   float* f32_u;      // u rounded to FP32
+  unsigned long long cond;  // CUDA-graph conditional handle of the device-side PDHG loop (0: none)
 };
 
 struct State {
   int n;             // PDHG updates taken in this solve
   int status;        // StStatus
   int max_iter;
-  int pad;
+  unsigned int trips;  // k_res launches since the solve was armed (bounds the device-side loop)
   double r;          // last stopping measure
   double r0;         // first stopping measure of this solve
   double thresh;     // stopping threshold on the measure
@@ -79,6 +80,8 @@ struct State {
   double best;       // smallest measure at which the measure last halved (stall detection)
   int best_n;        // update count at that point
   unsigned int ticket;
+  int total;         // defect-correction outer state: PDHG updates of this step's inner solves
+  int launches;      // defect-correction outer state: k_res launches of this step's inner solves
 };
 
 // Phases of one slot of a batch (device-side control of FP64 defect correction and time steps).

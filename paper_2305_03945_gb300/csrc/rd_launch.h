@@ -24,16 +24,20 @@ template <class T>
 cudaError_t launch_iteration(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
 
 
+// The step-level kernels (begin, FP64 residual, mass) run point_blocks(nx, ny) blocks of 256
+// threads, two points per thread; d.partials must hold ncomp * point_blocks(nx, ny) doubles.
+inline int point_blocks(int nx, int ny) { return (int)(((size_t)nx * ny / 2 + 255) / 256); }
+
 cudaError_t launch_begin(const Desc* d64, State* st, const double* uk, double* rhs, double tol, int tol_kind,
-                         int nbands, cudaStream_t s);
+                         int nblocks, cudaStream_t s);
 cudaError_t launch_resid64(const Desc& hd, const Desc* d64, State* outer, State* inner, const double* u,
                            const double* rhs, double* w64, float* r32, float* u32, float* z0, float* z1, int decide,
-                           double rtol, int nbands, cudaStream_t s);
+                           double rtol, int max_outer, int nblocks, cudaStream_t s);
 
 // Set the thread-local detail string returned by rd_last_error().
 void set_last_error(const char* msg);
 
-cudaError_t launch_axpy_dc(double* u, const float* dlt, size_t n, cudaStream_t s);
-cudaError_t launch_mass(const Desc* d64, State* st, const double* u, int nbands, cudaStream_t s);
+cudaError_t launch_axpy_dc(double* u, const float* dlt, size_t n, State* outer, const State* inner, cudaStream_t s);
+cudaError_t launch_mass(const Desc* d64, State* st, const double* u, const State* gate, int nblocks, cudaStream_t s);
 
 }  // namespace rd

@@ -240,6 +240,21 @@ __device__ inline void finalize_measure(const Desc& d, State* st, double* red, S
     slot->inner_total += st->n;
     slot->phase = st->status == ST_DIVERGED ? PH_FAILED : PH_AXPY;
   }
+  if (d.cond && st->status != ST_ACTIVE) cudaGraphSetConditional(d.cond, 0);  // ends the device-side loop
+}
+
+// Extra k_res launches a device-side loop may take beyond max_iter before it is stopped: covers
+// the launches that find the solve already finished inside the last loop trip (<= 256 per trip).
+constexpr unsigned kLoopSlack = 1024;
+
+// First thread of k_res inside a device-side loop (a WHILE node of a CUDA graph): counts the
+// launch and ends the loop when the solve is no longer active, or, as a hard bound that holds
+// whatever the stopping logic does, when the launches exceed max_iter + kLoopSlack.
+__device__ __forceinline__ void loop_guard(const Desc& d, State* st) {
+  const unsigned t = st->trips + 1u;
+  st->trips = t;
+  if (*((volatile const int*)&st->status) != ST_ACTIVE || t > (unsigned)st->max_iter + kLoopSlack)
+    cudaGraphSetConditional(d.cond, 0);
 }
 
 // 16-byte vectors
@@ -274,19 +289,34 @@ __device__ __forceinline__ void vst(T* __restrict__ p, const T* v) {
 }
 
 // Copy rows g0 .. g0+nrows-1 (boundary-mapped) of a plane into shared memory (row stride nx).
+// Each thread first gathers up to 8 vectors into registers and only then stores them, so that
+// all of its global loads are in flight together.
 template <class T, int W>
 __device__ __forceinline__ void stage_rows_w(T* dst, const T* __restrict__ src, int nx, int lognx, int ny, int bc,
                                              int g0, int nrows) {
+  constexpr int MAXV = 8;
   const int lw = W == 4 ? 2 : (W == 2 ? 1 : 0);
   const int lv = lognx - lw;  // log2 vectors per row
   const int total = nrows << lv;
-#pragma unroll 4
-  for (int v = threadIdx.x; v < total; v += blockDim.x) {
-    const int r = v >> lv, c = v & ((1 << lv) - 1);
-    const int g = bcmap(g0 + r, ny, bc);
-    T e[W];
-    vld<T, W>(src + (size_t)g * nx + c * W, e);
-    vst<T, W>(dst + r * nx + c * W, e);
+  const int nt = blockDim.x;
+  for (int base = 0; base < total; base += MAXV * nt) {
+    T e[MAXV][W];
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int v = base + threadIdx.x + q * nt;
+      if (v < total) {
+        const int r = v >> lv, c = v & ((1 << lv) - 1);
+        vld<T, W>(src + (size_t)bcmap(g0 + r, ny, bc) * nx + c * W, e[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int v = base + threadIdx.x + q * nt;
+      if (v < total) {
+        const int r = v >> lv, c = v & ((1 << lv) - 1);
+        vst<T, W>(dst + r * nx + c * W, e[q]);
+      }
+    }
   }
 }
 template <class T>
@@ -359,14 +389,29 @@ __device__ __forceinline__ void res_points(const Desc& d, cx<T>* buf, const T* x
   const bool transform = d.precond != 0;
   const int lw = W == 4 ? 2 : (W == 2 ? 1 : 0);
   const int lv = d.lognx - lw;
-  for (int v = threadIdx.x; v < (rows << lv); v += blockDim.x) {
+  constexpr int G = 4;  // vector groups whose right-hand sides are loaded together
+  const int total = rows << lv;
+  for (int base = 0; base < total; base += G * blockDim.x) {
+   T rrg0[G][W], rrg1[G][W];
+   if constexpr (!PC) {
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      const int v = base + threadIdx.x + q * blockDim.x;
+      if (v < total) {
+        const size_t o = (size_t)(y0 + (v >> lv)) * nx + (v & ((1 << lv) - 1)) * W;
+        vld<T, W>(R + o, rrg0[q]);
+        if constexpr (KT<K>::two) vld<T, W>(R + plane + o, rrg1[q]);
+      }
+    }
+   }
+#pragma unroll
+   for (int q = 0; q < G; ++q) {
+    const int v = base + threadIdx.x + q * blockDim.x;
+    if (v >= total) break;
     const int r = v >> lv, j0 = (v & ((1 << lv) - 1)) * W;
     const size_t o = (size_t)(y0 + r) * nx + j0;
-    T rr0[W], rr1[W];
-    if constexpr (!PC) {
-      vld<T, W>(R + o, rr0);
-      if constexpr (KT<K>::two) vld<T, W>(R + plane + o, rr1);
-    }
+    const T* rr0 = rrg0[q];
+    const T* rr1 = rrg1[q];
     T w0[W], w1[W];
     if (j0 >= 2 && j0 + W + 2 <= nx)
       res_group<T, K, false, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, lpc, ls, w0, w1);
@@ -393,6 +438,7 @@ __device__ __forceinline__ void res_points(const Desc& d, cx<T>* buf, const T* x
       vst<T, W>(WY + o, w0);
       if (nc > 1) vst<T, W>(WY + plane + o, w1);
     }
+   }
   }
 }
 
@@ -424,7 +470,9 @@ __device__ __forceinline__ void res_body(const Desc& d, State* __restrict__ st, 
   const cx<T>* dcs;
   cx<T>* buf = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, d.twx, d.dcx, nx, d.precond != 0,
                                                         d.precond != 0 && bc == BC_NEUMANN, tws, dcs));
-  T* xs = reinterpret_cast<T*>(buf + nc * lpc * ls);
+  const bool pp = (d.fft_pp & 1) != 0;
+  cx<T>* scr = pp ? buf + nc * lpc * ls : buf;
+  T* xs = reinterpret_cast<T*>(buf + (pp ? 2 : 1) * nc * lpc * ls);
   T* bs = xs + nc * srows * nx;
   const T* X = static_cast<const T*>(d.X);
   for (int c = 0; c < nc; ++c) stage_rows<T>(xs + c * srows * nx, X + c * plane, nx, lognx, ny, bc, y0 - H, srows);
@@ -442,13 +490,13 @@ __device__ __forceinline__ void res_body(const Desc& d, State* __restrict__ st, 
   // 3. forward row transform and its epilogue straight to global memory
   if (d.precond != 0) {
     __syncthreads();
-    block_fft<T, -1>(buf, nc * lpc, lognx, ls, tws, tid, nt);
+    const cx<T>* res = block_fft<T, -1>(buf, scr, nc * lpc, lognx, ls, tws, tid, nt);
     const int hn = nx >> 1, lh = lognx - 1;
     const cx<T>* dcx = dcs;
     for (int g = tid; g < ((nc * lpc) << lh); g += nt) {
       const int line = g >> lh, k = g & (hn - 1);
       const int c = (PC ? nc > 1 : KT<K>::two) ? line / lpc : 0, m = line - c * lpc;
-      const cx<T>* L = buf + line * ls;
+      const cx<T>* L = res + line * ls;
       T* Wa = WY + c * plane + (size_t)(y0 + 2 * m) * nx;
       T* Wb = Wa + nx;
       cx<T> ok, okp;
@@ -480,6 +528,9 @@ __device__ __forceinline__ void res_body(const Desc& d, State* __restrict__ st, 
 template <class T, int K>
 __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_res(const __grid_constant__ Desc d, State* __restrict__ st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if constexpr (K != KK_PCONLY) {
+    if (d.cond && blockIdx.x == 0 && threadIdx.x == 0) loop_guard(d, st);
+  }
   res_body<T, K>(d, st, nullptr, blockIdx.x, smem_raw);
 }
 
@@ -506,6 +557,7 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
   const cx<T>* twy;
   const cx<T>* dcy;
   cx<T>* buf = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, d.twy, d.dcy, ny, true, !per, twy, dcy));
+  cx<T>* scr = (d.fft_pp & 2) ? buf + nl * ls : buf;
   // spectral symbol 1 / (g_hat nx ny), g_hat = (1 + c1 mu + c2 mu^2)^2, mu = mu_x(kx) + mu_y(ky)
   const T* mux = static_cast<const T*>(d.mux);
   const T* muy = static_cast<const T*>(d.muy);
@@ -516,19 +568,34 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
     else return inn / (g * g);
   };
 
-#pragma unroll 4
-  for (int g = tid; g < (ny << lnl); g += nt) {
-    const int row = g >> lnl, m = g & (nl - 1);
-    const cx<T> v = *reinterpret_cast<const cx<T>*>(WY + (size_t)row * nx + x0 + 2 * m);
-    const int slot = per ? row : mk_slot(row, ny);
-    buf[m * ls + pidx(slot)] = v;
+  {
+    // gather all of this thread's column pairs first, then store them (loads in flight together)
+    constexpr int MAXV = 16;
+    const int total = ny << lnl;
+    for (int base = 0; base < total; base += MAXV * nt) {
+      cx<T> v[MAXV];
+#pragma unroll
+      for (int q = 0; q < MAXV; ++q) {
+        const int g = base + tid + q * nt;
+        if (g < total) v[q] = *reinterpret_cast<const cx<T>*>(WY + (size_t)(g >> lnl) * nx + x0 + 2 * (g & (nl - 1)));
+      }
+#pragma unroll
+      for (int q = 0; q < MAXV; ++q) {
+        const int g = base + tid + q * nt;
+        if (g < total) {
+          const int row = g >> lnl, m = g & (nl - 1);
+          buf[m * ls + pidx(per ? row : mk_slot(row, ny))] = v[q];
+        }
+      }
+    }
   }
   __syncthreads();
-  block_fft<T, -1>(buf, nl, logny, ls, twy, tid, nt);
+  cx<T>* cur = block_fft<T, -1>(buf, scr, nl, logny, ls, twy, tid, nt);
+  cx<T>* oth = cur == buf ? scr : buf;
   // forward epilogue and the spectral scaling 1 / (g_hat nx ny), in place
   for (int g = tid; g < (nl << lh); g += nt) {
     const int m = g >> lh, k = g & (hn - 1);
-    cx<T>* L = buf + m * ls;
+    cx<T>* L = cur + m * ls;
     const int col = x0 + 2 * m;
     cx<T> ok, okp;
     fwd_post(L, ny, d.bc, dcy, k, ok, okp);
@@ -544,18 +611,18 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
   }
   __syncthreads();
   if (per) {
-    block_fft<T, -1>(buf, nl, logny, ls, twy, tid, nt);
-    post_inplace(buf, nl, logny, ls, d.bc, dcy);
+    cx<T>* c2 = block_fft<T, -1>(cur, oth, nl, logny, ls, twy, tid, nt);
+    post_inplace(c2, nl, logny, ls, d.bc, dcy);
     __syncthreads();
 #pragma unroll 4
     for (int g = tid; g < (ny << lnl); g += nt) {
       const int row = g >> lnl, m = g & (nl - 1);
-      *reinterpret_cast<cx<T>*>(WY + (size_t)row * nx + x0 + 2 * m) = buf[m * ls + pidx(row)];
+      *reinterpret_cast<cx<T>*>(WY + (size_t)row * nx + x0 + 2 * m) = c2[m * ls + pidx(row)];
     }
   } else {
     for (int g = tid; g < (nl << lh); g += nt) {
       const int m = g >> lh, k = g & (hn - 1);
-      cx<T>* L = buf + m * ls;
+      cx<T>* L = cur + m * ls;
       const cx<T> w = dcy[k];
       cx<T> zk, zkp;
       if (k == 0) {
@@ -574,11 +641,11 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
       }
     }
     __syncthreads();
-    block_fft<T, 1>(buf, nl, logny, ls, twy, tid, nt);
+    cx<T>* c2 = block_fft<T, 1>(cur, oth, nl, logny, ls, twy, tid, nt);
 #pragma unroll 4
     for (int g = tid; g < (ny << lnl); g += nt) {
       const int n = g >> lnl, m = g & (nl - 1);
-      *reinterpret_cast<cx<T>*>(WY + (size_t)mk_perm(n, ny) * nx + x0 + 2 * m) = buf[m * ls + pidx(n)];
+      *reinterpret_cast<cx<T>*>(WY + (size_t)mk_perm(n, ny) * nx + x0 + 2 * m) = c2[m * ls + pidx(n)];
     }
   }
 }
@@ -623,20 +690,34 @@ __device__ __forceinline__ void upd_points(const Desc& d, const cx<T>* buf, int 
   const T* Bs = static_cast<const T*>(d.base);
   const int lw = W == 4 ? 2 : (W == 2 ? 1 : 0);
   const int lv = d.lognx - lw;
-  for (int v = threadIdx.x; v < (rows << lv); v += blockDim.x) {
-    const int r = v >> lv, j0 = (v & ((1 << lv) - 1)) * W;
-    const size_t o = (size_t)(y0 + r) * nx + j0;
-    T xa[W], xb[W], sa[W], sb[W];
-    vld<T, W>(X + o, xa);
-    if constexpr (KT<K>::two) vld<T, W>(X + plane + o, xb);
-    if constexpr (DC && KT<K>::nonlinear) {
-      vld<T, W>(Bs + o, sa);
-      if constexpr (KT<K>::two) vld<T, W>(Bs + plane + o, sb);
+  constexpr int G = KT<K>::two ? 2 : 4;  // vector groups loaded together
+  const int total = rows << lv;
+  for (int base = 0; base < total; base += G * blockDim.x) {
+    T xa[G][W], xb[G][W], sa[G][W], sb[G][W];
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      const int v = base + threadIdx.x + q * blockDim.x;
+      if (v < total) {
+        const size_t o = (size_t)(y0 + (v >> lv)) * nx + (v & ((1 << lv) - 1)) * W;
+        vld<T, W>(X + o, xa[q]);
+        if constexpr (KT<K>::two) vld<T, W>(X + plane + o, xb[q]);
+        if constexpr (DC && KT<K>::nonlinear) {
+          vld<T, W>(Bs + o, sa[q]);
+          if constexpr (KT<K>::two) vld<T, W>(Bs + plane + o, sb[q]);
+        }
+      }
     }
-    if (j0 >= 2 && j0 + W + 2 <= nx) upd_group<T, K, false, W>(d, buf, ls, lpc, H + r, j0, xa, xb, sa, sb);
-    else upd_group<T, K, true, W>(d, buf, ls, lpc, H + r, j0, xa, xb, sa, sb);
-    vst<T, W>(X + o, xa);
-    if constexpr (KT<K>::two) vst<T, W>(X + plane + o, xb);
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      const int v = base + threadIdx.x + q * blockDim.x;
+      if (v >= total) break;
+      const int r = v >> lv, j0 = (v & ((1 << lv) - 1)) * W;
+      const size_t o = (size_t)(y0 + r) * nx + j0;
+      if (j0 >= 2 && j0 + W + 2 <= nx) upd_group<T, K, false, W>(d, buf, ls, lpc, H + r, j0, xa[q], xb[q], sa[q], sb[q]);
+      else upd_group<T, K, true, W>(d, buf, ls, lpc, H + r, j0, xa[q], xb[q], sa[q], sb[q]);
+      vst<T, W>(X + o, xa[q]);
+      if constexpr (KT<K>::two) vst<T, W>(X + plane + o, xb[q]);
+    }
   }
 }
 
@@ -661,8 +742,10 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
   const T* WY = static_cast<const T*>(d.WY);
   const cx<T>* twx;
   const cx<T>* dcx;
-  cx<T>* buf = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, d.twx, d.dcx, nx, d.precond != 0,
-                                                        d.precond != 0 && bc == BC_NEUMANN, twx, dcx));
+  cx<T>* buf0 = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, d.twx, d.dcx, nx, d.precond != 0,
+                                                         d.precond != 0 && bc == BC_NEUMANN, twx, dcx));
+  cx<T>* scr = (d.fft_pp & 4) ? buf0 + nl * ls : buf0;
+  cx<T>* buf = buf0;  // the buffer that holds Y (then P~) after the inverse transform
   const int hn = nx >> 1, lh = lognx - 1;
   if (SmemTables<T>::value && d.precond != 0 && bc == BC_NEUMANN) __syncthreads();
 
@@ -676,12 +759,12 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
       const T* Wc = WY + c * plane;
       const cx<T> a = *reinterpret_cast<const cx<T>*>(Wc + (size_t)ga * nx + j);
       const cx<T> b = *reinterpret_cast<const cx<T>*>(Wc + (size_t)gb * nx + j);
-      buf[line * ls + pidx(j)] = cx<T>{a.x, b.x};
-      buf[line * ls + pidx(j + 1)] = cx<T>{a.y, b.y};
+      buf0[line * ls + pidx(j)] = cx<T>{a.x, b.x};
+      buf0[line * ls + pidx(j + 1)] = cx<T>{a.y, b.y};
     }
     __syncthreads();
     if (d.precond != 0) {
-      block_fft<T, -1>(buf, nl, lognx, ls, twx, tid, nt);
+      buf = block_fft<T, -1>(buf0, scr, nl, lognx, ls, twx, tid, nt);
       post_inplace(buf, nl, lognx, ls, bc, dcx);
       __syncthreads();
     }
@@ -692,7 +775,7 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
       const int ga = bcmap(y0 - H + 2 * m, ny, bc), gb = bcmap(y0 - H + 2 * m + 1, ny, bc);
       const T* Wa = WY + c * plane + (size_t)ga * nx;
       const T* Wb = WY + c * plane + (size_t)gb * nx;
-      cx<T>* L = buf + line * ls;
+      cx<T>* L = buf0 + line * ls;
       const cx<T> w = dcx[k];
       cx<T> zk, zkp;
       if (k == 0) {
@@ -710,7 +793,7 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
       }
     }
     __syncthreads();
-    block_fft<T, 1>(buf, nl, lognx, ls, twx, tid, nt);
+    buf = block_fft<T, 1>(buf0, scr, nl, lognx, ls, twx, tid, nt);
     // undo the Makhoul reordering in place (slot n holds column mk_perm(n)), in chunks of lines
     // so that each thread holds at most 16 values between the two barriers
     {
@@ -758,15 +841,31 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
     const T* Pin = static_cast<const T*>(d.P[(n - 1) & 1]);
     T* Pout = static_cast<T*>(d.P[n & 1]);
     const T tp = T(d.tau_p), tpe = T((1.0 + d.omega) * d.tau_p);
-#pragma unroll 2
-    for (int g = tid; g < (nl << lh); g += nt) {
+    constexpr int G = 8;  // slot pairs whose P values are loaded together
+    const int totalp = nl << lh;
+    for (int base = 0; base < totalp; base += G * nt) {
+     cx<T> pag[G], pbg[G];
+#pragma unroll
+     for (int q = 0; q < G; ++q) {
+      const int g = base + tid + q * nt;
+      if (g < totalp) {
+        const int line = g >> lh, j = 2 * (g & (hn - 1));
+        const int c = (PC ? nc > 1 : KT<K>::two) ? line / lpc : 0, m = line - c * lpc;
+        pag[q] = *reinterpret_cast<const cx<T>*>(Pin + c * plane + (size_t)bcmap(y0 - H + 2 * m, ny, bc) * nx + j);
+        pbg[q] = *reinterpret_cast<const cx<T>*>(Pin + c * plane + (size_t)bcmap(y0 - H + 2 * m + 1, ny, bc) * nx + j);
+      }
+     }
+#pragma unroll
+     for (int q = 0; q < G; ++q) {
+      const int g = base + tid + q * nt;
+      if (g >= totalp) break;
       const int line = g >> lh, j = 2 * (g & (hn - 1));
       const int c = (PC ? nc > 1 : KT<K>::two) ? line / lpc : 0, m = line - c * lpc;
       const int la = 2 * m, lb = 2 * m + 1;
       const size_t oa = c * plane + (size_t)bcmap(y0 - H + la, ny, bc) * nx + j;
       const size_t ob = c * plane + (size_t)bcmap(y0 - H + lb, ny, bc) * nx + j;
-      const cx<T> pa = *reinterpret_cast<const cx<T>*>(Pin + oa);
-      const cx<T> pb = *reinterpret_cast<const cx<T>*>(Pin + ob);
+      const cx<T> pa = pag[q];
+      const cx<T> pb = pbg[q];
       cx<T>* s0 = buf + line * ls + pidx(j);
       cx<T>* s1 = buf + line * ls + pidx(j + 1);
       const cx<T> y0v = *s0, y1v = *s1;  // (row a, row b) at columns j, j+1
@@ -774,6 +873,7 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
       *s1 = cx<T>{pa.y + tpe * y1v.x, pb.y + tpe * y1v.y};
       if (la >= H && la < H + rows) *reinterpret_cast<cx<T>*>(Pout + oa) = cx<T>{pa.x + tp * y0v.x, pa.y + tp * y1v.x};
       if (lb >= H && lb < H + rows) *reinterpret_cast<cx<T>*>(Pout + ob) = cx<T>{pb.x + tp * y0v.y, pb.y + tp * y1v.y};
+     }
     }
     __syncthreads();
 

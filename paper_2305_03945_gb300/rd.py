@@ -47,7 +47,7 @@ class rd_opts(ctypes.Structure):
                 ("omega", ctypes.c_double), ("precision", ctypes.c_int),
                 ("dc_inner_rtol", ctypes.c_double), ("dc_max_outer", ctypes.c_int),
                 ("graph_k", ctypes.c_int), ("band_rows", ctypes.c_int), ("col_width", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("fft_buffers", ctypes.c_int)]
 
 
 class rd_stats(ctypes.Structure):
@@ -161,8 +161,8 @@ def _check(status, ok=(RD_OK,)):
     return status
 
 
-def make_structs(pb, precision="fp64", graph_k=8, band_rows=0, col_width=0, dc_inner_rtol=1e-4,
-                 dc_max_outer=12, profile=0):
+def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_inner_rtol=1e-4,
+                 dc_max_outer=12, profile=0, fft_buffers=0):
     """C structs for a ``workloads.Problem``."""
     g = rd_grid()
     g.ndim = 2
@@ -188,6 +188,7 @@ def make_structs(pb, precision="fp64", graph_k=8, band_rows=0, col_width=0, dc_i
     o.dc_inner_rtol = dc_inner_rtol
     o.dc_max_outer = dc_max_outer
     o.profile = profile
+    o.fft_buffers = fft_buffers
     return g, rx, pc, o
 
 

@@ -212,3 +212,125 @@ def test_step_in_place_alias():
     with rd.Solver(pb) as s:
         s.step(u, u)
     assert rel_max(host(u), U_ref) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dc"])
+@pytest.mark.parametrize("kind,op,p,bc,shape", [STEP_CASES[1], STEP_CASES[3], STEP_CASES[4]])
+def test_transform_buffer_modes_agree(precision, kind, op, p, bc, shape):
+    """In-place (one buffer) and ping-pong (two buffers) shared-memory transforms perform the same
+    arithmetic: the steps agree bit for bit, and both match the oracle."""
+    pb = _problem(kind, op, p, bc, *shape)
+    uk = _state(pb, 9)
+    outs = []
+    for fb in (1, 2):
+        U, info, U_ref, _ = _compare_step(pb, uk, precision=precision, fft_buffers=fb)
+        assert info["status"] == 0, info
+        tol = 1e-10 if precision == "fp64" else 1e-9
+        assert np.linalg.norm(U - U_ref) <= tol * np.linalg.norm(U_ref)
+        outs.append(U)
+    assert np.array_equal(outs[0], outs[1])
+
+
+BENCH_WORKLOADS = {
+    "allen_cahn_neumann_1024": lambda: WL.config_allen_cahn_neumann(),
+    "cahn_hilliard_split_512": lambda: WL.config_cahn_hilliard_split(),
+    "gray_scott_2048": lambda: WL.config_gray_scott(),
+    "schnakenberg_128": lambda: WL.config_schnakenberg(),
+    "allen_cahn_periodic_64": lambda: WL.config_allen_cahn_periodic(),
+}
+
+
+def _apply_g(pb, Y):
+    """G Y with G = A_lin^2 applied as stencils (oracle five-point Laplacian), per component."""
+    out = np.empty_like(Y)
+    for c in range(pb.ncomp):
+        if pb.kind in ("gray_scott", "schnakenberg"):
+            A = lambda v, D=pb.p[c]: v - D * pb.dt * O.lap(v, pb)
+        elif pb.op == "laplacian":
+            A = lambda v: v - pb.a * pb.dt * O.lap(v, pb)
+        else:
+            A = lambda v: v + pb.a * pb.dt * O.lap(O.lap(v, pb), pb)
+        out[c] = A(A(Y[c]))
+    return out
+
+
+@pytest.mark.parametrize("name", sorted(BENCH_WORKLOADS))
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dc"])
+def test_benchmark_workloads_plan_in_both_precisions(name, precision):
+    """Every benchmarked workload finds a launch plan that fits shared memory in both precisions.
+    FP64: the preconditioner solve at that size against the oracle up to 512^2 points, above that
+    through G Y = W with G applied back as stencils.  FP32 defect correction: one step from the
+    workload's initial state meets the stopping rule, with F evaluated by the oracle."""
+    rd = _rd()
+    w = BENCH_WORKLOADS[name]()
+    pb = w.problem
+    if precision == "fp64":
+        W = WL.rng(12).standard_normal(pb.shape)
+        with rd.Solver(pb, precision=precision) as s:
+            y = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+            s.apply_precond(dev(W), y)
+            got = host(y)
+        if pb.nx * pb.ny <= 512 * 512:
+            assert rel_max(got, O.apply_ginv(pb, W)) <= 1e-12
+        else:
+            assert rel_max(_apply_g(pb, got), W) <= 1e-10
+    else:
+        with rd.Solver(pb, precision=precision) as s:
+            out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+            info = s.step(dev(w.u0), out)
+            U = host(out)
+        assert info["status"] == 0, info
+        r, thr = O.measure(pb, O.residual(pb, U, w.u0), w.u0)
+        assert r <= thr * (1 + 1e-6), (r, thr)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dc"])
+def test_device_loop_trip_length_does_not_change_results(precision):
+    """The device-side loop runs graph_k iterations per trip and stops itself: the trip length
+    changes neither the iterates (bit for bit) nor the iteration counts."""
+    rd = _rd()
+    pb = _problem("allen_cahn", "laplacian", (), "neumann", 64, 64)
+    uk = _state(pb, 10)
+    outs, infos = [], []
+    for gk in (1, 3, 8):
+        U, info, U_ref, info_ref = _compare_step(pb, uk, precision=precision, graph_k=gk)
+        assert info["status"] == 0, info
+        outs.append(U)
+        infos.append((info["iterations"], info["outer_rounds"]))
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+    assert len(set(infos)) == 1
+
+
+def test_host_syncs_per_step():
+    """FP64: one graph launch and one host read per step.  Defect correction: one per outer
+    round after the first FP64 residual (each round graph ends with the next residual)."""
+    rd = _rd()
+    w = WL.config_allen_cahn_periodic(64, 3)
+    for precision in ("fp64", "fp32_dc"):
+        u = dev(w.u0)
+        with rd.Solver(w.problem, precision=precision) as s:
+            s.reset_stats()
+            infos, st = s.solve(u, 3)
+            stats = s.stats()
+        assert st == 0
+        if precision == "fp64":
+            assert stats["host_syncs"] == 3 and stats["graph_launches"] == 3
+            assert stats["pdhg_iterations"] == sum(i["iterations"] for i in infos)
+        else:
+            rounds = sum(max(i["outer_rounds"] - 1, 1) for i in infos)
+            assert stats["host_syncs"] == rounds
+            assert stats["residual_passes"] == sum(i["outer_rounds"] for i in infos)
+            assert stats["pdhg_iterations"] == sum(i["iterations"] for i in infos)
+
+
+def test_defect_correction_outer_round_limit():
+    """dc_max_outer = 1: one inner solve, two FP64 residual evaluations, then NOT_CONVERGED
+    with the iterate after that one correction (the FP64 plain step converges to it only later)."""
+    rd = _rd()
+    pb = _problem("allen_cahn", "laplacian", (), "periodic", 32, 32)
+    uk = _state(pb, 11)
+    with rd.Solver(pb, precision="fp32_dc", dc_max_outer=1) as s:
+        out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        info = s.step(dev(uk), out, allow=(rd.RD_OK, rd.RD_ERR_NOT_CONVERGED))
+    assert info["status"] == rd.RD_ERR_NOT_CONVERGED
+    assert info["outer_rounds"] == 2 and info["iterations"] > 0
