@@ -120,6 +120,15 @@ typedef enum {
                             the stopping rule above holds for F(u) evaluated in FP64             */
 } rd_precision;
 
+typedef enum {
+    RD_LOOP_GRAPH = 0,    /* the PDHG iterations run in a WHILE node of the step's CUDA graph
+                             (graph_k iterations per trip) that the kernels end themselves: one
+                             graph launch per FP64 step or per defect-correction outer round  */
+    RD_LOOP_HOST = 1      /* plain CUDA graphs of graph_k iterations, launched until the host
+                             reads a finished state: the same kernels as ordinary graph kernel
+                             nodes (profilers cannot attribute kernels inside conditional nodes) */
+} rd_solve_loop;
+
 typedef struct {
     double tol;           /* stopping threshold (delta), default 1e-10                          */
     int tol_kind;         /* rd_tol_kind, default RD_TOL_RES_ABS                                */
@@ -137,6 +146,7 @@ typedef struct {
     int fft_buffers;      /* shared-memory transforms: 0 = chosen per kernel (two buffers where the
                              second costs no resident blocks), 1 = in place in one buffer,
                              2 = two buffers wherever they fit; default 0                       */
+    int solve_loop;       /* rd_solve_loop, default RD_LOOP_GRAPH                               */
 } rd_opts;
 
 typedef struct {

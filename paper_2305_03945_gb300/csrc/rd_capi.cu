@@ -207,6 +207,9 @@ struct rd_pdhg {
   // step (with the step set-up), [1] every later round.
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // RD_LOOP_HOST: graph_k PDHG iterations without conditional nodes, relaunched by the host
+  cudaGraph_t hgraph = nullptr;
+  cudaGraphExec_t hexec = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // around the first iteration's kernels
   int kernels_per_iter = 0;
   rd_stats stats{};
@@ -297,9 +300,9 @@ rd_status status_of(int st) {
 //   [k_begin, k_resid64], iteration 1, WHILE { graph_k iterations }, k_axpy_dc, k_resid64, k_mass
 // Iteration 1 sits outside the loop so that the profiling events (which a conditional body
 // cannot hold) bracket its three kernels.  The loop's condition starts at 1 on every launch;
-// k_res clears it when the solve is not active (or after max_iter + slack launches), and the
-// last block of k_res clears it when the stopping rule ends the solve.  k_axpy_dc, the second
-// k_resid64 and k_mass act only while (resp. once no longer) the outer loop is active.
+// k_loop_cond, run after iteration 1 and at the end of every trip, clears it once the solve has
+// ended (or after max_iter + slack k_res launches).  k_axpy_dc, the second k_resid64 and
+// k_mass act only while (resp. once no longer) the outer loop is active.
 rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraphExec_t* exec) {
   const int K = h->opts.graph_k;
   cudaStream_t cs = h->cap_stream;
@@ -313,8 +316,7 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   *out = g;
   cudaGraphConditionalHandle cond = 0;
   RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
-  Desc dd = h->dc ? h->h_desc[1] : h->h_desc[0];
-  dd.cond = cond;
+  const Desc dd = h->dc ? h->h_desc[1] : h->h_desc[0];
   auto iteration = [&](cudaStream_t st, cudaEvent_t* ev) {
     return h->dc ? launch_iteration<float>(dd, sti, h->cfg32, st, ev) : launch_iteration<double>(dd, sti, h->cfg64, st, ev);
   };
@@ -334,7 +336,8 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
                          h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, cs);
     if (e != cudaSuccess) return abort_capture(cs, "step set-up during capture", e);
   }
-  if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr)) != cudaSuccess)
+  if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr)) != cudaSuccess ||
+      (e = launch_loop_cond(sti, cond, 1u, cs)) != cudaSuccess)
     return abort_capture(cs, "kernel launch during capture", e);
   // the WHILE node, appended to the capture after the first iteration
   cudaStreamCaptureStatus cst;
@@ -358,6 +361,7 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
       cudaSuccess)
     return abort_capture(cs, "capturing the loop body", e);
   for (int k = 0; k < K && e == cudaSuccess; ++k) e = iteration(h->body_stream, nullptr);
+  if (e == cudaSuccess) e = launch_loop_cond(sti, cond, (unsigned)K, h->body_stream);
   if (e != cudaSuccess) {
     abort_capture(h->body_stream, "loop body", e);
     return abort_capture(cs, "kernel launch during capture", e);
@@ -381,11 +385,32 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   return RD_OK;
 }
 
+// RD_LOOP_HOST: one graph of graph_k PDHG iterations (profiling events around the first).
+rd_status capture_iter_graph(rd_pdhg* h) {
+  const int K = h->opts.graph_k;
+  RD_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < K; ++k) {
+    cudaEvent_t* ev = (k == 0 && h->opts.profile) ? h->ev : nullptr;
+    const cudaError_t e = h->dc ? launch_iteration<float>(h->h_desc[1], h->d_state + 1, h->cfg32, h->cap_stream, ev)
+                                : launch_iteration<double>(h->h_desc[0], h->d_state + 0, h->cfg64, h->cap_stream, ev);
+    if (e != cudaSuccess) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(h->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      return fail(RD_ERR_CUDA, std::string("kernel launch during capture: ") + cudaGetErrorString(e));
+    }
+  }
+  RD_CUDA(cudaStreamEndCapture(h->cap_stream, &h->hgraph));
+  RD_CUDA(cudaGraphInstantiate(&h->hexec, h->hgraph, 0));
+  return RD_OK;
+}
+
 rd_status capture_graphs(rd_pdhg* h) {
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
   h->kernels_per_iter = lc.transform ? 3 : 2;
   if (h->opts.profile)
     for (int i = 0; i < 4; ++i) RD_CUDA(cudaEventCreate(&h->ev[i]));
+  if (h->opts.solve_loop == RD_LOOP_HOST) return capture_iter_graph(h);
   RD_TRY(capture_step_graph(h, true, &h->graph[0], &h->gexec[0]));
   if (h->dc) RD_TRY(capture_step_graph(h, false, &h->graph[1], &h->gexec[1]));
   return RD_OK;
@@ -425,6 +450,7 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
     if (o->precision != RD_PREC_FP64 && o->precision != RD_PREC_FP32_DC) return fail(RD_ERR_INVALID_ARG, "bad precision");
     if (o->graph_k < 1 || o->graph_k > 256) return fail(RD_ERR_INVALID_ARG, "graph_k must be in [1, 256]");
     if (o->fft_buffers < 0 || o->fft_buffers > 2) return fail(RD_ERR_INVALID_ARG, "fft_buffers must be 0, 1 or 2");
+    if (o->solve_loop != RD_LOOP_GRAPH && o->solve_loop != RD_LOOP_HOST) return fail(RD_ERR_INVALID_ARG, "bad solve_loop");
     if (o->precision == RD_PREC_FP32_DC && (!(o->dc_inner_rtol > 0) || o->dc_max_outer < 1))
       return fail(RD_ERR_INVALID_ARG, "bad defect-correction options");
   }
@@ -641,8 +667,10 @@ rd_status graph_round(rd_pdhg* h, int which) {
     h->stats.kernel_launches += 2;  // k_begin, k_mass (the P_0 clear is a memset node)
   }
   h->stats.pdhg_iterations += updates;
-  // every k_res launch (active or not) is followed by k_col and k_upd in the graph
+  // every k_res launch (active or not) is followed by k_col and k_upd in the graph, and
+  // k_loop_cond runs after the first and then after every graph_k of them
   h->stats.kernel_launches += (long long)sweeps * h->kernels_per_iter;
+  h->stats.kernel_launches += sweeps > 0 ? 1 + (sweeps - 1) / h->opts.graph_k : 1;
   if (h->opts.profile && sweeps > 0) {
     float ms = 0.f;
     RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
@@ -663,10 +691,106 @@ rd_status graph_round(rd_pdhg* h, int which) {
   return RD_OK;
 }
 
+// RD_LOOP_HOST: launch the graph_k-iteration graph, read solve state `which` back and account.
+rd_status iter_round(rd_pdhg* h, int which) {
+  cudaStream_t s = h->stream;
+  const int n_before = h->h_state[which].n;
+  RD_CUDA(cudaGraphLaunch(h->hexec, s));
+  RD_CUDA(cudaMemcpyAsync(h->h_state + which, h->d_state + which, sizeof(State), cudaMemcpyDeviceToHost, s));
+  RD_CUDA(cudaStreamSynchronize(s));
+  const int updates = h->h_state[which].n - n_before;
+  h->stats.graph_launches += 1;
+  h->stats.kernel_launches += (long long)h->opts.graph_k * h->kernels_per_iter;
+  h->stats.host_syncs += 1;
+  h->stats.pdhg_iterations += updates;
+  if (h->opts.profile) {
+    float ms = 0.f;
+    RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+    h->stats.kernel_ms[0] += ms;
+    h->stats.kernel_samples[0] += 1;
+    if (updates > 0) {  // the first iteration updated: k_col and k_upd ran
+      if ((h->dc ? h->cfg32 : h->cfg64).transform) {
+        RD_CUDA(cudaEventElapsedTime(&ms, h->ev[1], h->ev[2]));
+        h->stats.kernel_ms[1] += ms;
+        h->stats.kernel_samples[1] += 1;
+      }
+      RD_CUDA(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
+      h->stats.kernel_ms[2] += ms;
+      h->stats.kernel_samples[2] += 1;
+    }
+  }
+  return RD_OK;
+}
+
+// RD_LOOP_HOST: one implicit step with the loop decisions taken on the host.  The step kernels
+// are the same as in the step graphs (k_resid64 applies the outer stopping rule and arms the
+// inner solve, k_axpy_dc ends the step when the inner solve failed).
+rd_status step_host(rd_pdhg* h, rd_step_info* info) {
+  cudaStream_t s = h->stream;
+  const Desc* d64 = h->d_desc + 0;
+  State* st0 = h->d_state + 0;
+  State* st1 = h->d_state + 1;
+  const int nb = point_blocks(h->nx, h->ny);
+  const int max_launch = h->opts.max_iter / h->opts.graph_k + 2;
+  rd_step_info inf{};
+  int final_status;
+  RD_CUDA(launch_begin(d64, st0, h->U64, h->rhs64, h->opts.tol, h->opts.tol_kind, nb, s));
+  h->stats.kernel_launches += 2;  // k_begin, k_mass
+  h->h_state[0].n = 0;
+  h->h_state[1].n = 0;
+  if (!h->dc) {
+    RD_CUDA(cudaMemsetAsync(h->P64[0], 0, h->npts * sizeof(double), s));
+    for (int it = 0; it <= max_launch; ++it) {
+      RD_TRY(iter_round(h, 0));
+      if (h->h_state[0].status != ST_ACTIVE) break;
+    }
+    final_status = h->h_state[0].status;
+    inf.iterations = h->h_state[0].n;
+    inf.residual = h->h_state[0].r;
+    if (final_status == ST_ACTIVE) return fail(RD_ERR_TIMEOUT, "PDHG loop exceeded its launch bound");
+  } else {
+    int inner_total = 0;
+    for (int round = 0; round <= h->opts.dc_max_outer + 1; ++round) {
+      RD_CUDA(launch_resid64(h->h_desc[0], d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, h->D32,
+                             h->P32[0], 1, h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, s));
+      RD_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, 2 * sizeof(State), cudaMemcpyDeviceToHost, s));
+      RD_CUDA(cudaStreamSynchronize(s));
+      h->stats.kernel_launches += 1;
+      h->stats.host_syncs += 1;
+      if (h->h_state[0].status != ST_ACTIVE) break;  // converged, diverged, or out of rounds
+      for (int it = 0; it <= max_launch; ++it) {
+        RD_TRY(iter_round(h, 1));
+        if (h->h_state[1].status != ST_ACTIVE) break;
+      }
+      inner_total += h->h_state[1].n;
+      RD_CUDA(launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, s));
+      h->stats.kernel_launches += 1;
+    }
+    final_status = h->h_state[0].status;
+    if (final_status == ST_ACTIVE) return fail(RD_ERR_TIMEOUT, "defect-correction loop exceeded its round bound");
+    h->stats.residual_passes += h->h_state[0].n;  // FP64 evaluations k_resid64 counted
+    inf.iterations = inner_total;
+    inf.outer_rounds = h->h_state[0].n;
+    inf.residual = h->h_state[0].r;
+  }
+  RD_CUDA(launch_mass(d64, h->d_state + 2, h->U64, nullptr, nb, s));
+  RD_CUDA(cudaMemcpyAsync(h->h_state + 2, h->d_state + 2, sizeof(State), cudaMemcpyDeviceToHost, s));
+  RD_CUDA(cudaStreamSynchronize(s));
+  h->stats.host_syncs += 1;
+  inf.mass = h->h_state[2].mass;
+  inf.converged = final_status == ST_CONVERGED;
+  inf.status = status_of(final_status);
+  if (info) *info = inf;
+  if (inf.status != RD_OK)
+    return fail((rd_status)inf.status, inf.status == RD_ERR_DIVERGED ? "PDHG diverged" : "PDHG did not converge");
+  return RD_OK;
+}
+
 // One implicit step on the handle's FP64 iterate U64 (holding U^k).  FP64: one graph launch
 // runs the whole step.  Defect correction: one graph launch per outer round; the host only
 // reads the outer state between rounds.
 rd_status step_impl(rd_pdhg* h, rd_step_info* info) {
+  if (h->opts.solve_loop == RD_LOOP_HOST) return step_host(h, info);
   rd_step_info inf{};
   int final_status;
   RD_TRY(graph_round(h, 0));
@@ -711,6 +835,7 @@ void rd_opts_default(rd_opts* o) {
   o->col_width = 0;
   o->profile = 0;
   o->fft_buffers = 0;
+  o->solve_loop = RD_LOOP_GRAPH;
 }
 
 rd_status rd_pdhg_create(rd_pdhg** out, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* reaction,
@@ -829,6 +954,8 @@ void rd_pdhg_destroy(rd_pdhg* h) {
     if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
     if (h->graph[k]) cudaGraphDestroy(h->graph[k]);
   }
+  if (h->hexec) cudaGraphExecDestroy(h->hexec);
+  if (h->hgraph) cudaGraphDestroy(h->hgraph);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

@@ -64,14 +64,13 @@ struct Desc {
   float* f32_p0;     // dual P_0 of the inner solve
   float* f32_r;      // r = F(u) rounded to FP32
   float* f32_u;      // u rounded to FP32
-  unsigned long long cond;  // CUDA-graph conditional handle of the device-side PDHG loop (0: none)
 };
 
 struct State {
   int n;             // PDHG updates taken in this solve
   int status;        // StStatus
   int max_iter;
-  unsigned int trips;  // k_res launches since the solve was armed (bounds the device-side loop)
+  unsigned int trips;  // k_res launches since the solve was armed (counted by k_loop_cond)
   double r;          // last stopping measure
   double r0;         // first stopping measure of this solve
   double thresh;     // stopping threshold on the measure

@@ -179,6 +179,23 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Extra k_res launches a device-side loop may take beyond max_iter before it is stopped: covers
+// the launches that find the solve already finished inside the last loop trip (<= 256 per trip).
+constexpr unsigned kLoopSlack = 1024;
+
+// Decision of the device-side PDHG loop (a WHILE node of the step's CUDA graph), taken by one
+// thread after the first iteration and at the end of every loop trip: adds the `sweeps` k_res
+// launches since the last check to st->trips, and clears the loop condition when the solve is
+// no longer active or, as a hard bound that holds whatever the stopping logic does, when the
+// launches exceed max_iter + kLoopSlack.  Kept out of the sweep kernels, which thereby use no
+// device-side graph API.
+__global__ void k_loop_cond(State* __restrict__ st, cudaGraphConditionalHandle cond, unsigned sweeps) {
+  volatile State* vs = st;
+  const unsigned t = vs->trips + sweeps;
+  vs->trips = t;
+  if (vs->status != ST_ACTIVE || t > (unsigned)vs->max_iter + kLoopSlack) cudaGraphSetConditional(cond, 0);
+}
+
 // u += d after an inner solve of defect correction, when `outer` is active and the inner solve
 // ended converged (or stalled at its rounding floor) or at its iteration limit; an inner solve
 // that diverged, or that is still active, ends the step as diverged.  Adds the inner solve's
@@ -273,6 +290,11 @@ cudaError_t launch_resid64(const Desc& hd, const Desc* d64, State* outer, State*
 
 cudaError_t launch_axpy_dc(double* u, const float* dlt, size_t n, State* outer, const State* inner, cudaStream_t s) {
   k_axpy_dc<<<wave_blocks(k_axpy_dc, (int)((n / 4 + 255) / 256)), 256, 0, s>>>(u, dlt, n, outer, inner);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_cond(State* st, unsigned long long cond, unsigned sweeps, cudaStream_t s) {
+  k_loop_cond<<<1, 1, 0, s>>>(st, (cudaGraphConditionalHandle)cond, sweeps);
   return cudaGetLastError();
 }
 

@@ -37,6 +37,9 @@ cudaError_t launch_resid64(const Desc& hd, const Desc* d64, State* outer, State*
 // Set the thread-local detail string returned by rd_last_error().
 void set_last_error(const char* msg);
 
+// Device-side loop decision (one thread): adds `sweeps` to st->trips and clears the graph
+// conditional `cond` when the solve has ended (or the launch bound is passed).
+cudaError_t launch_loop_cond(State* st, unsigned long long cond, unsigned sweeps, cudaStream_t s);
 cudaError_t launch_axpy_dc(double* u, const float* dlt, size_t n, State* outer, const State* inner, cudaStream_t s);
 cudaError_t launch_mass(const Desc* d64, State* st, const double* u, const State* gate, int nblocks, cudaStream_t s);
 

@@ -240,21 +240,6 @@ __device__ inline void finalize_measure(const Desc& d, State* st, double* red, S
     slot->inner_total += st->n;
     slot->phase = st->status == ST_DIVERGED ? PH_FAILED : PH_AXPY;
   }
-  if (d.cond && st->status != ST_ACTIVE) cudaGraphSetConditional(d.cond, 0);  // ends the device-side loop
-}
-
-// Extra k_res launches a device-side loop may take beyond max_iter before it is stopped: covers
-// the launches that find the solve already finished inside the last loop trip (<= 256 per trip).
-constexpr unsigned kLoopSlack = 1024;
-
-// First thread of k_res inside a device-side loop (a WHILE node of a CUDA graph): counts the
-// launch and ends the loop when the solve is no longer active, or, as a hard bound that holds
-// whatever the stopping logic does, when the launches exceed max_iter + kLoopSlack.
-__device__ __forceinline__ void loop_guard(const Desc& d, State* st) {
-  const unsigned t = st->trips + 1u;
-  st->trips = t;
-  if (*((volatile const int*)&st->status) != ST_ACTIVE || t > (unsigned)st->max_iter + kLoopSlack)
-    cudaGraphSetConditional(d.cond, 0);
 }
 
 // 16-byte vectors
@@ -528,9 +513,6 @@ __device__ __forceinline__ void res_body(const Desc& d, State* __restrict__ st, 
 template <class T, int K>
 __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_res(const __grid_constant__ Desc d, State* __restrict__ st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if constexpr (K != KK_PCONLY) {
-    if (d.cond && blockIdx.x == 0 && threadIdx.x == 0) loop_guard(d, st);
-  }
   res_body<T, K>(d, st, nullptr, blockIdx.x, smem_raw);
 }
 

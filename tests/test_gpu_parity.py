@@ -334,3 +334,19 @@ def test_defect_correction_outer_round_limit():
         info = s.step(dev(uk), out, allow=(rd.RD_OK, rd.RD_ERR_NOT_CONVERGED))
     assert info["status"] == rd.RD_ERR_NOT_CONVERGED
     assert info["outer_rounds"] == 2 and info["iterations"] > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dc"])
+@pytest.mark.parametrize("kind,op,p,bc,shape", [STEP_CASES[1], STEP_CASES[3], STEP_CASES[4]])
+def test_host_loop_matches_graph_loop(precision, kind, op, p, bc, shape):
+    """The host-relaunched loop (plain graphs, for profilers) runs the same kernels as the
+    device-side WHILE loop: bit-identical steps and the same iteration and round counts."""
+    pb = _problem(kind, op, p, bc, *shape)
+    uk = _state(pb, 13)
+    res = []
+    for loop in ("graph", "host"):
+        U, info, U_ref, _ = _compare_step(pb, uk, precision=precision, solve_loop=loop)
+        assert info["status"] == 0, info
+        res.append((U, info["iterations"], info["outer_rounds"]))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1:] == res[1][1:]
