@@ -147,6 +147,8 @@ typedef struct {
                              second costs no resident blocks), 1 = in place in one buffer,
                              2 = two buffers wherever they fit; default 0                       */
     int solve_loop;       /* rd_solve_loop, default RD_LOOP_GRAPH                               */
+    int fft_unrolled;     /* 1 (default): transform passes unrolled per line length at compile
+                             time; 0: one looped pass body for every pass                       */
 } rd_opts;
 
 typedef struct {

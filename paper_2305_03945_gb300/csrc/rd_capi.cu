@@ -84,7 +84,7 @@ bool use_pingpong(int fft_buffers, int threads, int smem_inplace, int smem_pp) {
 // Launch shape for one precision.  Returns false when the grid does not fit.
 template <class T>
 bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int col_req, int dc, int fft_buffers,
-                 Desc& d, LaunchCfg& c, std::string& why) {
+                 int fft_unrolled, Desc& d, LaunchCfg& c, std::string& why) {
   if (fft_line_threads<T>(nx) > MaxThreads<T>::value || fft_line_threads<T>(ny) > MaxThreads<T>::value) {
     why = "grid side too long for this precision";
     return false;
@@ -160,6 +160,7 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     d.fft_pp |= 4;
     smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 1);
   }
+  if (fft_unrolled) d.fft_pp |= 8;
   c.smem_res = smem_res;
   c.smem_upd = smem_upd;
   c.smem_col = smem_col;
@@ -451,6 +452,7 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
     if (o->graph_k < 1 || o->graph_k > 256) return fail(RD_ERR_INVALID_ARG, "graph_k must be in [1, 256]");
     if (o->fft_buffers < 0 || o->fft_buffers > 2) return fail(RD_ERR_INVALID_ARG, "fft_buffers must be 0, 1 or 2");
     if (o->solve_loop != RD_LOOP_GRAPH && o->solve_loop != RD_LOOP_HOST) return fail(RD_ERR_INVALID_ARG, "bad solve_loop");
+    if (o->fft_unrolled != 0 && o->fft_unrolled != 1) return fail(RD_ERR_INVALID_ARG, "fft_unrolled must be 0 or 1");
     if (o->precision == RD_PREC_FP32_DC && (!(o->dc_inner_rtol > 0) || o->dc_max_outer < 1))
       return fail(RD_ERR_INVALID_ARG, "bad defect-correction options");
   }
@@ -504,11 +506,11 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
 
   std::string why;
   Desc d64 = base, d32 = base;
-  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 0, h->opts.fft_buffers, d64, h->cfg64, why))
+  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 0, h->opts.fft_buffers, h->opts.fft_unrolled, d64, h->cfg64, why))
     if (!h->dc) return fail(RD_ERR_UNSUPPORTED, "FP64 path: " + why);
   if (h->dc) {
     // the FP64 kernels of the defect-correction loop only need the band decomposition
-    if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 1, h->opts.fft_buffers, d32, h->cfg32, why))
+    if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 1, h->opts.fft_buffers, h->opts.fft_unrolled, d32, h->cfg32, why))
       return fail(RD_ERR_UNSUPPORTED, "FP32 path: " + why);
     d64.band_rows = d32.band_rows;
     d64.nbands = d32.nbands;
@@ -836,6 +838,7 @@ void rd_opts_default(rd_opts* o) {
   o->profile = 0;
   o->fft_buffers = 0;
   o->solve_loop = RD_LOOP_GRAPH;
+  o->fft_unrolled = 1;
 }
 
 rd_status rd_pdhg_create(rd_pdhg** out, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* reaction,

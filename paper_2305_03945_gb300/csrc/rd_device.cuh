@@ -290,11 +290,13 @@ __device__ __forceinline__ cx<T>* block_fft_c(cx<T>* buf, cx<T>* scr, int nlines
 // buf and scr (one barrier per pass), or in place when scr == buf (two barriers per pass, half
 // the shared memory).  Returns the buffer (buf or scr) that holds the result.
 // Called by every thread of the block (it contains barriers); needs nthreads >=
-// fft_line_threads<T>(N).  Lengths 64 .. 2048 run the compile-time specialised passes.
+// fft_line_threads<T>(N).  With `unrolled`, lengths 64 .. 2048 run passes specialised and
+// unrolled at compile time for that length; otherwise one looped pass body serves every pass
+// (fewer distinct instructions, more index arithmetic; measured slower on GB300).
 template <class T, int DIR>
 __device__ cx<T>* block_fft(cx<T>* buf, cx<T>* scr, int nlines, int logN, int ls, const cx<T>* __restrict__ tw,
-                            int tid, int nthreads) {
-  switch (logN) {
+                            int tid, int nthreads, bool unrolled) {
+  if (unrolled) switch (logN) {
     case 6: return block_fft_c<T, DIR, 6>(buf, scr, nlines, ls, tw, tid, nthreads);
     case 7: return block_fft_c<T, DIR, 7>(buf, scr, nlines, ls, tw, tid, nthreads);
     case 8: return block_fft_c<T, DIR, 8>(buf, scr, nlines, ls, tw, tid, nthreads);

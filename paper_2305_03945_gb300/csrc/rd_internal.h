@@ -38,7 +38,8 @@ struct Desc {
   int meas_div_dt;   // 1: stopping measure is sum ||F_c|| / dt, else sum ||F_c||
   int stall_window;  // > 0: stop (as converged) when the measure has not halved for this many updates
   int batched;       // 1: member of a batch (Slot control block, device-side phase machine)
-  int fft_pp;        // bit 0 k_res, bit 1 k_col, bit 2 k_upd: transforms ping-pong between two buffers
+  int fft_pp;        // bit 0 k_res, bit 1 k_col, bit 2 k_upd: transforms ping-pong between two buffers;
+                     // bit 3: size-specialised unrolled transform passes (else looped passes)
   double hx2, hy2;   // 1/h_x^2, 1/h_y^2
   double dt, a, b;
   double p[6];

@@ -475,7 +475,7 @@ __device__ __forceinline__ void res_body(const Desc& d, State* __restrict__ st, 
   // 3. forward row transform and its epilogue straight to global memory
   if (d.precond != 0) {
     __syncthreads();
-    const cx<T>* res = block_fft<T, -1>(buf, scr, nc * lpc, lognx, ls, tws, tid, nt);
+    const cx<T>* res = block_fft<T, -1>(buf, scr, nc * lpc, lognx, ls, tws, tid, nt, (d.fft_pp & 8) != 0);
     const int hn = nx >> 1, lh = lognx - 1;
     const cx<T>* dcx = dcs;
     for (int g = tid; g < ((nc * lpc) << lh); g += nt) {
@@ -572,7 +572,7 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
     }
   }
   __syncthreads();
-  cx<T>* cur = block_fft<T, -1>(buf, scr, nl, logny, ls, twy, tid, nt);
+  cx<T>* cur = block_fft<T, -1>(buf, scr, nl, logny, ls, twy, tid, nt, (d.fft_pp & 8) != 0);
   cx<T>* oth = cur == buf ? scr : buf;
   // forward epilogue and the spectral scaling 1 / (g_hat nx ny), in place
   for (int g = tid; g < (nl << lh); g += nt) {
@@ -593,7 +593,7 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
   }
   __syncthreads();
   if (per) {
-    cx<T>* c2 = block_fft<T, -1>(cur, oth, nl, logny, ls, twy, tid, nt);
+    cx<T>* c2 = block_fft<T, -1>(cur, oth, nl, logny, ls, twy, tid, nt, (d.fft_pp & 8) != 0);
     post_inplace(c2, nl, logny, ls, d.bc, dcy);
     __syncthreads();
 #pragma unroll 4
@@ -623,7 +623,7 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
       }
     }
     __syncthreads();
-    cx<T>* c2 = block_fft<T, 1>(cur, oth, nl, logny, ls, twy, tid, nt);
+    cx<T>* c2 = block_fft<T, 1>(cur, oth, nl, logny, ls, twy, tid, nt, (d.fft_pp & 8) != 0);
 #pragma unroll 4
     for (int g = tid; g < (ny << lnl); g += nt) {
       const int n = g >> lnl, m = g & (nl - 1);
@@ -746,7 +746,7 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
     }
     __syncthreads();
     if (d.precond != 0) {
-      buf = block_fft<T, -1>(buf0, scr, nl, lognx, ls, twx, tid, nt);
+      buf = block_fft<T, -1>(buf0, scr, nl, lognx, ls, twx, tid, nt, (d.fft_pp & 8) != 0);
       post_inplace(buf, nl, lognx, ls, bc, dcx);
       __syncthreads();
     }
@@ -775,7 +775,7 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
       }
     }
     __syncthreads();
-    buf = block_fft<T, 1>(buf0, scr, nl, lognx, ls, twx, tid, nt);
+    buf = block_fft<T, 1>(buf0, scr, nl, lognx, ls, twx, tid, nt, (d.fft_pp & 8) != 0);
     // undo the Makhoul reordering in place (slot n holds column mk_perm(n)), in chunks of lines
     // so that each thread holds at most 16 values between the two barriers
     {

@@ -47,7 +47,8 @@ class rd_opts(ctypes.Structure):
                 ("omega", ctypes.c_double), ("precision", ctypes.c_int),
                 ("dc_inner_rtol", ctypes.c_double), ("dc_max_outer", ctypes.c_int),
                 ("graph_k", ctypes.c_int), ("band_rows", ctypes.c_int), ("col_width", ctypes.c_int),
-                ("profile", ctypes.c_int), ("fft_buffers", ctypes.c_int), ("solve_loop", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("fft_buffers", ctypes.c_int), ("solve_loop", ctypes.c_int),
+                ("fft_unrolled", ctypes.c_int)]
 
 
 class rd_stats(ctypes.Structure):
@@ -162,7 +163,7 @@ def _check(status, ok=(RD_OK,)):
 
 
 def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_inner_rtol=1e-4,
-                 dc_max_outer=12, profile=0, fft_buffers=0, solve_loop="graph"):
+                 dc_max_outer=12, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1):
     """C structs for a ``workloads.Problem``."""
     g = rd_grid()
     g.ndim = 2
@@ -190,6 +191,7 @@ def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_i
     o.profile = profile
     o.fft_buffers = fft_buffers
     o.solve_loop = {"graph": 0, "host": 1}[solve_loop]
+    o.fft_unrolled = fft_unrolled
     return g, rx, pc, o
 
 
