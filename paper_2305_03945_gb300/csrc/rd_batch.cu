@@ -776,9 +776,10 @@ rd_status rd_batch_create(rd_batch** out, size_t hbm_budget_bytes, int max_slots
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  b->smem_sweep = std::max(res_smem_bytes<float>(1, kBatchBandRows, 2, kBatchMaxSide, 1, 0),
-                           std::max(lines_smem_bytes<float>((kBatchBandRows + 4) / 2, kBatchMaxSide, 0),
-                                    lines_smem_bytes<float>(kBatchColWidth / 2, kBatchMaxSide, 0)));
+  const int tabs = table_bytes<float>(kBatchMaxSide, true, true);
+  b->smem_sweep = std::max(res_smem_bytes<float>(1, kBatchBandRows, 2, kBatchMaxSide, 1, 0, tabs),
+                           std::max(lines_smem_bytes<float>((kBatchBandRows + 4) / 2, kBatchMaxSide, 0, tabs),
+                                    lines_smem_bytes<float>(kBatchColWidth / 2, kBatchMaxSide, 0, tabs)));
   if ((e = allow_batch_kernels<float, KK_NONE_LAP>(optin)) != cudaSuccess ||
       (e = allow_batch_kernels<float, KK_AC>(optin)) != cudaSuccess ||
       (e = allow_batch_kernels<float, KK_CH_IMPL>(optin)) != cudaSuccess ||

@@ -83,8 +83,11 @@ bool use_pingpong(int fft_buffers, int threads, int smem_inplace, int smem_pp) {
 
 // Launch shape for one precision.  Returns false when the grid does not fit.
 template <class T>
-bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int col_req, int dc, int fft_buffers,
-                 int fft_unrolled, Desc& d, LaunchCfg& c, std::string& why) {
+// stage_base: the residual kernel stages the defect-correction base rows (Cahn-Hilliard in FP32).
+bool plan_launch(int nx, int ny, int nc, int H, int transform, int neumann, int band_req, int col_req, int stage_base,
+                 int fft_buffers, int fft_unrolled, Desc& d, LaunchCfg& c, std::string& why) {
+  const int tabx = table_bytes<T>(nx, transform != 0, transform && neumann);  // k_res, k_upd
+  const int taby = table_bytes<T>(ny, true, neumann != 0);                    // k_col
   if (fft_line_threads<T>(nx) > MaxThreads<T>::value || fft_line_threads<T>(ny) > MaxThreads<T>::value) {
     why = "grid side too long for this precision";
     return false;
@@ -101,7 +104,7 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
       if (cand > ny) continue;
       const int nb = (ny + cand - 1) / cand;
       const int sm =
-          std::max(lines_smem_bytes<T>(nc * ((cand + 2 * H) / 2), nx, 0), res_smem_bytes<T>(nc, cand, H, nx, dc, 0));
+          std::max(lines_smem_bytes<T>(nc * ((cand + 2 * H) / 2), nx, 0, tabx), res_smem_bytes<T>(nc, cand, H, nx, stage_base, 0, tabx));
       if (sm > kSmemLimit) continue;
       if (nb >= kTargetBlocks || cand == 2) {
         B = cand;
@@ -110,8 +113,8 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     }
     if (B == 0) B = 2;
   }
-  int smem_res = res_smem_bytes<T>(nc, B, H, nx, dc, 0);
-  int smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 0);
+  int smem_res = res_smem_bytes<T>(nc, B, H, nx, stage_base, 0, tabx);
+  int smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 0, tabx);
   if (smem_upd > kSmemLimit || smem_res > kSmemLimit) {
     why = "row band does not fit in shared memory";
     return false;
@@ -128,12 +131,12 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
     C = cmin;
     for (int cand = cmin * 2; cand <= nx; cand *= 2) {
       if (nc * (nx / cand) < 2 * kTargetBlocks) break;
-      if (lines_smem_bytes<T>(cand / 2, ny, 0) > kSmemLimit / 2) break;
+      if (lines_smem_bytes<T>(cand / 2, ny, 0, taby) > kSmemLimit / 2) break;
 
       C = cand;
     }
   }
-  int smem_col = lines_smem_bytes<T>(C / 2, ny, 0);
+  int smem_col = lines_smem_bytes<T>(C / 2, ny, 0, taby);
   if (smem_col > kSmemLimit) {
     why = "column block does not fit in shared memory";
     return false;
@@ -148,17 +151,17 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int band_req, int
   c.thr_upd = band_threads<T>(nc * ((B + 2 * H) / 2), nx);
   c.thr_col = band_threads<T>(C / 2, ny);
   d.fft_pp = 0;
-  if (use_pingpong<T>(fft_buffers, c.thr_res, smem_res, res_smem_bytes<T>(nc, B, H, nx, dc, 1))) {
+  if (use_pingpong<T>(fft_buffers, c.thr_res, smem_res, res_smem_bytes<T>(nc, B, H, nx, stage_base, 1, tabx))) {
     d.fft_pp |= 1;
-    smem_res = res_smem_bytes<T>(nc, B, H, nx, dc, 1);
+    smem_res = res_smem_bytes<T>(nc, B, H, nx, stage_base, 1, tabx);
   }
-  if (use_pingpong<T>(fft_buffers, c.thr_col, smem_col, lines_smem_bytes<T>(C / 2, ny, 1))) {
+  if (use_pingpong<T>(fft_buffers, c.thr_col, smem_col, lines_smem_bytes<T>(C / 2, ny, 1, taby))) {
     d.fft_pp |= 2;
-    smem_col = lines_smem_bytes<T>(C / 2, ny, 1);
+    smem_col = lines_smem_bytes<T>(C / 2, ny, 1, taby);
   }
-  if (use_pingpong<T>(fft_buffers, c.thr_upd, smem_upd, lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 1))) {
+  if (use_pingpong<T>(fft_buffers, c.thr_upd, smem_upd, lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 1, tabx))) {
     d.fft_pp |= 4;
-    smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 1);
+    smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 1, tabx);
   }
   if (fft_unrolled) d.fft_pp |= 8;
   c.smem_res = smem_res;
@@ -506,11 +509,12 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
 
   std::string why;
   Desc d64 = base, d32 = base;
-  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 0, h->opts.fft_buffers, h->opts.fft_unrolled, d64, h->cfg64, why))
+  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, bc == RD_BC_NEUMANN, h->opts.band_rows, h->opts.col_width, 0, h->opts.fft_buffers, h->opts.fft_unrolled, d64, h->cfg64, why))
     if (!h->dc) return fail(RD_ERR_UNSUPPORTED, "FP64 path: " + why);
   if (h->dc) {
     // the FP64 kernels of the defect-correction loop only need the band decomposition
-    if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, h->opts.band_rows, h->opts.col_width, 1, h->opts.fft_buffers, h->opts.fft_unrolled, d32, h->cfg32, why))
+    if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, bc == RD_BC_NEUMANN, h->opts.band_rows, h->opts.col_width,
+                           rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT, h->opts.fft_buffers, h->opts.fft_unrolled, d32, h->cfg32, why))
       return fail(RD_ERR_UNSUPPORTED, "FP32 path: " + why);
     d64.band_rows = d32.band_rows;
     d64.nbands = d32.nbands;

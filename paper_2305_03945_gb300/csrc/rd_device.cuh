@@ -442,21 +442,32 @@ __device__ __forceinline__ T lap13(const F& f, int i, int j, T c, T hx2, T hy2) 
 // need twice the bytes per line) read them from global memory.
 template <class T> struct SmemTables { static constexpr bool value = sizeof(T) == 4; };
 
+// Entries of the twiddle table that transforms of length n read: w^k for k < n/2 only (a
+// radix-R pass, R <= 8, reads w^step, w^(2 step), w^(4 step) up to w^((R/2) step) with
+// step < n/R; see job_twiddles), rounded up to an even count so that what follows in shared
+// memory stays 16-byte aligned.
+__host__ __device__ inline int tw_entries(int n) { return n >= 4 ? n >> 1 : 2; }
+// Shared-memory bytes of the tables a sweep block loads: the half twiddle table (tw) and the
+// DCT rotation table of n entries (dc); none for FP64, whose tables stay in global memory.
 template <class T>
-__host__ __device__ inline int res_smem_bytes(int nc, int rows, int H, int nx, int dc, int pp) {
+__host__ __device__ inline int table_bytes(int n, bool tw, bool dc) {
+  if (!SmemTables<T>::value) return 0;
+  return ((tw ? tw_entries(n) : 0) + (dc ? n : 0)) * (int)sizeof(cx<T>);
+}
+
+template <class T>
+__host__ __device__ inline int res_smem_bytes(int nc, int rows, int H, int nx, int stage_base, int pp, int tabs) {
   const int ls = padded_len(nx);
-  const int tabs = SmemTables<T>::value ? 2 * nx * (int)sizeof(cx<T>) : 0;
   const int buf = nc * (rows >> 1) * ls * (int)sizeof(cx<T>) * (pp ? 2 : 1);
   const int stg = nc * (rows + 2 * H) * nx * (int)sizeof(T);
-  return tabs + buf + stg * (dc ? 2 : 1);
+  return tabs + buf + stg * (stage_base ? 2 : 1);
 }
 
 // Shared-memory bytes of a kernel holding `nlines` transform lines of length n plus the
 // twiddle and DCT rotation tables of that length.
 template <class T>
-__host__ __device__ inline int lines_smem_bytes(int nlines, int n, int pp) {
-  return ((SmemTables<T>::value ? 2 * n : 0) + nlines * padded_len(n) * (pp ? 2 : 1)) *
-         (int)sizeof(cx<T>);
+__host__ __device__ inline int lines_smem_bytes(int nlines, int n, int pp, int tabs) {
+  return tabs + nlines * padded_len(n) * (pp ? 2 : 1) * (int)sizeof(cx<T>);
 }
 
 // Copy n entries of a complex table from global to shared memory (called by the whole block).
@@ -473,11 +484,13 @@ __device__ __forceinline__ unsigned char* place_tables(unsigned char* smem, cons
                                                        const cx<T>*& dc) {
   if constexpr (SmemTables<T>::value) {
     cx<T>* t = reinterpret_cast<cx<T>*>(smem);
-    if (load_tw) load_table(t, static_cast<const cx<T>*>(tw_g), n);
-    if (load_dc) load_table(t + n, static_cast<const cx<T>*>(dc_g), n);
+    if (load_tw) load_table(t, static_cast<const cx<T>*>(tw_g), tw_entries(n));
     tw = t;
-    dc = t + n;
-    return smem + 2 * n * sizeof(cx<T>);
+    if (load_tw) t += tw_entries(n);
+    if (load_dc) load_table(t, static_cast<const cx<T>*>(dc_g), n);
+    dc = t;
+    if (load_dc) t += n;
+    return reinterpret_cast<unsigned char*>(t);
   } else {
     tw = static_cast<const cx<T>*>(tw_g);
     dc = static_cast<const cx<T>*>(dc_g);

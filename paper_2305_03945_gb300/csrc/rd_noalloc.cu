@@ -191,9 +191,9 @@ extern "C" RD_API rd_status rd_apply_precond_static(const rd_grid* grid, rd_bc b
   cfg.thr_res = threads(nc, nx);
   cfg.thr_upd = threads(nc, nx);
   cfg.thr_col = threads(1, ny);
-  cfg.smem_res = rd::res_smem_bytes<double>(nc, 2, 0, nx, 0, 0);
-  cfg.smem_upd = rd::lines_smem_bytes<double>(nc, nx, 0);
-  cfg.smem_col = rd::lines_smem_bytes<double>(1, ny, 0);
+  cfg.smem_res = rd::res_smem_bytes<double>(nc, 2, 0, nx, 0, 0, 0);
+  cfg.smem_upd = rd::lines_smem_bytes<double>(nc, nx, 0, 0);
+  cfg.smem_col = rd::lines_smem_bytes<double>(1, ny, 0, 0);
   cfg.transform = 1;
 
   cudaError_t e;

@@ -59,6 +59,21 @@ struct Rows {
   }
 };
 
+// Base values of the points of one vector group, held in registers (kinds whose residual reads
+// the defect-correction base state only at the point itself)
+template <class T>
+struct PtVals {
+  const T* v;
+  int j0;
+  __device__ __forceinline__ T operator()(int, int j) const { return v[j - j0]; }
+};
+
+// Does the defect-correction residual of kind K read the base state at neighbouring points
+// (Cahn-Hilliard: the Laplacian of the linearised chemical potential)?  Otherwise only at the
+// point itself, and the base rows are not staged in shared memory.
+template <int K>
+__host__ __device__ constexpr bool base_stencil() { return K == KK_CH_IMPL || K == KK_CH_SPLIT; }
+
 // P~ in the complex transform buffer: two rows per line (row a in .x, row b in .y)
 template <class T, bool EDGE>
 struct Pairs {
@@ -75,8 +90,8 @@ struct Pairs {
 //   plain (DC = false): X = U, r = rhs of the step (U^k plus the explicit / constant terms)
 //   DC    (DC = true) : X = d, B = u, r = F(u); returns F(u + d) = F(u) + A_lin d + N(u + d) - N(u)
 //                       with the nonlinear increment expanded so that no large terms cancel.
-template <class T, int K, bool DC, class A>
-__device__ __forceinline__ void residual_pt(const Desc& d, const A& x0, const A& x1, const A& b0, const A& b1,
+template <class T, int K, bool DC, class A, class B = A>
+__device__ __forceinline__ void residual_pt(const Desc& d, const A& x0, const A& x1, const B& b0, const B& b1,
                                             int i, int j, T r0, T r1, T* w) {
   const T hx2 = T(d.hx2), hy2 = T(d.hy2), dt = T(d.dt), a = T(d.a), b = T(d.b);
   const T c0 = x0(i, j);
@@ -339,18 +354,22 @@ __device__ __forceinline__ void post_inplace(cx<T>* buf, int nlines, int logN, i
 // ---------------------------------------------------------------------------------------
 template <class T, int K, bool EDGE, int W>
 __device__ __forceinline__ void res_group(const Desc& d, cx<T>* buf, const T* xs, const T* bs, int srows, int r,
-                                          int j0, const T* rr0, const T* rr1, int lpc, int ls, T* w0, T* w1) {
+                                          int j0, const T* rr0, const T* rr1, const T* pb0, const T* pb1, int lpc,
+                                          int ls, T* w0, T* w1) {
   constexpr bool PC = K == KK_PCONLY;
   constexpr bool DC = !PC && sizeof(T) == 4;
   constexpr int H = KT<K>::H;
   const Rows<T, EDGE> x0{xs, d.nx, d.bc}, x1{xs + srows * d.nx, d.nx, d.bc};
   const Rows<T, EDGE> b0{bs, d.nx, d.bc}, b1{bs + srows * d.nx, d.nx, d.bc};
+  const PtVals<T> v0{pb0, j0}, v1{pb1, j0};
 #pragma unroll
   for (int q = 0; q < W; ++q) {
     T w[2] = {T(0), T(0)};
     if constexpr (PC) {
       w[0] = x0(r, j0 + q);
       if (d.ncomp > 1) w[1] = x1(r, j0 + q);
+    } else if constexpr (DC && !base_stencil<K>()) {
+      residual_pt<T, K, DC>(d, x0, x1, v0, v1, H + r, j0 + q, rr0[q], KT<K>::two ? rr1[q] : T(0), w);
     } else {
       residual_pt<T, K, DC>(d, x0, x1, b0, b1, H + r, j0 + q, rr0[q], KT<K>::two ? rr1[q] : T(0), w);
     }
@@ -374,10 +393,13 @@ __device__ __forceinline__ void res_points(const Desc& d, cx<T>* buf, const T* x
   const bool transform = d.precond != 0;
   const int lw = W == 4 ? 2 : (W == 2 ? 1 : 0);
   const int lv = d.lognx - lw;
-  constexpr int G = 4;  // vector groups whose right-hand sides are loaded together
+  // defect-correction base values read at the point only (not staged in shared memory)
+  constexpr bool PTB = !PC && sizeof(T) == 4 && KT<K>::nonlinear && !base_stencil<K>();
+  const T* Bg = static_cast<const T*>(d.base);
+  constexpr int G = PTB ? 2 : 4;  // vector groups whose right-hand sides are loaded together
   const int total = rows << lv;
   for (int base = 0; base < total; base += G * blockDim.x) {
-   T rrg0[G][W], rrg1[G][W];
+   T rrg0[G][W], rrg1[G][W], pbg0[G][W], pbg1[G][W];
    if constexpr (!PC) {
 #pragma unroll
     for (int q = 0; q < G; ++q) {
@@ -386,6 +408,10 @@ __device__ __forceinline__ void res_points(const Desc& d, cx<T>* buf, const T* x
         const size_t o = (size_t)(y0 + (v >> lv)) * nx + (v & ((1 << lv) - 1)) * W;
         vld<T, W>(R + o, rrg0[q]);
         if constexpr (KT<K>::two) vld<T, W>(R + plane + o, rrg1[q]);
+        if constexpr (PTB) {
+          vld<T, W>(Bg + o, pbg0[q]);
+          if constexpr (KT<K>::two) vld<T, W>(Bg + plane + o, pbg1[q]);
+        }
       }
     }
    }
@@ -399,9 +425,9 @@ __device__ __forceinline__ void res_points(const Desc& d, cx<T>* buf, const T* x
     const T* rr1 = rrg1[q];
     T w0[W], w1[W];
     if (j0 >= 2 && j0 + W + 2 <= nx)
-      res_group<T, K, false, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, lpc, ls, w0, w1);
+      res_group<T, K, false, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, pbg0[q], pbg1[q], lpc, ls, w0, w1);
     else
-      res_group<T, K, true, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, lpc, ls, w0, w1);
+      res_group<T, K, true, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, pbg0[q], pbg1[q], lpc, ls, w0, w1);
 #pragma unroll
     for (int q = 0; q < W; ++q) {
       acc0 += w0[q] * w0[q];
@@ -461,7 +487,7 @@ __device__ __forceinline__ void res_body(const Desc& d, State* __restrict__ st, 
   T* bs = xs + nc * srows * nx;
   const T* X = static_cast<const T*>(d.X);
   for (int c = 0; c < nc; ++c) stage_rows<T>(xs + c * srows * nx, X + c * plane, nx, lognx, ny, bc, y0 - H, srows);
-  if constexpr (DC && KT<K>::nonlinear) {
+  if constexpr (DC && base_stencil<K>()) {
     const T* Bg = static_cast<const T*>(d.base);
     for (int c = 0; c < nc; ++c) stage_rows<T>(bs + c * srows * nx, Bg + c * plane, nx, lognx, ny, bc, y0 - H, srows);
   }
