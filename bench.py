@@ -313,7 +313,8 @@ def run_ours(args, rank, world, local_rank):
     # ---- chosen form: FP32 sweeps + FP64 defect correction ----
     u = torch.from_numpy(w.u0.copy()).to(dev)
     tune = dict(band_rows=args.band_rows, col_width=args.col_width, graph_k=args.graph_k,
-                fft_buffers=args.fft_buffers, solve_loop=args.solve_loop, fft_unrolled=args.fft_unrolled)
+                fft_buffers=args.fft_buffers, solve_loop=args.solve_loop, fft_unrolled=args.fft_unrolled,
+                autotune=args.autotune)
     sv = rd.Solver(pb, precision=args.precision, profile=1, **tune)
     with ClockSampler(local_rank) as clk:
         tot_ms, its, infos = timed_steps(sv, u, args.steps, args.warmup)
@@ -430,7 +431,10 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "iterations_per_step": its / args.steps,
                    "residual_passes_per_step": st["residual_passes"] / args.steps,
-                   "band_rows": args.band_rows, "col_width": args.col_width, "graph_k": args.graph_k,
+                   "band_rows": st["plan_band_rows"], "col_width": st["plan_col_width"],
+                   "tiles": "autotuned at create" if (args.autotune and not args.band_rows and not args.col_width)
+                            else ("given" if (args.band_rows or args.col_width) else "planner"),
+                   "graph_k": args.graph_k,
                    "fft_buffers": args.fft_buffers, "solve_loop": args.solve_loop,
                    "fft_unrolled": args.fft_unrolled},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "parity_full_size": parity, "fp64_plain": fp64,
@@ -460,6 +464,8 @@ def main():
     ap.add_argument("--solve-loop", default="graph", choices=("graph", "host"),
                     help="PDHG loop: WHILE node of the step graph, or host-relaunched plain graphs "
                          "(for profilers, which cannot attribute kernels inside conditional nodes)")
+    ap.add_argument("--autotune", type=int, default=1, choices=(0, 1),
+                    help="1: time the candidate tile shapes at create and keep the fastest")
     ap.add_argument("--fft-unrolled", type=int, default=1, choices=(0, 1),
                     help="1: transform passes unrolled per line length; 0: looped passes")
     ap.add_argument("--fft-buffers", type=int, default=0, choices=(0, 1, 2),

@@ -149,6 +149,11 @@ typedef struct {
     int solve_loop;       /* rd_solve_loop, default RD_LOOP_GRAPH                               */
     int fft_unrolled;     /* 1 (default): transform passes unrolled per line length at compile
                              time; 0: one looped pass body for every pass                       */
+    int autotune;         /* 1: at create, time a few PDHG iterations of every (band rows, column
+                             width) pair that fits and keep the fastest (ignored when band_rows
+                             or col_width is set); 0 (default): the occupancy-based planner.
+                             Timing noise can change the choice between runs, and with it the
+                             summation order of the stopping norm (results agree to rounding). */
 } rd_opts;
 
 typedef struct {
@@ -169,6 +174,8 @@ typedef struct {
     long long host_syncs;        /* device -> host status reads                                 */
     double kernel_ms[3];         /* profile = 1: summed CUDA-event time of k_res, k_col, k_upd   */
     long long kernel_samples[3]; /* number of timed launches behind kernel_ms                    */
+    int plan_band_rows;          /* rows per CTA of the sweeps chosen at create (planner/autotune) */
+    int plan_col_width;          /* columns per CTA of the column transform chosen at create      */
 } rd_stats;
 
 typedef struct rd_pdhg rd_pdhg;

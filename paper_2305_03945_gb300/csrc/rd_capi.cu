@@ -456,9 +456,99 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
     if (o->fft_buffers < 0 || o->fft_buffers > 2) return fail(RD_ERR_INVALID_ARG, "fft_buffers must be 0, 1 or 2");
     if (o->solve_loop != RD_LOOP_GRAPH && o->solve_loop != RD_LOOP_HOST) return fail(RD_ERR_INVALID_ARG, "bad solve_loop");
     if (o->fft_unrolled != 0 && o->fft_unrolled != 1) return fail(RD_ERR_INVALID_ARG, "fft_unrolled must be 0 or 1");
+    if (o->autotune != 0 && o->autotune != 1) return fail(RD_ERR_INVALID_ARG, "autotune must be 0 or 1");
     if (o->precision == RD_PREC_FP32_DC && (!(o->dc_inner_rtol > 0) || o->dc_max_outer < 1))
       return fail(RD_ERR_INVALID_ARG, "bad defect-correction options");
   }
+  return RD_OK;
+}
+
+// opts.autotune: time kTuneIters PDHG iterations of every (band rows, column width) pair that the
+// planner accepts and that fits the device's shared memory, on the handle's own arrays (zeroed,
+// with a solve state that never stops, so that every candidate runs the full sweeps), and keep
+// the fastest.  The chosen pair is reported in rd_stats.plan_band_rows / plan_col_width.
+constexpr int kTuneIters = 4;
+
+template <class T>
+rd_status autotune_plan(rd_pdhg* h, int H, int transform, int stage_base, int usable) {
+  const int ti = h->dc ? 1 : 0;
+  cudaStream_t s = h->stream;
+  const size_t n = h->npts;
+  if (h->dc) {
+    for (void* p : {(void*)h->D32, (void*)h->P32[0], (void*)h->P32[1], (void*)h->WY32, (void*)h->r32, (void*)h->u32})
+      RD_CUDA(cudaMemsetAsync(p, 0, n * sizeof(float), s));
+  } else {
+    for (void* p : {(void*)h->U64, (void*)h->rhs64, (void*)h->P64[0], (void*)h->P64[1], (void*)h->WY64})
+      RD_CUDA(cudaMemsetAsync(p, 0, n * sizeof(double), s));
+  }
+  State run{};
+  run.status = ST_ACTIVE;
+  run.max_iter = 1 << 30;
+  run.thresh = -1.0;  // never met: the sweeps stay active
+  State* dst = h->d_state + 2;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RD_CUDA(cudaEventCreate(&e0));
+  RD_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bestB = 0, bestC = 0;
+  std::string why;
+  for (int B = 2; B <= 16 && B <= h->ny; B *= 2) {
+    for (int Cw = 2; Cw <= 64 && Cw <= h->nx; Cw *= 2) {
+      if (h->nx % Cw) continue;
+      Desc dt = h->h_desc[ti];
+      LaunchCfg ct{};
+      if (!plan_launch<T>(h->nx, h->ny, h->nc, H, transform, h->bc == RD_BC_NEUMANN, B, Cw, stage_base,
+                          h->opts.fft_buffers, h->opts.fft_unrolled, dt, ct, why))
+        continue;
+      if (std::max(ct.smem_res, std::max(ct.smem_col, ct.smem_upd)) > usable) continue;
+      float ms = 0.f;
+      bool ok = true;
+      for (int rep = 0; rep < 2 && ok; ++rep) {
+        RD_CUDA(cudaMemcpyAsync(dst, &run, sizeof(State), cudaMemcpyHostToDevice, s));
+        ok = launch_iteration<T>(dt, dst, ct, s, nullptr) == cudaSuccess;  // warm-up
+        RD_CUDA(cudaEventRecord(e0, s));
+        for (int k = 0; k < kTuneIters && ok; ++k) ok = launch_iteration<T>(dt, dst, ct, s, nullptr) == cudaSuccess;
+        RD_CUDA(cudaEventRecord(e1, s));
+        RD_CUDA(cudaStreamSynchronize(s));
+        float t = 0.f;
+        RD_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        if (rep == 0 || t < ms) ms = t;
+      }
+      if (!ok) {
+        cudaGetLastError();
+        continue;
+      }
+      if (ms < best) {
+        best = ms;
+        bestB = B;
+        bestC = Cw;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (bestB == 0) return RD_OK;  // nothing measured: keep the planner's choice
+  Desc& d = h->h_desc[ti];
+  LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
+  if (!plan_launch<T>(h->nx, h->ny, h->nc, H, transform, h->bc == RD_BC_NEUMANN, bestB, bestC, stage_base,
+                      h->opts.fft_buffers, h->opts.fft_unrolled, d, lc, why))
+    return fail(RD_ERR_CUDA, "autotune: re-planning the chosen tiles failed: " + why);
+  if (h->dc) {
+    h->h_desc[0].band_rows = d.band_rows;
+    h->h_desc[0].nbands = d.nbands;
+    h->h_desc[0].col_width = d.col_width;
+    h->h_desc[0].ncolblk = d.ncolblk;
+  } else {
+    h->cfgpc = lc;
+    const Desc& d0 = h->h_desc[0];
+    Desc& dp = h->h_desc[2];
+    dp.band_rows = d0.band_rows;
+    dp.nbands = d0.nbands;
+    dp.col_width = d0.col_width;
+    dp.ncolblk = d0.ncolblk;
+    dp.fft_pp = d0.fft_pp;
+  }
+  RD_CUDA(cudaMemcpy(h->d_desc, h->h_desc, 3 * sizeof(Desc), cudaMemcpyHostToDevice));
   return RD_OK;
 }
 
@@ -526,7 +616,9 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   RD_TRY(dalloc(h, &h->U64, n * sizeof(double)));
   RD_TRY(dalloc(h, &h->rhs64, n * sizeof(double)));
   const int nb = std::max(d64.nbands, d32.nbands);
-  RD_TRY(dalloc(h, &h->partials, (size_t)2 * std::max(std::max(nb, point_blocks(h->nx, h->ny)), 1) * sizeof(double)));
+  // partials: per band (any band height the autotuner may try) or per step-kernel block
+  const int nb_any = std::max(nb, h->ny / 2 + 1);
+  RD_TRY(dalloc(h, &h->partials, (size_t)2 * std::max(std::max(nb_any, point_blocks(h->nx, h->ny)), 1) * sizeof(double)));
   RD_TRY(dalloc(h, &h->d_desc, 3 * sizeof(Desc)));
   RD_TRY(dalloc(h, &h->d_state, 3 * sizeof(State)));
   RD_CUDA(cudaMallocHost(&h->h_state, 3 * sizeof(State)));
@@ -639,6 +731,13 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
   if (std::max(lc.smem_res, std::max(lc.smem_col, lc.smem_upd)) > usable)
     return fail(RD_ERR_UNSUPPORTED, "the grid needs more shared memory per block than this device offers");
+  if (h->opts.autotune && h->opts.band_rows == 0 && h->opts.col_width == 0) {
+    const int stage_base = h->dc && (rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT);
+    RD_TRY(h->dc ? autotune_plan<float>(h, H, transform, stage_base, usable)
+                 : autotune_plan<double>(h, H, transform, stage_base, usable));
+  }
+  h->stats.plan_band_rows = h->h_desc[h->dc ? 1 : 0].band_rows;
+  h->stats.plan_col_width = h->h_desc[h->dc ? 1 : 0].col_width;
   RD_TRY(capture_graphs(h));
   RD_CUDA(cudaDeviceSynchronize());
   return RD_OK;
@@ -843,6 +942,7 @@ void rd_opts_default(rd_opts* o) {
   o->fft_buffers = 0;
   o->solve_loop = RD_LOOP_GRAPH;
   o->fft_unrolled = 1;
+  o->autotune = 0;
 }
 
 rd_status rd_pdhg_create(rd_pdhg** out, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* reaction,
@@ -948,7 +1048,10 @@ rd_status rd_pdhg_get_stats(const rd_pdhg* h, rd_stats* out) {
 
 rd_status rd_pdhg_reset_stats(rd_pdhg* h) {
   if (!h) return fail(RD_ERR_INVALID_ARG, "NULL handle");
+  const int pb = h->stats.plan_band_rows, pc = h->stats.plan_col_width;
   h->stats = rd_stats{};
+  h->stats.plan_band_rows = pb;
+  h->stats.plan_col_width = pc;
   return RD_OK;
 }
 

@@ -372,3 +372,22 @@ def test_transform_pass_forms_match_oracle(fft_unrolled, bc):
     U, info, U_ref, _ = _compare_step(pb, uk, precision="fp32_dc", fft_unrolled=fft_unrolled)
     assert info["status"] == 0, info
     assert np.linalg.norm(U - U_ref) <= 1e-9 * np.linalg.norm(U_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dc"])
+def test_autotuned_tiles_match_oracle(precision):
+    """The autotuner times the candidate tile shapes at create and keeps one that fits; the step
+    it then takes matches the oracle within the usual tolerances."""
+    rd = _rd()
+    pb = _problem("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06), "periodic", 64, 128)
+    uk = _state(pb, 16)
+    U_ref, info_ref = O.pdhg_step(pb, uk)
+    with rd.Solver(pb, precision=precision, autotune=1) as s:
+        st = s.stats()
+        assert st["plan_band_rows"] in (2, 4, 8, 16) and st["plan_col_width"] in (2, 4, 8, 16, 32, 64)
+        out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        info = s.step(dev(uk), out)
+        U = host(out)
+    assert info["status"] == 0, info
+    tol = 1e-10 if precision == "fp64" else 1e-9
+    assert np.linalg.norm(U - U_ref) <= tol * np.linalg.norm(U_ref)
