@@ -424,10 +424,8 @@ __device__ __forceinline__ void res_points(const Desc& d, cx<T>* buf, const T* x
     const T* rr0 = rrg0[q];
     const T* rr1 = rrg1[q];
     T w0[W], w1[W];
-    if (j0 >= 2 && j0 + W + 2 <= nx)
-      res_group<T, K, false, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, pbg0[q], pbg1[q], lpc, ls, w0, w1);
-    else
-      res_group<T, K, true, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, pbg0[q], pbg1[q], lpc, ls, w0, w1);
+    // boundary-mapped columns everywhere (one copy of the residual code; see upd_points)
+    res_group<T, K, true, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, pbg0[q], pbg1[q], lpc, ls, w0, w1);
 #pragma unroll
     for (int q = 0; q < W; ++q) {
       acc0 += w0[q] * w0[q];
@@ -698,7 +696,8 @@ __device__ __forceinline__ void upd_points(const Desc& d, const cx<T>* buf, int 
   const T* Bs = static_cast<const T*>(d.base);
   const int lw = W == 4 ? 2 : (W == 2 ? 1 : 0);
   const int lv = d.lognx - lw;
-  constexpr int G = KT<K>::two ? 2 : 4;  // vector groups loaded together
+  constexpr int G = 1;  // one vector group per trip: more unrolled groups cost more in
+                        // instruction fetch than they gained in loads in flight (measured)
   const int total = rows << lv;
   for (int base = 0; base < total; base += G * blockDim.x) {
     T xa[G][W], xb[G][W], sa[G][W], sb[G][W];
@@ -721,8 +720,9 @@ __device__ __forceinline__ void upd_points(const Desc& d, const cx<T>* buf, int 
       if (v >= total) break;
       const int r = v >> lv, j0 = (v & ((1 << lv) - 1)) * W;
       const size_t o = (size_t)(y0 + r) * nx + j0;
-      if (j0 >= 2 && j0 + W + 2 <= nx) upd_group<T, K, false, W>(d, buf, ls, lpc, H + r, j0, xa[q], xb[q], sa[q], sb[q]);
-      else upd_group<T, K, true, W>(d, buf, ls, lpc, H + r, j0, xa[q], xb[q], sa[q], sb[q]);
+      // boundary-mapped columns everywhere: one copy of the gradient code, not an interior and
+      // an edge copy (the smaller kernel is faster: instruction fetch dominates its stalls)
+      upd_group<T, K, true, W>(d, buf, ls, lpc, H + r, j0, xa[q], xb[q], sa[q], sb[q]);
       vst<T, W>(X + o, xa[q]);
       if constexpr (KT<K>::two) vst<T, W>(X + plane + o, xb[q]);
     }
