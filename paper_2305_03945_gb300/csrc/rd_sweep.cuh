@@ -849,7 +849,7 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
     const T* Pin = static_cast<const T*>(d.P[(n - 1) & 1]);
     T* Pout = static_cast<T*>(d.P[n & 1]);
     const T tp = T(d.tau_p), tpe = T((1.0 + d.omega) * d.tau_p);
-    constexpr int G = 8;  // slot pairs whose P values are loaded together
+    constexpr int G = 2;  // slot pairs whose P values are loaded together (2: measured best)
     const int totalp = nl << lh;
     for (int base = 0; base < totalp; base += G * nt) {
      cx<T> pag[G], pbg[G];
