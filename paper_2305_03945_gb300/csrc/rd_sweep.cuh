@@ -757,7 +757,9 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
   const int hn = nx >> 1, lh = lognx - 1;
   if (SmemTables<T>::value && d.precond != 0 && bc == BC_NEUMANN) __syncthreads();
 
-  // 1. Y on rows y0-H .. y0+rows+H-1 (boundary-mapped) into buf, two rows per line
+  // 1. Y on rows y0-H .. y0+rows+H-1 (boundary-mapped) into buf, two rows per line.  Both
+  //    boundary kinds use the same (forward) transform call: the Neumann input is the conjugated
+  //    DCT-III preparation, and the conjugate of its forward transform is the inverse transform.
   if (d.precond == 0 || bc == BC_PERIODIC) {
 #pragma unroll 2
     for (int g = tid; g < (nl << lh); g += nt) {
@@ -769,12 +771,6 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
       const cx<T> b = *reinterpret_cast<const cx<T>*>(Wc + (size_t)gb * nx + j);
       buf0[line * ls + pidx(j)] = cx<T>{a.x, b.x};
       buf0[line * ls + pidx(j + 1)] = cx<T>{a.y, b.y};
-    }
-    __syncthreads();
-    if (d.precond != 0) {
-      buf = block_fft<T, -1>(buf0, scr, nl, lognx, ls, twx, tid, nt, (d.fft_pp & 8) != 0);
-      post_inplace(buf, nl, lognx, ls, bc, dcx);
-      __syncthreads();
     }
   } else {
     for (int g = tid; g < (nl << lh); g += nt) {
@@ -792,18 +788,25 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
         const cx<T> wm = dcx[hn];
         cx<T> zm, zmp;
         dct_inv_pre(Xm, Xm, wm.x, wm.y, zm, zmp);
-        L[pidx(0)] = zk;
-        L[pidx(hn)] = zm;
+        L[pidx(0)] = cx<T>{zk.x, -zk.y};
+        L[pidx(hn)] = cx<T>{zm.x, -zm.y};
       } else {
         dct_inv_pre(cx<T>{Wa[k], Wb[k]}, cx<T>{Wa[nx - k], Wb[nx - k]}, w.x, w.y, zk, zkp);
-        L[pidx(k)] = zk;
-        L[pidx(nx - k)] = zkp;
+        L[pidx(k)] = cx<T>{zk.x, -zk.y};
+        L[pidx(nx - k)] = cx<T>{zkp.x, -zkp.y};
       }
     }
-    __syncthreads();
-    buf = block_fft<T, 1>(buf0, scr, nl, lognx, ls, twx, tid, nt, (d.fft_pp & 8) != 0);
-    // undo the Makhoul reordering in place (slot n holds column mk_perm(n)), in chunks of lines
-    // so that each thread holds at most 16 values between the two barriers
+  }
+  __syncthreads();
+  if (d.precond != 0) {
+    buf = block_fft<T, -1>(buf0, scr, nl, lognx, ls, twx, tid, nt, (d.fft_pp & 8) != 0);
+    if (bc == BC_PERIODIC) {
+      post_inplace(buf, nl, lognx, ls, bc, dcx);
+      __syncthreads();
+    } else {
+    // undo the conjugation and the Makhoul reordering in place (slot n holds column
+    // mk_perm(n)), in chunks of lines so that each thread holds at most 16 values between the
+    // two barriers
     {
       constexpr int MAXV = 16;
       int chunk = (nt * MAXV) >> lognx;
@@ -816,7 +819,10 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
 #pragma unroll
         for (int s = 0; s < MAXV; ++s) {
           const int g = tid + s * nthr;
-          if (tid < nthr && g < total) v[s] = buf[(l0 + (g >> lognx)) * ls + pidx(g & (nx - 1))];
+          if (tid < nthr && g < total) {
+            const cx<T> e = buf[(l0 + (g >> lognx)) * ls + pidx(g & (nx - 1))];
+            v[s] = cx<T>{e.x, -e.y};
+          }
         }
         __syncthreads();
 #pragma unroll
@@ -827,6 +833,7 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
         }
         __syncthreads();
       }
+    }
     }
   }
 
