@@ -616,16 +616,9 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
     L[pidx(k2)] = cx<T>{okp.x * sym(ma + m2), okp.y * sym(mb + m2)};
   }
   __syncthreads();
-  if (per) {
-    cx<T>* c2 = block_fft<T, -1>(cur, oth, nl, logny, ls, twy, tid, nt, (d.fft_pp & 8) != 0);
-    post_inplace(c2, nl, logny, ls, d.bc, dcy);
-    __syncthreads();
-#pragma unroll 4
-    for (int g = tid; g < (ny << lnl); g += nt) {
-      const int row = g >> lnl, m = g & (nl - 1);
-      *reinterpret_cast<cx<T>*>(WY + (size_t)row * nx + x0 + 2 * m) = c2[m * ls + pidx(row)];
-    }
-  } else {
+  // The second transform is one forward call for both boundary kinds: the Neumann inverse is
+  // the conjugate of the forward transform of the conjugated DCT-III preparation.
+  if (!per) {
     for (int g = tid; g < (nl << lh); g += nt) {
       const int m = g >> lh, k = g & (hn - 1);
       cx<T>* L = cur + m * ls;
@@ -638,20 +631,31 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
         const cx<T> wm = dcy[hn];
         cx<T> zm, zmp;
         dct_inv_pre(Xm, Xm, wm.x, wm.y, zm, zmp);
-        L[pidx(0)] = zk;
-        L[pidx(hn)] = zm;
+        L[pidx(0)] = cx<T>{zk.x, -zk.y};
+        L[pidx(hn)] = cx<T>{zm.x, -zm.y};
       } else {
         dct_inv_pre(L[pidx(k)], L[pidx(ny - k)], w.x, w.y, zk, zkp);
-        L[pidx(k)] = zk;
-        L[pidx(ny - k)] = zkp;
+        L[pidx(k)] = cx<T>{zk.x, -zk.y};
+        L[pidx(ny - k)] = cx<T>{zkp.x, -zkp.y};
       }
     }
     __syncthreads();
-    cx<T>* c2 = block_fft<T, 1>(cur, oth, nl, logny, ls, twy, tid, nt, (d.fft_pp & 8) != 0);
+  }
+  cx<T>* y2 = block_fft<T, -1>(cur, oth, nl, logny, ls, twy, tid, nt, (d.fft_pp & 8) != 0);
+  if (per) {
+    post_inplace(y2, nl, logny, ls, d.bc, dcy);
+    __syncthreads();
+#pragma unroll 4
+    for (int g = tid; g < (ny << lnl); g += nt) {
+      const int row = g >> lnl, m = g & (nl - 1);
+      *reinterpret_cast<cx<T>*>(WY + (size_t)row * nx + x0 + 2 * m) = y2[m * ls + pidx(row)];
+    }
+  } else {
 #pragma unroll 4
     for (int g = tid; g < (ny << lnl); g += nt) {
       const int n = g >> lnl, m = g & (nl - 1);
-      *reinterpret_cast<cx<T>*>(WY + (size_t)mk_perm(n, ny) * nx + x0 + 2 * m) = c2[m * ls + pidx(n)];
+      const cx<T> v = y2[m * ls + pidx(n)];
+      *reinterpret_cast<cx<T>*>(WY + (size_t)mk_perm(n, ny) * nx + x0 + 2 * m) = cx<T>{v.x, -v.y};
     }
   }
 }
