@@ -431,7 +431,8 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "iterations_per_step": its / args.steps,
                    "residual_passes_per_step": st["residual_passes"] / args.steps,
-                   "band_rows": st["plan_band_rows"], "col_width": st["plan_col_width"],
+                   "band_rows": st["plan_band_rows"], "upd_rows": st["plan_upd_rows"],
+                   "col_width": st["plan_col_width"],
                    "tiles": "autotuned at create" if (args.autotune and not args.band_rows and not args.col_width)
                             else ("given" if (args.band_rows or args.col_width) else "planner"),
                    "graph_k": args.graph_k,

@@ -139,8 +139,11 @@ typedef struct {
     int dc_max_outer;     /* DC outer rounds per step, default 12                                */
     int graph_k;          /* PDHG iterations per trip of the device-side loop (a WHILE node of the
                              step's CUDA graph), default 2                                      */
-    int band_rows;        /* rows per CTA of the stencil sweeps; 0 = autotuned                   */
-    int col_width;        /* columns per CTA of the column transform; 0 = autotuned              */
+    int band_rows;        /* rows per CTA of the stencil sweeps (k_res and k_upd); 0 = chosen at
+                             create (occupancy planner, or measured with autotune)              */
+    int col_width;        /* columns per CTA of the column transform; 0 = chosen at create      */
+    int upd_rows;         /* rows per CTA of the update sweep k_upd when it differs from k_res;
+                             0 (default) = band_rows                                            */
     int profile;          /* 1: time the three PDHG kernels of the first iteration of every graph
                              launch with CUDA events (read back by rd_pdhg_get_stats)            */
     int fft_buffers;      /* shared-memory transforms: 0 = chosen per kernel (two buffers where the
@@ -149,8 +152,9 @@ typedef struct {
     int solve_loop;       /* rd_solve_loop, default RD_LOOP_GRAPH                               */
     int fft_unrolled;     /* 1 (default): transform passes unrolled per line length at compile
                              time; 0: one looped pass body for every pass                       */
-    int autotune;         /* 1: at create, time a few PDHG iterations of every (band rows, column
-                             width) pair that fits and keep the fastest (ignored when band_rows
+    int autotune;         /* 1: at create, time each sweep kernel over a few PDHG iterations at
+                             every tile that fits and keep the fastest per kernel (band rows of
+                             k_res and of k_upd, column width of k_col; ignored when band_rows
                              or col_width is set); 0 (default): the occupancy-based planner.
                              Timing noise can change the choice between runs, and with it the
                              summation order of the stopping norm (results agree to rounding). */
@@ -176,6 +180,7 @@ typedef struct {
     long long kernel_samples[3]; /* number of timed launches behind kernel_ms                    */
     int plan_band_rows;          /* rows per CTA of the sweeps chosen at create (planner/autotune) */
     int plan_col_width;          /* columns per CTA of the column transform chosen at create      */
+    int plan_upd_rows;           /* rows per CTA of the update sweep (k_upd) chosen at create    */
 } rd_stats;
 
 typedef struct rd_pdhg rd_pdhg;

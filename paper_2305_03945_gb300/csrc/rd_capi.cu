@@ -84,8 +84,9 @@ bool use_pingpong(int fft_buffers, int threads, int smem_inplace, int smem_pp) {
 // Launch shape for one precision.  Returns false when the grid does not fit.
 template <class T>
 // stage_base: the residual kernel stages the defect-correction base rows (Cahn-Hilliard in FP32).
-bool plan_launch(int nx, int ny, int nc, int H, int transform, int neumann, int band_req, int col_req, int stage_base,
-                 int fft_buffers, int fft_unrolled, Desc& d, LaunchCfg& c, std::string& why) {
+// band_req: rows per CTA of k_res (0: planner); upd_req: rows per CTA of k_upd (0: as k_res).
+bool plan_launch(int nx, int ny, int nc, int H, int transform, int neumann, int band_req, int col_req, int upd_req,
+                 int stage_base, int fft_buffers, int fft_unrolled, Desc& d, LaunchCfg& c, std::string& why) {
   const int tabx = table_bytes<T>(nx, transform != 0, transform && neumann);  // k_res, k_upd
   const int taby = table_bytes<T>(ny, true, neumann != 0);                    // k_col
   if (fft_line_threads<T>(nx) > MaxThreads<T>::value || fft_line_threads<T>(ny) > MaxThreads<T>::value) {
@@ -113,8 +114,13 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int neumann, int 
     }
     if (B == 0) B = 2;
   }
+  const int U = upd_req > 0 ? upd_req : B;  // k_upd band rows
+  if (U % 2 || U > ny) {
+    why = "k_upd band rows must be even and <= ny";
+    return false;
+  }
   int smem_res = res_smem_bytes<T>(nc, B, H, nx, stage_base, 0, tabx);
-  int smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 0, tabx);
+  int smem_upd = lines_smem_bytes<T>(nc * ((U + 2 * H) / 2), nx, 0, tabx);
   if (smem_upd > kSmemLimit || smem_res > kSmemLimit) {
     why = "row band does not fit in shared memory";
     return false;
@@ -145,10 +151,13 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int neumann, int 
   d.nbands = (ny + B - 1) / B;
   d.col_width = C;
   d.ncolblk = nx / C;
+  d.upd_rows = U;
+  d.nupd = (ny + U - 1) / U;
   c.grid_bands = d.nbands;
+  c.grid_upd = d.nupd;
   c.grid_cols = nc * d.ncolblk;
   c.thr_res = band_threads<T>(nc * (B / 2), nx);
-  c.thr_upd = band_threads<T>(nc * ((B + 2 * H) / 2), nx);
+  c.thr_upd = band_threads<T>(nc * ((U + 2 * H) / 2), nx);
   c.thr_col = band_threads<T>(C / 2, ny);
   d.fft_pp = 0;
   if (use_pingpong<T>(fft_buffers, c.thr_res, smem_res, res_smem_bytes<T>(nc, B, H, nx, stage_base, 1, tabx))) {
@@ -159,9 +168,9 @@ bool plan_launch(int nx, int ny, int nc, int H, int transform, int neumann, int 
     d.fft_pp |= 2;
     smem_col = lines_smem_bytes<T>(C / 2, ny, 1, taby);
   }
-  if (use_pingpong<T>(fft_buffers, c.thr_upd, smem_upd, lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 1, tabx))) {
+  if (use_pingpong<T>(fft_buffers, c.thr_upd, smem_upd, lines_smem_bytes<T>(nc * ((U + 2 * H) / 2), nx, 1, tabx))) {
     d.fft_pp |= 4;
-    smem_upd = lines_smem_bytes<T>(nc * ((B + 2 * H) / 2), nx, 1, tabx);
+    smem_upd = lines_smem_bytes<T>(nc * ((U + 2 * H) / 2), nx, 1, tabx);
   }
   if (fft_unrolled) d.fft_pp |= 8;
   c.smem_res = smem_res;
@@ -457,16 +466,19 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
     if (o->solve_loop != RD_LOOP_GRAPH && o->solve_loop != RD_LOOP_HOST) return fail(RD_ERR_INVALID_ARG, "bad solve_loop");
     if (o->fft_unrolled != 0 && o->fft_unrolled != 1) return fail(RD_ERR_INVALID_ARG, "fft_unrolled must be 0 or 1");
     if (o->autotune != 0 && o->autotune != 1) return fail(RD_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (o->upd_rows < 0 || o->band_rows < 0 || o->col_width < 0) return fail(RD_ERR_INVALID_ARG, "negative tile size");
     if (o->precision == RD_PREC_FP32_DC && (!(o->dc_inner_rtol > 0) || o->dc_max_outer < 1))
       return fail(RD_ERR_INVALID_ARG, "bad defect-correction options");
   }
   return RD_OK;
 }
 
-// opts.autotune: time kTuneIters PDHG iterations of every (band rows, column width) pair that the
-// planner accepts and that fits the device's shared memory, on the handle's own arrays (zeroed,
-// with a solve state that never stops, so that every candidate runs the full sweeps), and keep
-// the fastest.  The chosen pair is reported in rd_stats.plan_band_rows / plan_col_width.
+// opts.autotune: on the handle's own arrays (zeroed, with a solve state that never stops, so that
+// every candidate runs the full sweeps) time each kernel over kTuneIters iterations and keep the
+// fastest tiles per kernel: band rows of k_res and of k_upd (each over 2..16 rows), column width
+// of k_col (over 2..64 columns); the three are independent.  Candidates that the planner rejects
+// or that exceed the device's shared memory are skipped.  The choice is reported in rd_stats
+// (plan_band_rows, plan_upd_rows, plan_col_width).
 constexpr int kTuneIters = 4;
 
 template <class T>
@@ -486,67 +498,96 @@ rd_status autotune_plan(rd_pdhg* h, int H, int transform, int stage_base, int us
   run.max_iter = 1 << 30;
   run.thresh = -1.0;  // never met: the sweeps stay active
   State* dst = h->d_state + 2;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  RD_CUDA(cudaEventCreate(&e0));
-  RD_CUDA(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int bestB = 0, bestC = 0;
+  // per-kernel time (ms, best of two) of kTuneIters iterations for one plan; false if it failed
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int i = 0; i < 4; ++i) RD_CUDA(cudaEventCreate(&ev[i]));
+  auto time_plan = [&](const Desc& dt, const LaunchCfg& ct, float* kms) -> bool {
+    for (int k = 0; k < 3; ++k) kms[k] = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (cudaMemcpyAsync(dst, &run, sizeof(State), cudaMemcpyHostToDevice, s) != cudaSuccess) return false;
+      if (launch_iteration<T>(dt, dst, ct, s, nullptr) != cudaSuccess) return false;  // warm-up
+      float acc[3] = {0.f, 0.f, 0.f};
+      for (int it = 0; it < kTuneIters; ++it) {
+        if (launch_iteration<T>(dt, dst, ct, s, ev) != cudaSuccess) return false;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+        for (int k = 0; k < 3; ++k) {
+          float t = 0.f;
+          if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) != cudaSuccess) return false;
+          acc[k] += t;
+        }
+      }
+      for (int k = 0; k < 3; ++k) kms[k] = std::min(kms[k], acc[k]);
+    }
+    return true;
+  };
+  auto fits = [&](const LaunchCfg& ct) { return std::max(ct.smem_res, std::max(ct.smem_col, ct.smem_upd)) <= usable; };
   std::string why;
+  const Desc& d0 = h->h_desc[ti];
+  // band rows: k_res and k_upd timed at each height (column width as planned)
+  float best_res = 1e30f, best_upd = 1e30f, best_col = 1e30f;
+  int bestB = 0, bestU = 0, bestC = 0;
   for (int B = 2; B <= 16 && B <= h->ny; B *= 2) {
+    Desc dt = d0;
+    LaunchCfg ct{};
+    if (!plan_launch<T>(h->nx, h->ny, h->nc, H, transform, h->bc == RD_BC_NEUMANN, B, d0.col_width, B, stage_base,
+                        h->opts.fft_buffers, h->opts.fft_unrolled, dt, ct, why) ||
+        !fits(ct))
+      continue;
+    float kms[3];
+    if (!time_plan(dt, ct, kms)) {
+      cudaGetLastError();
+      continue;
+    }
+    if (kms[0] < best_res) best_res = kms[0], bestB = B;
+    if (kms[2] < best_upd) best_upd = kms[2], bestU = B;
+  }
+  // column width: k_col timed at each width (band rows as planned)
+  if (transform) {
     for (int Cw = 2; Cw <= 64 && Cw <= h->nx; Cw *= 2) {
       if (h->nx % Cw) continue;
-      Desc dt = h->h_desc[ti];
+      Desc dt = d0;
       LaunchCfg ct{};
-      if (!plan_launch<T>(h->nx, h->ny, h->nc, H, transform, h->bc == RD_BC_NEUMANN, B, Cw, stage_base,
-                          h->opts.fft_buffers, h->opts.fft_unrolled, dt, ct, why))
+      if (!plan_launch<T>(h->nx, h->ny, h->nc, H, transform, h->bc == RD_BC_NEUMANN, d0.band_rows, Cw, d0.upd_rows,
+                          stage_base, h->opts.fft_buffers, h->opts.fft_unrolled, dt, ct, why) ||
+          !fits(ct))
         continue;
-      if (std::max(ct.smem_res, std::max(ct.smem_col, ct.smem_upd)) > usable) continue;
-      float ms = 0.f;
-      bool ok = true;
-      for (int rep = 0; rep < 2 && ok; ++rep) {
-        RD_CUDA(cudaMemcpyAsync(dst, &run, sizeof(State), cudaMemcpyHostToDevice, s));
-        ok = launch_iteration<T>(dt, dst, ct, s, nullptr) == cudaSuccess;  // warm-up
-        RD_CUDA(cudaEventRecord(e0, s));
-        for (int k = 0; k < kTuneIters && ok; ++k) ok = launch_iteration<T>(dt, dst, ct, s, nullptr) == cudaSuccess;
-        RD_CUDA(cudaEventRecord(e1, s));
-        RD_CUDA(cudaStreamSynchronize(s));
-        float t = 0.f;
-        RD_CUDA(cudaEventElapsedTime(&t, e0, e1));
-        if (rep == 0 || t < ms) ms = t;
-      }
-      if (!ok) {
+      float kms[3];
+      if (!time_plan(dt, ct, kms)) {
         cudaGetLastError();
         continue;
       }
-      if (ms < best) {
-        best = ms;
-        bestB = B;
-        bestC = Cw;
-      }
+      if (kms[1] < best_col) best_col = kms[1], bestC = Cw;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (bestB == 0) return RD_OK;  // nothing measured: keep the planner's choice
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (bestB == 0 || bestU == 0) return RD_OK;  // nothing measured: keep the planner's choice
+  if (bestC == 0) bestC = d0.col_width;
   Desc& d = h->h_desc[ti];
   LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
-  if (!plan_launch<T>(h->nx, h->ny, h->nc, H, transform, h->bc == RD_BC_NEUMANN, bestB, bestC, stage_base,
-                      h->opts.fft_buffers, h->opts.fft_unrolled, d, lc, why))
-    return fail(RD_ERR_CUDA, "autotune: re-planning the chosen tiles failed: " + why);
+  LaunchCfg tuned{};
+  Desc dtn = d;
+  if (!plan_launch<T>(h->nx, h->ny, h->nc, H, transform, h->bc == RD_BC_NEUMANN, bestB, bestC, bestU, stage_base,
+                      h->opts.fft_buffers, h->opts.fft_unrolled, dtn, tuned, why) || !fits(tuned))
+    return RD_OK;  // the combination does not fit: keep the planner's choice
+  d = dtn;
+  lc = tuned;
   if (h->dc) {
     h->h_desc[0].band_rows = d.band_rows;
     h->h_desc[0].nbands = d.nbands;
     h->h_desc[0].col_width = d.col_width;
     h->h_desc[0].ncolblk = d.ncolblk;
+    h->h_desc[0].upd_rows = d.upd_rows;
+    h->h_desc[0].nupd = d.nupd;
   } else {
     h->cfgpc = lc;
-    const Desc& d0 = h->h_desc[0];
     Desc& dp = h->h_desc[2];
-    dp.band_rows = d0.band_rows;
-    dp.nbands = d0.nbands;
-    dp.col_width = d0.col_width;
-    dp.ncolblk = d0.ncolblk;
-    dp.fft_pp = d0.fft_pp;
+    dp.band_rows = d.band_rows;
+    dp.nbands = d.nbands;
+    dp.col_width = d.col_width;
+    dp.ncolblk = d.ncolblk;
+    dp.upd_rows = d.upd_rows;
+    dp.nupd = d.nupd;
+    dp.fft_pp = d.fft_pp;
   }
   RD_CUDA(cudaMemcpy(h->d_desc, h->h_desc, 3 * sizeof(Desc), cudaMemcpyHostToDevice));
   return RD_OK;
@@ -599,17 +640,20 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
 
   std::string why;
   Desc d64 = base, d32 = base;
-  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, bc == RD_BC_NEUMANN, h->opts.band_rows, h->opts.col_width, 0, h->opts.fft_buffers, h->opts.fft_unrolled, d64, h->cfg64, why))
+  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, bc == RD_BC_NEUMANN, h->opts.band_rows, h->opts.col_width,
+                           h->opts.upd_rows, 0, h->opts.fft_buffers, h->opts.fft_unrolled, d64, h->cfg64, why))
     if (!h->dc) return fail(RD_ERR_UNSUPPORTED, "FP64 path: " + why);
   if (h->dc) {
     // the FP64 kernels of the defect-correction loop only need the band decomposition
     if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, bc == RD_BC_NEUMANN, h->opts.band_rows, h->opts.col_width,
-                           rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT, h->opts.fft_buffers, h->opts.fft_unrolled, d32, h->cfg32, why))
+                           h->opts.upd_rows, rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT, h->opts.fft_buffers, h->opts.fft_unrolled, d32, h->cfg32, why))
       return fail(RD_ERR_UNSUPPORTED, "FP32 path: " + why);
     d64.band_rows = d32.band_rows;
     d64.nbands = d32.nbands;
     d64.col_width = d32.col_width;
     d64.ncolblk = d32.ncolblk;
+    d64.upd_rows = d32.upd_rows;
+    d64.nupd = d32.nupd;
   }
 
   const size_t n = h->npts;
@@ -731,12 +775,13 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
   if (std::max(lc.smem_res, std::max(lc.smem_col, lc.smem_upd)) > usable)
     return fail(RD_ERR_UNSUPPORTED, "the grid needs more shared memory per block than this device offers");
-  if (h->opts.autotune && h->opts.band_rows == 0 && h->opts.col_width == 0) {
+  if (h->opts.autotune && h->opts.band_rows == 0 && h->opts.col_width == 0 && h->opts.upd_rows == 0) {
     const int stage_base = h->dc && (rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT);
     RD_TRY(h->dc ? autotune_plan<float>(h, H, transform, stage_base, usable)
                  : autotune_plan<double>(h, H, transform, stage_base, usable));
   }
   h->stats.plan_band_rows = h->h_desc[h->dc ? 1 : 0].band_rows;
+  h->stats.plan_upd_rows = h->h_desc[h->dc ? 1 : 0].upd_rows;
   h->stats.plan_col_width = h->h_desc[h->dc ? 1 : 0].col_width;
   RD_TRY(capture_graphs(h));
   RD_CUDA(cudaDeviceSynchronize());
@@ -938,6 +983,7 @@ void rd_opts_default(rd_opts* o) {
   o->graph_k = 2;
   o->band_rows = 0;
   o->col_width = 0;
+  o->upd_rows = 0;
   o->profile = 0;
   o->fft_buffers = 0;
   o->solve_loop = RD_LOOP_GRAPH;
@@ -1048,10 +1094,11 @@ rd_status rd_pdhg_get_stats(const rd_pdhg* h, rd_stats* out) {
 
 rd_status rd_pdhg_reset_stats(rd_pdhg* h) {
   if (!h) return fail(RD_ERR_INVALID_ARG, "NULL handle");
-  const int pb = h->stats.plan_band_rows, pc = h->stats.plan_col_width;
+  const int pb = h->stats.plan_band_rows, pc = h->stats.plan_col_width, pu = h->stats.plan_upd_rows;
   h->stats = rd_stats{};
   h->stats.plan_band_rows = pb;
   h->stats.plan_col_width = pc;
+  h->stats.plan_upd_rows = pu;
   return RD_OK;
 }
 

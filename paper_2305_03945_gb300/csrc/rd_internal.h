@@ -40,6 +40,8 @@ struct Desc {
   int batched;       // 1: member of a batch (Slot control block, device-side phase machine)
   int fft_pp;        // bit 0 k_res, bit 1 k_col, bit 2 k_upd: transforms ping-pong between two buffers;
                      // bit 3: size-specialised unrolled transform passes (else looped passes)
+  int upd_rows;      // rows per CTA of k_upd (0: band_rows); k_res keeps band_rows
+  int nupd;          // ceil(ny / upd_rows)
   double hx2, hy2;   // 1/h_x^2, 1/h_y^2
   double dt, a, b;
   double p[6];

@@ -14,6 +14,7 @@ struct LaunchCfg {
   int thr_res, thr_col, thr_upd;
   int smem_res, smem_col, smem_upd;
   int transform;     // 0 when G = I (no spectral solve)
+  int grid_upd;      // k_upd bands (0: grid_bands)
 };
 
 // Raise the dynamic shared-memory limit of the PDHG kernels; *usable receives the bytes a launch may ask.

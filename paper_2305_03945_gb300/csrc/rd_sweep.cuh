@@ -738,15 +738,16 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
                                          unsigned char* smem_raw) {
   constexpr bool PC = K == KK_PCONLY;
   constexpr int H = KT<K>::H;
-  if (band >= d.nbands) return;
+  const int brows = d.upd_rows ? d.upd_rows : d.band_rows;
+  if (band >= (d.upd_rows ? d.nupd : d.nbands)) return;
   if (!PC && !sweep_active(st, slot)) return;
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nx = d.nx, ny = d.ny, bc = d.bc, lognx = d.lognx;
   const int nc = PC ? d.ncomp : (KT<K>::two ? 2 : 1);
   const size_t plane = (size_t)nx * ny;
-  const int y0 = band * d.band_rows;
-  const int rows = min(d.band_rows, ny - y0);
+  const int y0 = band * brows;
+  const int rows = min(brows, ny - y0);
   const int lrows = rows + 2 * H;
   const int lpc = lrows >> 1;
   const int nl = nc * lpc;
@@ -922,13 +923,27 @@ static cudaError_t allow_smem_k(K_ kernel, int optin) {
 template <class T, int K>
 static cudaError_t launch_iter_k(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev) {
   constexpr bool PC = K == KK_PCONLY;
-  if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  // inside a stream capture the events become external event-record nodes of the graph;
+  // outside one they are ordinary records (the external flag is for capture only)
+  unsigned flags = cudaEventRecordDefault;
+  if (ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusActive) flags = cudaEventRecordExternal;
+  }
+  cudaError_t e = cudaSuccess;
+  auto mark = [&](int i) {
+    if (ev && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[i], s, flags);
+  };
+  mark(0);
   k_res<T, K><<<c.grid_bands, c.thr_res, c.smem_res, s>>>(d, st);
-  if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+  mark(1);
   if (c.transform) k_col<T, PC><<<c.grid_cols, c.thr_col, c.smem_col, s>>>(d, st);
-  if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
-  k_upd<T, K><<<c.grid_bands, c.thr_upd, c.smem_upd, s>>>(d, st);
-  if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
+  mark(2);
+  k_upd<T, K><<<c.grid_upd ? c.grid_upd : c.grid_bands, c.thr_upd, c.smem_upd, s>>>(d, st);
+  mark(3);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -376,18 +376,38 @@ def test_transform_pass_forms_match_oracle(fft_unrolled, bc):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_dc"])
 def test_autotuned_tiles_match_oracle(precision):
-    """The autotuner times the candidate tile shapes at create and keeps one that fits; the step
-    it then takes matches the oracle within the usual tolerances."""
+    """The autotuner times the candidate tile shapes at create and keeps one that fits (the
+    residual and update sweeps may get different band heights); the step it then takes matches
+    the oracle within the usual tolerances."""
     rd = _rd()
     pb = _problem("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06), "periodic", 64, 128)
     uk = _state(pb, 16)
     U_ref, info_ref = O.pdhg_step(pb, uk)
     with rd.Solver(pb, precision=precision, autotune=1) as s:
         st = s.stats()
-        assert st["plan_band_rows"] in (2, 4, 8, 16) and st["plan_col_width"] in (2, 4, 8, 16, 32, 64)
+        assert st["plan_band_rows"] in (2, 4, 8, 16) and st["plan_upd_rows"] in (2, 4, 8, 16)
+        assert st["plan_col_width"] in (2, 4, 8, 16, 32, 64)
         out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
         info = s.step(dev(uk), out)
         U = host(out)
     assert info["status"] == 0, info
     tol = 1e-10 if precision == "fp64" else 1e-9
     assert np.linalg.norm(U - U_ref) <= tol * np.linalg.norm(U_ref)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("res_rows,upd_rows", [(2, 8), (8, 2), (4, 16)])
+def test_different_band_heights_for_residual_and_update(bc, res_rows, upd_rows):
+    """k_res and k_upd with different band heights (as the autotuner may choose) give a step that
+    matches the oracle and agrees with one common height to rounding of the norm partials."""
+    rd = _rd()
+    pb = _problem("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06), bc, 64, 64)
+    uk = _state(pb, 17)
+    U_ref, _ = O.pdhg_step(pb, uk)
+    res = []
+    for u_rows in (upd_rows, res_rows):
+        U, info, _, _ = _compare_step(pb, uk, precision="fp32_dc", band_rows=res_rows, upd_rows=u_rows)
+        assert info["status"] == 0, info
+        assert np.linalg.norm(U - U_ref) <= 1e-9 * np.linalg.norm(U_ref)
+        res.append(U)
+    assert np.linalg.norm(res[0] - res[1]) <= 1e-10 * np.linalg.norm(U_ref)
