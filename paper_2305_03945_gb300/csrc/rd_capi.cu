@@ -479,7 +479,7 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
 // of k_col (over 2..64 columns); the three are independent.  Candidates that the planner rejects
 // or that exceed the device's shared memory are skipped.  The choice is reported in rd_stats
 // (plan_band_rows, plan_upd_rows, plan_col_width).
-constexpr int kTuneIters = 4;
+constexpr int kTuneIters = 8;
 
 template <class T>
 rd_status autotune_plan(rd_pdhg* h, int H, int transform, int stage_base, int usable) {
@@ -498,12 +498,12 @@ rd_status autotune_plan(rd_pdhg* h, int H, int transform, int stage_base, int us
   run.max_iter = 1 << 30;
   run.thresh = -1.0;  // never met: the sweeps stay active
   State* dst = h->d_state + 2;
-  // per-kernel time (ms, best of two) of kTuneIters iterations for one plan; false if it failed
+  // per-kernel time (ms, best of three) of kTuneIters iterations for one plan; false if it failed
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   for (int i = 0; i < 4; ++i) RD_CUDA(cudaEventCreate(&ev[i]));
   auto time_plan = [&](const Desc& dt, const LaunchCfg& ct, float* kms) -> bool {
     for (int k = 0; k < 3; ++k) kms[k] = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
       if (cudaMemcpyAsync(dst, &run, sizeof(State), cudaMemcpyHostToDevice, s) != cudaSuccess) return false;
       if (launch_iteration<T>(dt, dst, ct, s, nullptr) != cudaSuccess) return false;  // warm-up
       float acc[3] = {0.f, 0.f, 0.f};

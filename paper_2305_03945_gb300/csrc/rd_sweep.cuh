@@ -424,8 +424,13 @@ __device__ __forceinline__ void res_points(const Desc& d, cx<T>* buf, const T* x
     const T* rr0 = rrg0[q];
     const T* rr1 = rrg1[q];
     T w0[W], w1[W];
-    // boundary-mapped columns everywhere (one copy of the residual code; see upd_points)
-    res_group<T, K, true, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, pbg0[q], pbg1[q], lpc, ls, w0, w1);
+    // five-point kinds: boundary-mapped columns everywhere (one copy of the residual code, see
+    // upd_points); the 13-point biharmonic stencil keeps an interior copy without the mapping
+    // (its 13 mapped reads per point cost more than the extra code)
+    if (KT<K>::biharm && j0 >= 2 && j0 + W + 2 <= nx)
+      res_group<T, K, false, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, pbg0[q], pbg1[q], lpc, ls, w0, w1);
+    else
+      res_group<T, K, true, W>(d, buf, xs, bs, srows, r, j0, rr0, rr1, pbg0[q], pbg1[q], lpc, ls, w0, w1);
 #pragma unroll
     for (int q = 0; q < W; ++q) {
       acc0 += w0[q] * w0[q];
