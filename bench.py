@@ -312,7 +312,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- chosen form: FP32 sweeps + FP64 defect correction ----
     u = torch.from_numpy(w.u0.copy()).to(dev)
-    tune = dict(band_rows=args.band_rows, col_width=args.col_width, graph_k=args.graph_k,
+    tune = dict(band_rows=args.band_rows, col_width=args.col_width, upd_rows=args.upd_rows, graph_k=args.graph_k,
                 fft_buffers=args.fft_buffers, solve_loop=args.solve_loop, fft_unrolled=args.fft_unrolled,
                 autotune=args.autotune)
     sv = rd.Solver(pb, precision=args.precision, profile=1, **tune)
@@ -433,8 +433,8 @@ def run_ours(args, rank, world, local_rank):
                    "residual_passes_per_step": st["residual_passes"] / args.steps,
                    "band_rows": st["plan_band_rows"], "upd_rows": st["plan_upd_rows"],
                    "col_width": st["plan_col_width"],
-                   "tiles": "autotuned at create" if (args.autotune and not args.band_rows and not args.col_width)
-                            else ("given" if (args.band_rows or args.col_width) else "planner"),
+                   "tiles": "autotuned at create" if (args.autotune and not (args.band_rows or args.col_width or args.upd_rows))
+                            else ("given" if (args.band_rows or args.col_width or args.upd_rows) else "planner"),
                    "graph_k": args.graph_k,
                    "fft_buffers": args.fft_buffers, "solve_loop": args.solve_loop,
                    "fft_unrolled": args.fft_unrolled},
@@ -465,6 +465,7 @@ def main():
     ap.add_argument("--solve-loop", default="graph", choices=("graph", "host"),
                     help="PDHG loop: WHILE node of the step graph, or host-relaunched plain graphs "
                          "(for profilers, which cannot attribute kernels inside conditional nodes)")
+    ap.add_argument("--upd-rows", type=int, default=0, help="rows per CTA of k_upd (0: as --band-rows)")
     ap.add_argument("--autotune", type=int, default=1, choices=(0, 1),
                     help="1: time the candidate tile shapes at create and keep the fastest")
     ap.add_argument("--fft-unrolled", type=int, default=1, choices=(0, 1),
