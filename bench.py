@@ -314,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
     u = torch.from_numpy(w.u0.copy()).to(dev)
     tune = dict(band_rows=args.band_rows, col_width=args.col_width, upd_rows=args.upd_rows, graph_k=args.graph_k,
                 fft_buffers=args.fft_buffers, solve_loop=args.solve_loop, fft_unrolled=args.fft_unrolled,
-                autotune=args.autotune)
+                autotune=args.autotune, dc_inner_rtol=args.dc_inner_rtol, dc_stall_window=args.dc_stall_window)
     sv = rd.Solver(pb, precision=args.precision, profile=1, **tune)
     with ClockSampler(local_rank) as clk:
         tot_ms, its, infos = timed_steps(sv, u, args.steps, args.warmup)
@@ -444,6 +444,7 @@ def run_ours(args, rank, world, local_rank):
                             else ("given" if (args.band_rows or args.col_width or args.upd_rows) else "planner"),
                    "graph_k": args.graph_k,
                    "fft_buffers": args.fft_buffers, "solve_loop": args.solve_loop,
+                   "dc_inner_rtol": args.dc_inner_rtol, "dc_stall_window": args.dc_stall_window,
                    "fft_unrolled": args.fft_unrolled},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "parity_full_size": parity, "fp64_plain": fp64,
         "serving": serving,
@@ -473,6 +474,11 @@ def main():
                     help="PDHG loop: WHILE node of the step graph, or host-relaunched plain graphs "
                          "(for profilers, which cannot attribute kernels inside conditional nodes)")
     ap.add_argument("--upd-rows", type=int, default=0, help="rows per CTA of k_upd (0: as --band-rows)")
+    ap.add_argument("--dc-stall-window", type=int, default=None,
+                    help="defect correction: stop the FP32 inner solve when its residual has not halved "
+                         "for this many updates (default: the library's)")
+    ap.add_argument("--dc-inner-rtol", type=float, default=None,
+                    help="defect correction: inner FP32 solve to this fraction of the FP64 residual")
     ap.add_argument("--autotune", type=int, default=1, choices=(0, 1),
                     help="1: time the candidate tile shapes at create and keep the fastest")
     ap.add_argument("--fft-unrolled", type=int, default=1, choices=(0, 1),

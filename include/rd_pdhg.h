@@ -135,7 +135,8 @@ typedef struct {
     int max_iter;         /* PDHG updates per step (FP64) or per inner solve (DC); default 10000 */
     double omega;         /* extrapolation coefficient, default 1 (Section 3)                   */
     int precision;        /* rd_precision, default RD_PREC_FP64                                 */
-    double dc_inner_rtol; /* DC inner tolerance factor, default 1e-4                             */
+    double dc_inner_rtol; /* DC inner tolerance factor, default 1e-5: the FP32 solve of a round
+                             stops at max(dc_inner_rtol ||r||, half the outer threshold)        */
     int dc_max_outer;     /* DC outer rounds per step, default 12                                */
     int graph_k;          /* PDHG iterations per trip of the device-side loop (a WHILE node of the
                              step's CUDA graph), default 2                                      */
@@ -158,6 +159,9 @@ typedef struct {
                              or col_width is set); 0 (default): the occupancy-based planner.
                              Timing noise can change the choice between runs, and with it the
                              summation order of the stopping norm (results agree to rounding). */
+    int dc_stall_window;  /* DC: the FP32 inner solve also stops (as converged) when its residual
+                             has not halved for this many updates (its rounding floor); default
+                             8                                                                   */
 } rd_opts;
 
 typedef struct {

@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256) k_step_b(const Desc* __restrict__ d64s, S
         in->n = 0;
         in->r = 0.0;
         in->r0 = 0.0;
-        in->thresh = sl->rtol * tot;
+        in->thresh = fmax(sl->rtol * tot, 0.5 * outer->thresh * (d.meas_div_dt ? d.dt : 1.0));
         in->status = ST_ACTIVE;
         in->ticket = 0u;
         sl->phase = PH_INNER;
@@ -576,7 +576,7 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   d64.f32_u = u32;
   d32.dc = 1;
   d32.meas_div_dt = 0;
-  d32.stall_window = 32;
+  d32.stall_window = b->opts.dc_stall_window > 0 ? b->opts.dc_stall_window : 8;
   d32.X = dl;
   d32.base = u32;
   d32.rhs = r32;

@@ -37,7 +37,7 @@ constexpr int kTargetBlocks = 152;  // one wave on a GB300
 // The FP32 inner solve of defect correction stops, as converged, once its residual has not
 // halved over this many updates: it has reached the FP32 rounding floor of the correction
 // equation and the FP64 outer loop takes over.
-constexpr int kDcStallWindow = 32;
+constexpr int kDcStallWindow = 8;  // default of rd_opts.dc_stall_window
 
 bool pow2(int n) { return n >= 2 && (n & (n - 1)) == 0; }
 int ilog2(int n) {
@@ -466,6 +466,8 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
     if (o->solve_loop != RD_LOOP_GRAPH && o->solve_loop != RD_LOOP_HOST) return fail(RD_ERR_INVALID_ARG, "bad solve_loop");
     if (o->fft_unrolled != 0 && o->fft_unrolled != 1) return fail(RD_ERR_INVALID_ARG, "fft_unrolled must be 0 or 1");
     if (o->autotune != 0 && o->autotune != 1) return fail(RD_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (o->precision == RD_PREC_FP32_DC && o->dc_stall_window < 1)
+      return fail(RD_ERR_INVALID_ARG, "dc_stall_window must be >= 1");
     if (o->upd_rows < 0 || o->band_rows < 0 || o->col_width < 0) return fail(RD_ERR_INVALID_ARG, "negative tile size");
     if (o->precision == RD_PREC_FP32_DC && (!(o->dc_inner_rtol > 0) || o->dc_max_outer < 1))
       return fail(RD_ERR_INVALID_ARG, "bad defect-correction options");
@@ -737,7 +739,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   d32.dc = 1;
   d32.mode = MODE_PDHG;
   d32.meas_div_dt = 0;
-  d32.stall_window = kDcStallWindow;
+  d32.stall_window = h->opts.dc_stall_window;
   d32.X = h->D32;
   d32.base = h->u32;
   d32.rhs = h->r32;
@@ -978,7 +980,7 @@ void rd_opts_default(rd_opts* o) {
   o->max_iter = 10000;
   o->omega = 1.0;
   o->precision = RD_PREC_FP64;
-  o->dc_inner_rtol = 1e-4;
+  o->dc_inner_rtol = 1e-5;
   o->dc_max_outer = 12;
   o->graph_k = 2;
   o->band_rows = 0;
@@ -989,6 +991,7 @@ void rd_opts_default(rd_opts* o) {
   o->solve_loop = RD_LOOP_GRAPH;
   o->fft_unrolled = 1;
   o->autotune = 0;
+  o->dc_stall_window = kDcStallWindow;
 }
 
 rd_status rd_pdhg_create(rd_pdhg** out, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* reaction,

@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(256) k_begin(const Desc* __restrict__ d64, Sta
 // `decide`, the kernel does nothing unless `outer` is active; its last block applies the outer
 // stopping rule of defect correction to `outer` (evaluation number max_outer, counting from 0,
 // ends the step as not converged) and otherwise arms the inner FP32 solve `inner` (threshold
-// rtol * sum_c ||W_c||).  zero32 (optional, two FP32 arrays) are cleared: the inner unknown d
-// and the dual P_0.
+// max(rtol * sum_c ||W_c||, half the outer threshold in the same units)).  zero32 (optional,
+// two FP32 arrays) are cleared: the inner unknown d and the dual P_0.
 template <int K>
 __global__ void __launch_bounds__(256)
     k_resid64(const Desc* __restrict__ d64, State* __restrict__ outer, State* __restrict__ inner,
@@ -171,7 +171,9 @@ __global__ void __launch_bounds__(256)
         inner->trips = 0u;
         inner->r = 0.0;
         inner->r0 = 0.0;
-        inner->thresh = rtol * tot;
+        // rtol of the current FP64 residual, but no tighter than half of what the outer
+        // stopping rule still needs: the last round solves no further than the step requires
+        inner->thresh = fmax(rtol * tot, 0.5 * outer->thresh * (d.meas_div_dt ? d.dt : 1.0));
         inner->status = ST_ACTIVE;
         inner->ticket = 0u;
       }

@@ -49,7 +49,7 @@ class rd_opts(ctypes.Structure):
                 ("graph_k", ctypes.c_int), ("band_rows", ctypes.c_int), ("col_width", ctypes.c_int),
                 ("upd_rows", ctypes.c_int),
                 ("profile", ctypes.c_int), ("fft_buffers", ctypes.c_int), ("solve_loop", ctypes.c_int),
-                ("fft_unrolled", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("fft_unrolled", ctypes.c_int), ("autotune", ctypes.c_int), ("dc_stall_window", ctypes.c_int)]
 
 
 class rd_stats(ctypes.Structure):
@@ -164,8 +164,8 @@ def _check(status, ok=(RD_OK,)):
     return status
 
 
-def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_inner_rtol=1e-4,
-                 dc_max_outer=12, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1, autotune=0, upd_rows=0):
+def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_inner_rtol=None,
+                 dc_max_outer=12, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1, autotune=0, upd_rows=0, dc_stall_window=None):
     """C structs for a ``workloads.Problem``."""
     g = rd_grid()
     g.ndim = 2
@@ -188,7 +188,8 @@ def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_i
     o.graph_k = graph_k
     o.band_rows = band_rows
     o.col_width = col_width
-    o.dc_inner_rtol = dc_inner_rtol
+    if dc_inner_rtol is not None:
+        o.dc_inner_rtol = dc_inner_rtol
     o.dc_max_outer = dc_max_outer
     o.profile = profile
     o.fft_buffers = fft_buffers
@@ -196,6 +197,8 @@ def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_i
     o.fft_unrolled = fft_unrolled
     o.autotune = autotune
     o.upd_rows = upd_rows
+    if dc_stall_window is not None:
+        o.dc_stall_window = dc_stall_window
     return g, rx, pc, o
 
 
@@ -281,13 +284,15 @@ class Batch:
     ``workloads.Problem`` records plus a host float64 initial state and a step count; results
     come back through ``poll``, final states in the host arrays returned by ``submit``."""
 
-    def __init__(self, hbm_budget_bytes, max_slots, graph_k=8, max_iter=10000, dc_inner_rtol=1e-4,
+    def __init__(self, hbm_budget_bytes, max_slots, graph_k=8, max_iter=10000, dc_inner_rtol=None,
                  dc_max_outer=12, stream=None):
         import torch
         lib = load()
         o = rd_opts()
         lib.rd_opts_default(ctypes.byref(o))
-        o.graph_k, o.max_iter, o.dc_inner_rtol, o.dc_max_outer = graph_k, max_iter, dc_inner_rtol, dc_max_outer
+        o.graph_k, o.max_iter, o.dc_max_outer = graph_k, max_iter, dc_max_outer
+        if dc_inner_rtol is not None:
+            o.dc_inner_rtol = dc_inner_rtol
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         h = ctypes.c_void_p()
