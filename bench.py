@@ -131,13 +131,30 @@ def kernel_bytes(pb, precision):
     return {"k_res": (3 + base) * es * npts, "k_col": 2 * es * npts, "k_upd": (5 + base) * es * npts}
 
 
-def read_traffic(name, kernel, shash):
+# the files that define each profiled kernel: a traffic figure stays valid while they are unchanged
+SWEEP_SOURCES = ("rd_sweep.cuh", "rd_device.cuh", "rd_internal.h", "rd_launch.h", "rd_sweep_f32.cu", "rd_sweep_f64.cu")
+KERNEL_SOURCES = {"k_res": SWEEP_SOURCES, "k_col": SWEEP_SOURCES, "k_upd": SWEEP_SOURCES,
+                  "k_resid64": SWEEP_SOURCES + ("rd_kernels.cu",)}
+
+
+def kernel_source_hash(kernel):
+    h = hashlib.sha256()
+    d = os.path.join(HERE, "paper_2305_03945_gb300", "csrc")
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(name, kernel, shash=None):
+    """DRAM bytes per launch from profiles/traffic.json, or None when the kernel's sources changed
+    after the capture."""
     p = os.path.join(HERE, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
     d = json.load(open(p))
     e = d.get(name, {}).get(kernel)
-    if not e or e.get("source_hash") != shash:
+    if not e or e.get("kernel_source_hash") != kernel_source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
