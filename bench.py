@@ -128,12 +128,15 @@ def kernel_bytes(pb, precision):
     es = 4 if precision == "fp32_dc" else 8
     npts = pb.ncomp * pb.nx * pb.ny
     base = 1 if (precision == "fp32_dc" and pb.kind != "none") else 0
-    return {"k_res": (3 + base) * es * npts, "k_col": 2 * es * npts, "k_upd": (5 + base) * es * npts}
+    # k_updres (fused update): k_upd's touches plus the right-hand side read and the transformed
+    # residual written (the unknown is read and written once for both)
+    return {"k_res": (3 + base) * es * npts, "k_col": 2 * es * npts, "k_upd": (5 + base) * es * npts,
+            "k_updres": (7 + base) * es * npts}
 
 
 # the files that define each profiled kernel: a traffic figure stays valid while they are unchanged
 SWEEP_SOURCES = ("rd_sweep.cuh", "rd_device.cuh", "rd_internal.h", "rd_launch.h", "rd_sweep_f32.cu", "rd_sweep_f64.cu")
-KERNEL_SOURCES = {"k_res": SWEEP_SOURCES, "k_col": SWEEP_SOURCES, "k_upd": SWEEP_SOURCES,
+KERNEL_SOURCES = {"k_res": SWEEP_SOURCES, "k_col": SWEEP_SOURCES, "k_upd": SWEEP_SOURCES, "k_updres": SWEEP_SOURCES,
                   "k_resid64": SWEEP_SOURCES + ("rd_kernels.cu",)}
 
 
@@ -331,7 +334,8 @@ def run_ours(args, rank, world, local_rank):
     u = torch.from_numpy(w.u0.copy()).to(dev)
     tune = dict(band_rows=args.band_rows, col_width=args.col_width, upd_rows=args.upd_rows, graph_k=args.graph_k,
                 fft_buffers=args.fft_buffers, solve_loop=args.solve_loop, fft_unrolled=args.fft_unrolled,
-                autotune=args.autotune, dc_inner_rtol=args.dc_inner_rtol, dc_stall_window=args.dc_stall_window)
+                autotune=args.autotune, dc_inner_rtol=args.dc_inner_rtol, dc_stall_window=args.dc_stall_window,
+                fused_update=args.fused_update)
     sv = rd.Solver(pb, precision=args.precision, profile=1, **tune)
     with ClockSampler(local_rank) as clk:
         tot_ms, its, infos = timed_steps(sv, u, args.steps, args.warmup)
@@ -348,7 +352,7 @@ def run_ours(args, rank, world, local_rank):
     # per-kernel roofline from the live CUDA-event samples
     peak, peak_kind = load_peaks()
     kb = kernel_bytes(pb, args.precision)
-    names = ("k_res", "k_col", "k_upd")
+    names = ("k_res", "k_col", "k_updres" if st.get("fused_update") else "k_upd")
     per = {}
     for i, nm in enumerate(names):
         n = st["kernel_samples"][i]
@@ -365,12 +369,14 @@ def run_ours(args, rank, world, local_rank):
                 "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "traffic": read_traffic(args.workload, dom, shash), "per_kernel": per}
-        if len(per) == 3:
-            # the whole PDHG sweep of one iteration (k_res + k_col + k_upd): algorithmic bytes of
-            # the three kernels over the sum of their average durations
-            sb = sum(per[k]["algorithmic_bytes"] for k in per)
-            su = sum(per[k]["avg_us"] for k in per)
-            roof["sweep"] = {"kernels": "k_res+k_col+k_upd", "algorithmic_bytes": sb, "avg_us": su,
+        # the whole PDHG sweep of one iteration (k_res + k_col + k_upd, or with the fused update
+        # k_col + k_updres, k_res running only before the first update): algorithmic bytes of its
+        # kernels over the sum of their average durations
+        it_k = [k for k in ("k_col", "k_updres") if k in per] if "k_updres" in per else list(per)
+        if len(it_k) >= 2:
+            sb = sum(per[k]["algorithmic_bytes"] for k in it_k)
+            su = sum(per[k]["avg_us"] for k in it_k)
+            roof["sweep"] = {"kernels": "+".join(it_k), "algorithmic_bytes": sb, "avg_us": su,
                              "achieved": sb / (su * 1e-6) / 1e9, "frac": sb / (su * 1e-6) / 1e9 / peak}
 
     # ---- end to end through the public API with host buffers ----
@@ -462,6 +468,7 @@ def run_ours(args, rank, world, local_rank):
                    "graph_k": args.graph_k,
                    "fft_buffers": args.fft_buffers, "solve_loop": args.solve_loop,
                    "dc_inner_rtol": args.dc_inner_rtol, "dc_stall_window": args.dc_stall_window,
+                   "fused_update": st.get("fused_update", 0),
                    "fft_unrolled": args.fft_unrolled},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "parity_full_size": parity, "fp64_plain": fp64,
         "serving": serving,
@@ -491,6 +498,8 @@ def main():
                     help="PDHG loop: WHILE node of the step graph, or host-relaunched plain graphs "
                          "(for profilers, which cannot attribute kernels inside conditional nodes)")
     ap.add_argument("--upd-rows", type=int, default=0, help="rows per CTA of k_upd (0: as --band-rows)")
+    ap.add_argument("--fused-update", type=int, default=1, choices=(0, 1),
+                    help="1: the update of each PDHG iteration fused with the next residual (k_updres)")
     ap.add_argument("--dc-stall-window", type=int, default=None,
                     help="defect correction: stop the FP32 inner solve when its residual has not halved "
                          "for this many updates (default: the library's)")

@@ -162,6 +162,11 @@ typedef struct {
     int dc_stall_window;  /* DC: the FP32 inner solve also stops (as converged) when its residual
                              has not halved for this many updates (its rounding floor); default
                              8                                                                   */
+    int fused_update;     /* 1 (default): FP32 defect correction in the graph loop runs the update
+                             of each iteration fused with the next residual (k_col + k_updres
+                             per iteration; k_res only before the first update) when its block
+                             fits, and with autotune only where it measures faster; 0: never.
+                             Fused and unfused inner iterates differ by FP32 rounding only.     */
 } rd_opts;
 
 typedef struct {
@@ -185,6 +190,7 @@ typedef struct {
     int plan_band_rows;          /* rows per CTA of the sweeps chosen at create (planner/autotune) */
     int plan_col_width;          /* columns per CTA of the column transform chosen at create      */
     int plan_upd_rows;           /* rows per CTA of the update sweep (k_upd) chosen at create    */
+    int fused_update;            /* 1 when the fused update + residual kernel (k_updres) runs      */
 } rd_stats;
 
 typedef struct rd_pdhg rd_pdhg;

@@ -206,6 +206,9 @@ struct rd_pdhg {
   float* D32 = nullptr;
   float* P32[2] = {nullptr, nullptr};
   float* WY32 = nullptr;
+  float* WY32b = nullptr;   // fused update: second transform buffer
+  float* halo32 = nullptr;  // fused update: per-band copies of U on the halo rows
+  size_t halo_bytes = 0;
   float* mu32[2] = {nullptr, nullptr};
   float* r32 = nullptr;
   float* u32 = nullptr;
@@ -330,7 +333,8 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   cudaGraphConditionalHandle cond = 0;
   RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
   const Desc dd = h->dc ? h->h_desc[1] : h->h_desc[0];
-  auto iteration = [&](cudaStream_t st, cudaEvent_t* ev) {
+  auto iteration = [&](cudaStream_t st, cudaEvent_t* ev, bool first_it) {
+    if (h->dc && dd.fused) return launch_fused<float>(dd, sti, h->cfg32, st, ev, first_it);
     return h->dc ? launch_iteration<float>(dd, sti, h->cfg32, st, ev) : launch_iteration<double>(dd, sti, h->cfg64, st, ev);
   };
   auto abort_capture = [&](cudaStream_t st, const char* what, cudaError_t e) {
@@ -349,7 +353,10 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
                          h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, cs);
     if (e != cudaSuccess) return abort_capture(cs, "step set-up during capture", e);
   }
-  if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr)) != cudaSuccess ||
+  // fused update: the per-band halo copies of U start at U_0 = d = 0
+  if (dd.fused && (e = cudaMemsetAsync(h->halo32, 0, h->halo_bytes, cs)) != cudaSuccess)
+    return abort_capture(cs, "clearing the halo copies during capture", e);
+  if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr, true)) != cudaSuccess ||
       (e = launch_loop_cond(sti, cond, 1u, cs)) != cudaSuccess)
     return abort_capture(cs, "kernel launch during capture", e);
   // the WHILE node, appended to the capture after the first iteration
@@ -373,7 +380,7 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   if ((e = cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
       cudaSuccess)
     return abort_capture(cs, "capturing the loop body", e);
-  for (int k = 0; k < K && e == cudaSuccess; ++k) e = iteration(h->body_stream, nullptr);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) e = iteration(h->body_stream, nullptr, false);
   if (e == cudaSuccess) e = launch_loop_cond(sti, cond, (unsigned)K, h->body_stream);
   if (e != cudaSuccess) {
     abort_capture(h->body_stream, "loop body", e);
@@ -420,7 +427,7 @@ rd_status capture_iter_graph(rd_pdhg* h) {
 
 rd_status capture_graphs(rd_pdhg* h) {
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
-  h->kernels_per_iter = lc.transform ? 3 : 2;
+  h->kernels_per_iter = h->dc && h->h_desc[1].fused ? 2 : (lc.transform ? 3 : 2);
   if (h->opts.profile)
     for (int i = 0; i < 4; ++i) RD_CUDA(cudaEventCreate(&h->ev[i]));
   if (h->opts.solve_loop == RD_LOOP_HOST) return capture_iter_graph(h);
@@ -466,6 +473,7 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
     if (o->solve_loop != RD_LOOP_GRAPH && o->solve_loop != RD_LOOP_HOST) return fail(RD_ERR_INVALID_ARG, "bad solve_loop");
     if (o->fft_unrolled != 0 && o->fft_unrolled != 1) return fail(RD_ERR_INVALID_ARG, "fft_unrolled must be 0 or 1");
     if (o->autotune != 0 && o->autotune != 1) return fail(RD_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (o->fused_update != 0 && o->fused_update != 1) return fail(RD_ERR_INVALID_ARG, "fused_update must be 0 or 1");
     if (o->precision == RD_PREC_FP32_DC && o->dc_stall_window < 1)
       return fail(RD_ERR_INVALID_ARG, "dc_stall_window must be >= 1");
     if (o->upd_rows < 0 || o->band_rows < 0 || o->col_width < 0) return fail(RD_ERR_INVALID_ARG, "negative tile size");
@@ -591,6 +599,74 @@ rd_status autotune_plan(rd_pdhg* h, int H, int transform, int stage_base, int us
     dp.nupd = d.nupd;
     dp.fft_pp = d.fft_pp;
   }
+  RD_CUDA(cudaMemcpy(h->d_desc, h->h_desc, 3 * sizeof(Desc), cudaMemcpyHostToDevice));
+  return RD_OK;
+}
+
+// Fused update (opts.fused_update, FP32 defect correction, graph loop): iterations after the
+// first run k_col + k_updres, which needs a second transform buffer and per-band halo copies of
+// U.  Left off when its block does not fit the device's shared memory, and, with opts.autotune,
+// when a fused iteration is not at least 5% faster than an unfused one on this grid.
+rd_status plan_fused(rd_pdhg* h, int H, int stage_base, int usable) {
+  Desc& d = h->h_desc[1];
+  LaunchCfg& lc = h->cfg32;
+  const int U = d.upd_rows, nc = h->nc, nx = h->nx;
+  const int lines = nc * ((U + 4 * H) / 2);
+  const int smem = table_bytes<float>(nx, true, h->bc == RD_BC_NEUMANN) + lines * padded_len(nx) * (int)sizeof(cx<float>) +
+                   nc * (U + 2 * H) * nx * (int)sizeof(float) * (stage_base ? 2 : 1);
+  if (smem > usable) return RD_OK;
+  RD_TRY(dalloc(h, &h->WY32b, h->npts * sizeof(float)));
+  h->halo_bytes = (size_t)d.nupd * nc * 2 * H * nx * sizeof(float);
+  RD_TRY(dalloc(h, &h->halo32, h->halo_bytes));
+  Desc df = d;
+  df.fused = 1;
+  df.WYb[0] = h->WY32;
+  df.WYb[1] = h->WY32b;
+  df.halo = h->halo32;
+  lc.thr_updres = band_threads<float>(lines, nx);
+  lc.smem_updres = smem;
+  if (h->opts.autotune) {
+    // keep the fused update only if a fused iteration is faster than an unfused one here:
+    // kTuneIters iterations of each on the handle's zeroed arrays, a solve that never stops
+    cudaStream_t s = h->stream;
+    for (void* p : {(void*)h->D32, (void*)h->P32[0], (void*)h->P32[1], (void*)h->WY32, (void*)h->WY32b,
+                    (void*)h->r32, (void*)h->u32})
+      RD_CUDA(cudaMemsetAsync(p, 0, h->npts * sizeof(float), s));
+    RD_CUDA(cudaMemsetAsync(h->halo32, 0, h->halo_bytes, s));
+    State run{};
+    run.status = ST_ACTIVE;
+    run.max_iter = 1 << 30;
+    run.thresh = -1.0;
+    State* dst = h->d_state + 2;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    RD_CUDA(cudaEventCreate(&e0));
+    RD_CUDA(cudaEventCreate(&e1));
+    float t[2] = {1e30f, 1e30f};
+    bool ok = true;
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      for (int f = 0; f < 2 && ok; ++f) {
+        RD_CUDA(cudaMemcpyAsync(dst, &run, sizeof(State), cudaMemcpyHostToDevice, s));
+        ok = (f ? launch_fused<float>(df, dst, lc, s, nullptr, true) : launch_iteration<float>(d, dst, lc, s, nullptr)) ==
+             cudaSuccess;
+        RD_CUDA(cudaEventRecord(e0, s));
+        for (int k = 0; k < kTuneIters && ok; ++k)
+          ok = (f ? launch_fused<float>(df, dst, lc, s, nullptr, false) : launch_iteration<float>(d, dst, lc, s, nullptr)) ==
+               cudaSuccess;
+        RD_CUDA(cudaEventRecord(e1, s));
+        RD_CUDA(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        RD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        t[f] = std::min(t[f], ms);
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) cudaGetLastError();
+    // stream-launched timing flatters the fused loop by a few percent against the graph loop
+    // (measured): demand a 5% margin
+    if (!ok || t[1] >= 0.95f * t[0]) return RD_OK;
+  }
+  d = df;
   RD_CUDA(cudaMemcpy(h->d_desc, h->h_desc, 3 * sizeof(Desc), cudaMemcpyHostToDevice));
   return RD_OK;
 }
@@ -782,6 +858,11 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
     RD_TRY(h->dc ? autotune_plan<float>(h, H, transform, stage_base, usable)
                  : autotune_plan<double>(h, H, transform, stage_base, usable));
   }
+  if (h->dc && h->opts.fused_update && transform && h->opts.solve_loop == RD_LOOP_GRAPH) {
+    const int stage_base = rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT;
+    RD_TRY(plan_fused(h, H, stage_base, usable));
+  }
+  h->stats.fused_update = h->h_desc[1].fused;
   h->stats.plan_band_rows = h->h_desc[h->dc ? 1 : 0].band_rows;
   h->stats.plan_upd_rows = h->h_desc[h->dc ? 1 : 0].upd_rows;
   h->stats.plan_col_width = h->h_desc[h->dc ? 1 : 0].col_width;
@@ -992,6 +1073,7 @@ void rd_opts_default(rd_opts* o) {
   o->fft_unrolled = 1;
   o->autotune = 0;
   o->dc_stall_window = kDcStallWindow;
+  o->fused_update = 1;
 }
 
 rd_status rd_pdhg_create(rd_pdhg** out, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* reaction,
@@ -1098,7 +1180,9 @@ rd_status rd_pdhg_get_stats(const rd_pdhg* h, rd_stats* out) {
 rd_status rd_pdhg_reset_stats(rd_pdhg* h) {
   if (!h) return fail(RD_ERR_INVALID_ARG, "NULL handle");
   const int pb = h->stats.plan_band_rows, pc = h->stats.plan_col_width, pu = h->stats.plan_upd_rows;
+  const int fu = h->stats.fused_update;
   h->stats = rd_stats{};
+  h->stats.fused_update = fu;
   h->stats.plan_band_rows = pb;
   h->stats.plan_col_width = pc;
   h->stats.plan_upd_rows = pu;

@@ -40,8 +40,9 @@ struct Desc {
   int batched;       // 1: member of a batch (Slot control block, device-side phase machine)
   int fft_pp;        // bit 0 k_res, bit 1 k_col, bit 2 k_upd: transforms ping-pong between two buffers;
                      // bit 3: size-specialised unrolled transform passes (else looped passes)
-  int upd_rows;      // rows per CTA of k_upd (0: band_rows); k_res keeps band_rows
+  int upd_rows;      // rows per CTA of k_upd / k_updres (0: band_rows); k_res keeps band_rows
   int nupd;          // ceil(ny / upd_rows)
+  int fused;         // 1: iterations after the first run k_col + k_updres (fused update and residual)
   double hx2, hy2;   // 1/h_x^2, 1/h_y^2
   double dt, a, b;
   double p[6];
@@ -67,6 +68,12 @@ struct Desc {
   float* f32_p0;     // dual P_0 of the inner solve
   float* f32_r;      // r = F(u) rounded to FP32
   float* f32_u;      // u rounded to FP32
+  // fused update + residual (fused = 1): the transform buffer ping-pongs by update parity
+  // (WYb[(n-1)&1] holds the spectrum of update n, k_updres writes F(U_n) into WYb[n&1]); every
+  // k_updres block keeps U on its own halo rows in `halo` ([band][component][2H][nx]), written
+  // and read by that block only
+  void* WYb[2];
+  void* halo;
 };
 
 struct State {

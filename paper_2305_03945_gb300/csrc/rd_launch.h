@@ -15,6 +15,7 @@ struct LaunchCfg {
   int smem_res, smem_col, smem_upd;
   int transform;     // 0 when G = I (no spectral solve)
   int grid_upd;      // k_upd bands (0: grid_bands)
+  int thr_updres, smem_updres;  // fused update + residual kernel (k_updres)
 };
 
 // Raise the dynamic shared-memory limit of the PDHG kernels; *usable receives the bytes a launch may ask.
@@ -23,6 +24,10 @@ template <class T> cudaError_t set_kernel_smem_limits(int* usable);
 // kernels); with ev != NULL, events ev[0..3] are recorded around the three kernels.
 template <class T>
 cudaError_t launch_iteration(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
+// One PDHG iteration with the fused update (d.fused = 1, FP32 only): k_res (first only), k_col,
+// k_updres; events ev[0..3] around them as in launch_iteration.
+template <class T>
+cudaError_t launch_fused(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev, bool first);
 
 
 // The step-level kernels (begin, FP64 residual, mass) run point_blocks(nx, ny) blocks of 256

@@ -222,10 +222,11 @@ __device__ __forceinline__ void load_desc(Desc& dst, const Desc* src) {
 // block call it): r <= threshold -> converged; non-finite or 1e8-fold growth -> diverged;
 // max_iter updates done -> not converged; otherwise count the coming update.  A batch member
 // hands control back to its slot's defect-correction loop when the solve stops.
-__device__ inline void finalize_measure(const Desc& d, State* st, double* red, Slot* slot = nullptr) {
+__device__ inline void finalize_measure(const Desc& d, State* st, double* red, Slot* slot = nullptr, int nblk = 0) {
   __threadfence();
+  const int nb = nblk > 0 ? nblk : d.nbands;
   double tot = 0.0;
-  for (int c = 0; c < d.ncomp; ++c) tot += sqrt(sum_partials(d.partials + c * d.nbands, d.nbands, red));
+  for (int c = 0; c < d.ncomp; ++c) tot += sqrt(sum_partials(d.partials + c * nb, nb, red));
   if (threadIdx.x != 0) return;
   const double meas = d.meas_div_dt ? tot / d.dt : tot;
   st->ticket = 0u;
@@ -286,6 +287,12 @@ __device__ __forceinline__ void vst(T* __restrict__ p, const T* v) {
 #pragma unroll
     for (int k = 0; k < W; ++k) p[k] = v[k];
   }
+}
+
+// two adjacent entries of an array as one 8- or 16-byte load
+template <class T>
+__device__ __forceinline__ cx<T> ld_pair(const T* p) {
+  return *reinterpret_cast<const cx<T>*>(p);
 }
 
 // Copy rows g0 .. g0+nrows-1 (boundary-mapped) of a plane into shared memory (row stride nx).
@@ -562,7 +569,7 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
   const int nl = d.col_width >> 1;
   const int lnl = ilog2i(nl);
   const int ls = padded_len(ny);
-  T* WY = static_cast<T*>(d.WY) + c * plane;
+  T* WY = static_cast<T*>(d.fused ? d.WYb[(*((volatile const int*)&st->n) - 1) & 1] : d.WY) + c * plane;
   const bool per = d.bc == BC_PERIODIC;
   const int hn = ny >> 1, lh = logny - 1;
   const cx<T>* twy;
@@ -908,6 +915,242 @@ __device__ __forceinline__ void upd_body(const Desc& d, State* __restrict__ st, 
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// k_updres: update n of the PDHG iteration fused with the residual of the next one
+// ---------------------------------------------------------------------------------------
+
+// U_{n+1} on rows y0-H .. y0+rows+H-1 of one band from P~ (in buf, rows y0-2H .. y0+rows+2H-1):
+// band rows read U_n from X and write U_{n+1} back; halo rows read and write this block's own
+// copy in d.halo; every row also goes to the staging rows xs for the residual.
+template <class T, int K, int W>
+__device__ __forceinline__ void updres_points(const Desc& d, const cx<T>* buf, T* xs, int band, int y0, int rows,
+                                              int ls, int lpc) {
+  constexpr bool DC = sizeof(T) == 4;
+  constexpr int H = KT<K>::H;
+  constexpr int HY = 2 * H;
+  const int nx = d.nx, ny = d.ny, bc = d.bc;
+  const int nc = KT<K>::two ? 2 : 1;
+  const size_t plane = (size_t)nx * ny;
+  const int srows = rows + 2 * H;
+  T* X = static_cast<T*>(d.X);
+  T* Hb = static_cast<T*>(d.halo) + (size_t)band * nc * 2 * H * nx;
+  const T* Bs = static_cast<const T*>(d.base);
+  const int lw = W == 4 ? 2 : (W == 2 ? 1 : 0);
+  const int lv = d.lognx - lw;
+  const int total = srows << lv;
+  for (int v = threadIdx.x; v < total; v += blockDim.x) {
+    const int r = (v >> lv) - H;  // -H .. rows+H-1
+    const int j0 = (v & ((1 << lv) - 1)) * W;
+    const bool own = r >= 0 && r < rows;
+    const int slot = r < 0 ? r + H : r - rows + H;  // halo slot 0 .. 2H-1
+    T* u0 = own ? X + (size_t)(y0 + r) * nx + j0 : Hb + (size_t)slot * nx + j0;
+    T* u1 = own ? u0 + plane : Hb + (size_t)(2 * H + slot) * nx + j0;
+    T xa[W], xb[W], sa[W], sb[W];
+    vld<T, W>(u0, xa);
+    if constexpr (KT<K>::two) vld<T, W>(u1, xb);
+    if constexpr (DC && KT<K>::nonlinear) {
+      const size_t ob = (size_t)bcmap(y0 + r, ny, bc) * nx + j0;
+      vld<T, W>(Bs + ob, sa);
+      if constexpr (KT<K>::two) vld<T, W>(Bs + plane + ob, sb);
+    }
+    upd_group<T, K, true, W>(d, buf, ls, lpc, HY + r, j0, xa, xb, sa, sb);
+    vst<T, W>(u0, xa);
+    if constexpr (KT<K>::two) vst<T, W>(u1, xb);
+    T* x0 = xs + (size_t)(r + H) * nx + j0;
+#pragma unroll
+    for (int q = 0; q < W; ++q) x0[q] = xa[q];
+    if constexpr (KT<K>::two) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) x0[(size_t)srows * nx + q] = xb[q];
+    }
+  }
+}
+
+// One band of update n (the P and U updates of k_upd, with the transform spectrum and P~ on a
+// halo of 2H rows so that U_{n+1} is known on H halo rows) followed by the residual of update
+// n+1 on the band (k_res on the staged U_{n+1}: W = F(U_{n+1}), forward row transform into the
+// other transform buffer, norm partials, stopping decision).  FP32 defect correction with a
+// spectral preconditioner only.
+template <class T, int K>
+__device__ __forceinline__ void updres_body(const Desc& d, State* __restrict__ st, int band, unsigned char* smem_raw) {
+  constexpr int H = KT<K>::H;
+  constexpr int HY = 2 * H;
+  if (band >= d.nupd) return;
+
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nx = d.nx, ny = d.ny, bc = d.bc, lognx = d.lognx;
+  const int nc = KT<K>::two ? 2 : 1;
+  const size_t plane = (size_t)nx * ny;
+  const int y0 = band * d.upd_rows;
+  const int rows = min(d.upd_rows, ny - y0);
+  const int lrows = rows + 2 * HY;
+  const int lpc = lrows >> 1;
+  const int nl = nc * lpc;
+  const int ls = padded_len(nx);
+  const cx<T>* twx;
+  const cx<T>* dcx;
+  cx<T>* buf = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, d.twx, d.dcx, nx, true, bc == BC_NEUMANN, twx, dcx));
+  T* xs = reinterpret_cast<T*>(buf + nl * ls);
+  T* bs = xs + nc * (rows + 2 * H) * nx;
+  const int hn = nx >> 1, lh = lognx - 1;
+  if (!sweep_active(st, nullptr)) return;
+  const int n = *((volatile const int*)&st->n);  // already counts this update
+  const T* WY = static_cast<const T*>(d.WYb[(n - 1) & 1]);
+  T* Wout = static_cast<T*>(d.WYb[n & 1]);
+  if constexpr (sizeof(T) == 4 && base_stencil<K>()) {
+    const T* Bg = static_cast<const T*>(d.base);
+    for (int c = 0; c < nc; ++c)
+      stage_rows<T>(bs + c * (rows + 2 * H) * nx, Bg + c * plane, nx, lognx, ny, bc, y0 - H, rows + 2 * H);
+  }
+  if (SmemTables<T>::value && bc == BC_NEUMANN) __syncthreads();
+
+  // 1. the spectrum rows y0-2H .. y0+rows+2H-1 into buf, two rows per line (as k_upd)
+  if (bc == BC_PERIODIC) {
+    for (int g = tid; g < (nl << lh); g += nt) {
+      const int line = g >> lh, j = 2 * (g & (hn - 1));
+      const int c = KT<K>::two ? line / lpc : 0, m = line - c * lpc;
+      const int ga = bcmap(y0 - HY + 2 * m, ny, bc), gb = bcmap(y0 - HY + 2 * m + 1, ny, bc);
+      const T* Wc = WY + c * plane;
+      const cx<T> a = ld_pair(Wc + (size_t)ga * nx + j);
+      const cx<T> b = ld_pair(Wc + (size_t)gb * nx + j);
+      buf[line * ls + pidx(j)] = cx<T>{a.x, b.x};
+      buf[line * ls + pidx(j + 1)] = cx<T>{a.y, b.y};
+    }
+  } else {
+    for (int g = tid; g < (nl << lh); g += nt) {
+      const int line = g >> lh, k = g & (hn - 1);
+      const int c = KT<K>::two ? line / lpc : 0, m = line - c * lpc;
+      const int ga = bcmap(y0 - HY + 2 * m, ny, bc), gb = bcmap(y0 - HY + 2 * m + 1, ny, bc);
+      const T* Wa = WY + c * plane + (size_t)ga * nx;
+      const T* Wb = WY + c * plane + (size_t)gb * nx;
+      cx<T>* L = buf + line * ls;
+      const cx<T> w = dcx[k];
+      cx<T> zk, zkp;
+      if (k == 0) {
+        dct_inv_pre(cx<T>{Wa[0], Wb[0]}, cx<T>{T(0), T(0)}, w.x, w.y, zk, zkp);
+        const cx<T> Xm{Wa[hn], Wb[hn]};
+        const cx<T> wm = dcx[hn];
+        cx<T> zm, zmp;
+        dct_inv_pre(Xm, Xm, wm.x, wm.y, zm, zmp);
+        L[pidx(0)] = cx<T>{zk.x, -zk.y};
+        L[pidx(hn)] = cx<T>{zm.x, -zm.y};
+      } else {
+        dct_inv_pre(cx<T>{Wa[k], Wb[k]}, cx<T>{Wa[nx - k], Wb[nx - k]}, w.x, w.y, zk, zkp);
+        L[pidx(k)] = cx<T>{zk.x, -zk.y};
+        L[pidx(nx - k)] = cx<T>{zkp.x, -zkp.y};
+      }
+    }
+  }
+  __syncthreads();
+  // inverse row transform (the forward transform, conjugated for Neumann), in place
+  {
+    cx<T>* r = block_fft<T, -1>(buf, buf, nl, lognx, ls, twx, tid, nt, (d.fft_pp & 8) != 0);
+    if (bc == BC_PERIODIC) {
+      post_inplace(r, nl, lognx, ls, bc, dcx);
+      __syncthreads();
+    } else {
+      constexpr int MAXV = 16;
+      int chunk = (nt * MAXV) >> lognx;
+      if (chunk < 1) chunk = 1;
+      for (int l0 = 0; l0 < nl; l0 += chunk) {
+        const int cl = nl - l0 < chunk ? nl - l0 : chunk;
+        const int total = cl << lognx;
+        const int nthr = (total + MAXV - 1) / MAXV;
+        cx<T> v[MAXV];
+#pragma unroll
+        for (int q = 0; q < MAXV; ++q) {
+          const int g = tid + q * nthr;
+          if (tid < nthr && g < total) {
+            const cx<T> e = r[(l0 + (g >> lognx)) * ls + pidx(g & (nx - 1))];
+            v[q] = cx<T>{e.x, -e.y};
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < MAXV; ++q) {
+          const int g = tid + q * nthr;
+          if (tid < nthr && g < total) r[(l0 + (g >> lognx)) * ls + pidx(mk_perm(g & (nx - 1), nx))] = v[q];
+        }
+        __syncthreads();
+      }
+    }
+  }
+
+  // 2. P~ = P_n + (1 + omega) tau_p Y on all local rows (in place); P_{n+1} on the band rows
+  {
+    const T* Pin = static_cast<const T*>(d.P[(n - 1) & 1]);
+    T* Pout = static_cast<T*>(d.P[n & 1]);
+    const T tp = T(d.tau_p), tpe = T((1.0 + d.omega) * d.tau_p);
+    for (int g = tid; g < (nl << lh); g += nt) {
+      const int line = g >> lh, j = 2 * (g & (hn - 1));
+      const int c = KT<K>::two ? line / lpc : 0, m = line - c * lpc;
+      const int la = 2 * m, lb = 2 * m + 1;
+      const size_t oa = c * plane + (size_t)bcmap(y0 - HY + la, ny, bc) * nx + j;
+      const size_t ob = c * plane + (size_t)bcmap(y0 - HY + lb, ny, bc) * nx + j;
+      const cx<T> pa = ld_pair(Pin + oa);
+      const cx<T> pb = ld_pair(Pin + ob);
+      cx<T>* s0 = buf + line * ls + pidx(j);
+      cx<T>* s1 = buf + line * ls + pidx(j + 1);
+      const cx<T> y0v = *s0, y1v = *s1;
+      *s0 = cx<T>{pa.x + tpe * y0v.x, pb.x + tpe * y0v.y};
+      *s1 = cx<T>{pa.y + tpe * y1v.x, pb.y + tpe * y1v.y};
+      if (la >= HY && la < HY + rows) *reinterpret_cast<cx<T>*>(Pout + oa) = cx<T>{pa.x + tp * y0v.x, pa.y + tp * y1v.x};
+      if (lb >= HY && lb < HY + rows) *reinterpret_cast<cx<T>*>(Pout + ob) = cx<T>{pb.x + tp * y0v.y, pb.y + tp * y1v.y};
+    }
+  }
+  __syncthreads();
+
+  // 3. U_{n+1} on the band and H halo rows, staged in xs
+  if (nx >= V16<T>::n) updres_points<T, K, V16<T>::n>(d, buf, xs, band, y0, rows, ls, lpc);
+  else updres_points<T, K, 1>(d, buf, xs, band, y0, rows, ls, lpc);
+  __syncthreads();
+
+  // 4. W = F(U_{n+1}) on the band rows into buf (now free), forward row transform into Wout
+  T acc0 = T(0), acc1 = T(0);
+  if (nx >= V16<T>::n) res_points<T, K, V16<T>::n>(d, buf, xs, bs, y0, rows, ls, acc0, acc1);
+  else res_points<T, K, 1>(d, buf, xs, bs, y0, rows, ls, acc0, acc1);
+  __syncthreads();
+  {
+    const int rl = rows >> 1;
+    const cx<T>* res = block_fft<T, -1>(buf, buf, nc * rl, lognx, ls, twx, tid, nt, (d.fft_pp & 8) != 0);
+    for (int g = tid; g < ((nc * rl) << lh); g += nt) {
+      const int line = g >> lh, k = g & (hn - 1);
+      const int c = KT<K>::two ? line / rl : 0, m = line - c * rl;
+      const cx<T>* L = res + line * ls;
+      T* Wa = Wout + c * plane + (size_t)(y0 + 2 * m) * nx;
+      T* Wb = Wa + nx;
+      cx<T> ok, okp;
+      fwd_post(L, nx, bc, dcx, k, ok, okp);
+      Wa[k] = ok.x;
+      Wb[k] = ok.y;
+      if (k != 0) {
+        Wa[nx - k] = okp.x;
+        Wb[nx - k] = okp.y;
+      } else {
+        fwd_post(L, nx, bc, dcx, hn, ok, okp);
+        Wa[hn] = ok.x;
+        Wb[hn] = ok.y;
+      }
+    }
+  }
+
+  // 5. partial norms of F(U_{n+1}), ticket, stopping decision in the last block
+  const double s0 = block_sum((double)acc0, red);
+  const double s1 = KT<K>::two ? block_sum((double)acc1, red) : 0.0;
+  if (tid == 0) {
+    d.partials[band] = s0;
+    if (KT<K>::two) d.partials[d.nupd + band] = s1;
+  }
+  if (last_block(st, d.nupd)) finalize_measure(d, st, red, nullptr, d.nupd);
+}
+
+template <class T, int K>
+__global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_updres(const __grid_constant__ Desc d, State* __restrict__ st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  updres_body<T, K>(d, st, blockIdx.x, smem_raw);
+}
+
 template <class T, int K>
 __global__ void __launch_bounds__(MaxThreads<T>::value, MinBlocks<T>::value) k_upd(const __grid_constant__ Desc d, State* __restrict__ st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -952,11 +1195,44 @@ static cudaError_t launch_iter_k(const Desc& d, State* st, const LaunchCfg& c, c
   return cudaGetLastError();
 }
 
+// One PDHG iteration with the fused update: first = true launches k_res, k_col and k_updres (the
+// residual of U_0 comes first), first = false k_col and k_updres.  Events as in launch_iter_k.
+template <class T, int K>
+static cudaError_t launch_fused_k(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev,
+                                  bool first) {
+  if constexpr (sizeof(T) != 4 || K == KK_PCONLY) {
+    return cudaErrorNotSupported;
+  } else {
+    unsigned flags = cudaEventRecordDefault;
+    if (ev) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaError_t e = cudaStreamIsCapturing(s, &cs);
+      if (e != cudaSuccess) return e;
+      if (cs == cudaStreamCaptureStatusActive) flags = cudaEventRecordExternal;
+    }
+    cudaError_t e = cudaSuccess;
+    auto mark = [&](int i) {
+      if (ev && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[i], s, flags);
+    };
+    mark(0);
+    if (first) k_res<T, K><<<c.grid_bands, c.thr_res, c.smem_res, s>>>(d, st);
+    mark(1);
+    k_col<T, false><<<c.grid_cols, c.thr_col, c.smem_col, s>>>(d, st);
+    mark(2);
+    k_updres<T, K><<<c.grid_upd ? c.grid_upd : c.grid_bands, c.thr_updres, c.smem_updres, s>>>(d, st);
+    mark(3);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+}
+
 template <class T, int K>
 static cudaError_t allow_k(int optin) {
   cudaError_t e;
   if ((e = allow_smem_k(k_res<T, K>, optin)) != cudaSuccess) return e;
   if ((e = allow_smem_k(k_upd<T, K>, optin)) != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4 && K != KK_PCONLY)
+    if ((e = allow_smem_k(k_updres<T, K>, optin)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -973,6 +1249,20 @@ static cudaError_t allow_k(int optin) {
       case KK_SCHNAK: return launch_iter_k<T, KK_SCHNAK>(d, st, c, s, ev);                               \
       case KK_NONE_BIH: return launch_iter_k<T, KK_NONE_BIH>(d, st, c, s, ev);                           \
       default: return launch_iter_k<T, KK_PCONLY>(d, st, c, s, ev);                                     \
+    }                                                                                                    \
+  }                                                                                                      \
+  template <>                                                                                            \
+  cudaError_t launch_fused<T>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev, \
+                              bool first) {                                                              \
+    switch (kind_key(d)) {                                                                               \
+      case KK_NONE_LAP: return launch_fused_k<T, KK_NONE_LAP>(d, st, c, s, ev, first);                   \
+      case KK_AC: return launch_fused_k<T, KK_AC>(d, st, c, s, ev, first);                               \
+      case KK_CH_IMPL: return launch_fused_k<T, KK_CH_IMPL>(d, st, c, s, ev, first);                     \
+      case KK_CH_SPLIT: return launch_fused_k<T, KK_CH_SPLIT>(d, st, c, s, ev, first);                   \
+      case KK_GS: return launch_fused_k<T, KK_GS>(d, st, c, s, ev, first);                               \
+      case KK_SCHNAK: return launch_fused_k<T, KK_SCHNAK>(d, st, c, s, ev, first);                       \
+      case KK_NONE_BIH: return launch_fused_k<T, KK_NONE_BIH>(d, st, c, s, ev, first);                   \
+      default: return cudaErrorNotSupported;                                                             \
     }                                                                                                    \
   }                                                                                                      \
   template <>                                                                                            \

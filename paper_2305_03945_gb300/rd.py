@@ -49,7 +49,8 @@ class rd_opts(ctypes.Structure):
                 ("graph_k", ctypes.c_int), ("band_rows", ctypes.c_int), ("col_width", ctypes.c_int),
                 ("upd_rows", ctypes.c_int),
                 ("profile", ctypes.c_int), ("fft_buffers", ctypes.c_int), ("solve_loop", ctypes.c_int),
-                ("fft_unrolled", ctypes.c_int), ("autotune", ctypes.c_int), ("dc_stall_window", ctypes.c_int)]
+                ("fft_unrolled", ctypes.c_int), ("autotune", ctypes.c_int), ("dc_stall_window", ctypes.c_int),
+                ("fused_update", ctypes.c_int)]
 
 
 class rd_stats(ctypes.Structure):
@@ -57,7 +58,8 @@ class rd_stats(ctypes.Structure):
                 ("pdhg_iterations", ctypes.c_longlong), ("residual_passes", ctypes.c_longlong),
                 ("host_syncs", ctypes.c_longlong), ("kernel_ms", ctypes.c_double * 3),
                 ("kernel_samples", ctypes.c_longlong * 3), ("plan_band_rows", ctypes.c_int),
-                ("plan_col_width", ctypes.c_int), ("plan_upd_rows", ctypes.c_int)]
+                ("plan_col_width", ctypes.c_int), ("plan_upd_rows", ctypes.c_int),
+                ("fused_update", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -165,7 +167,7 @@ def _check(status, ok=(RD_OK,)):
 
 
 def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_inner_rtol=None,
-                 dc_max_outer=12, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1, autotune=0, upd_rows=0, dc_stall_window=None):
+                 dc_max_outer=12, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1, autotune=0, upd_rows=0, dc_stall_window=None, fused_update=1):
     """C structs for a ``workloads.Problem``."""
     g = rd_grid()
     g.ndim = 2
@@ -199,6 +201,7 @@ def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_i
     o.upd_rows = upd_rows
     if dc_stall_window is not None:
         o.dc_stall_window = dc_stall_window
+    o.fused_update = fused_update
     return g, rx, pc, o
 
 

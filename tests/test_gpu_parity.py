@@ -340,12 +340,13 @@ def test_defect_correction_outer_round_limit():
 @pytest.mark.parametrize("kind,op,p,bc,shape", [STEP_CASES[1], STEP_CASES[3], STEP_CASES[4]])
 def test_host_loop_matches_graph_loop(precision, kind, op, p, bc, shape):
     """The host-relaunched loop (plain graphs, for profilers) runs the same kernels as the
-    device-side WHILE loop: bit-identical steps and the same iteration and round counts."""
+    device-side WHILE loop (unfused): bit-identical steps and the same iteration and round
+    counts."""
     pb = _problem(kind, op, p, bc, *shape)
     uk = _state(pb, 13)
     res = []
     for loop in ("graph", "host"):
-        U, info, U_ref, _ = _compare_step(pb, uk, precision=precision, solve_loop=loop)
+        U, info, U_ref, _ = _compare_step(pb, uk, precision=precision, solve_loop=loop, fused_update=0)
         assert info["status"] == 0, info
         res.append((U, info["iterations"], info["outer_rounds"]))
     assert np.array_equal(res[0][0], res[1][0])
@@ -411,3 +412,49 @@ def test_different_band_heights_for_residual_and_update(bc, res_rows, upd_rows):
         assert np.linalg.norm(U - U_ref) <= 1e-9 * np.linalg.norm(U_ref)
         res.append(U)
     assert np.linalg.norm(res[0] - res[1]) <= 1e-10 * np.linalg.norm(U_ref)
+
+
+FUSED_CASES = [
+    ("allen_cahn", "laplacian", (), "periodic", (64, 64)),
+    ("allen_cahn", "laplacian", (), "neumann", (32, 128)),
+    ("ch_split", "neg_biharmonic", (), "neumann", (64, 32)),
+    ("ch_implicit", "neg_biharmonic", (), "periodic", (64, 64)),
+    ("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06), "periodic", (64, 64)),
+    ("schnakenberg", "laplacian", (0.05, 1.0, 100.0, 0.1305, 0.7695), "neumann", (64, 64)),
+]
+
+
+@pytest.mark.parametrize("kind,op,p,bc,shape", FUSED_CASES)
+@pytest.mark.parametrize("upd_rows", [2, 4])
+def test_fused_update_matches_oracle(kind, op, p, bc, shape, upd_rows):
+    """The fused update + residual kernel (per-band halo copies of U, ping-pong transform buffer)
+    gives a defect-corrected step within 1e-9 of the oracle, with several bands per grid."""
+    pb = _problem(kind, op, p, bc, *shape)
+    uk = _state(pb, 18)
+    rd = _rd()
+    with rd.Solver(pb, precision="fp32_dc", fused_update=1, upd_rows=upd_rows) as s:
+        assert s.stats()["fused_update"] == 1
+        out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        info = s.step(dev(uk), out)
+        U = host(out)
+    U_ref, _ = O.pdhg_step(pb, uk)
+    assert info["status"] == 0, info
+    assert info["outer_rounds"] >= 2
+    assert np.linalg.norm(U - U_ref) <= 1e-9 * np.linalg.norm(U_ref)
+
+
+def test_fused_update_twenty_steps_match_unfused():
+    """Allen-Cahn periodic 64^2, 20 steps: the fused and unfused loops agree to the step
+    tolerance (their FP32 inner iterates differ only by rounding)."""
+    rd = _rd()
+    w = WL.config_allen_cahn_periodic()
+    outs = []
+    for fu in (0, 1):
+        w = WL.config_allen_cahn_periodic()
+        pb = w.problem.replace(tol_kind="f_rel", tol=1e-11)
+        u = dev(w.u0)
+        with rd.Solver(pb, precision="fp32_dc", fused_update=fu) as s:
+            infos, st = s.solve(u, w.nsteps)
+        assert st == 0
+        outs.append(host(u))
+    assert rel_max(outs[1], outs[0]) <= 1e-9
