@@ -135,8 +135,10 @@ def kernel_bytes(pb, precision):
 
 
 # the files that define each profiled kernel: a traffic figure stays valid while they are unchanged
-SWEEP_SOURCES = ("rd_sweep.cuh", "rd_device.cuh", "rd_internal.h", "rd_launch.h", "rd_sweep_f32.cu", "rd_sweep_f64.cu")
-KERNEL_SOURCES = {"k_res": SWEEP_SOURCES, "k_col": SWEEP_SOURCES, "k_upd": SWEEP_SOURCES, "k_updres": SWEEP_SOURCES,
+SWEEP_SOURCES = ("rd_sweep.cuh", "rd_device.cuh", "rd_internal.h", "rd_launch.h", "rd_sweep_col.cu",
+                 "rd_sweep_f32_lap.cu", "rd_sweep_f32_bih.cu", "rd_sweep_f64_lap.cu", "rd_sweep_f64_bih.cu")
+KERNEL_SOURCES = {"k_res": SWEEP_SOURCES, "k_col": SWEEP_SOURCES, "k_upd": SWEEP_SOURCES,
+                  "k_updres": SWEEP_SOURCES + ("rd_fused_lap.cu", "rd_fused_bih.cu"),
                   "k_resid64": SWEEP_SOURCES + ("rd_kernels.cu",)}
 
 
@@ -416,7 +418,7 @@ def run_ours(args, rank, world, local_rank):
         st64 = sv64.stats()
         kb64 = kernel_bytes(pb, "fp64")
         per64 = {}
-        for i, nm in enumerate(names):
+        for i, nm in enumerate(("k_res", "k_col", "k_updres" if st64.get("fused_update") else "k_upd")):
             n = st64["kernel_samples"][i]
             if n:
                 a = st64["kernel_ms"][i] / n

@@ -162,7 +162,7 @@ typedef struct {
     int dc_stall_window;  /* DC: the FP32 inner solve also stops (as converged) when its residual
                              has not halved for this many updates (its rounding floor); default
                              8                                                                   */
-    int fused_update;     /* 1 (default): FP32 defect correction in the graph loop runs the update
+    int fused_update;     /* 1 (default): FP32 defect correction (either loop) runs the update
                              of each iteration fused with the next residual (k_col + k_updres
                              per iteration; k_res only before the first update) when its block
                              fits, and with autotune only where it measures faster; 0: never.

@@ -226,6 +226,8 @@ struct rd_pdhg {
   // RD_LOOP_HOST: graph_k PDHG iterations without conditional nodes, relaunched by the host
   cudaGraph_t hgraph = nullptr;
   cudaGraphExec_t hexec = nullptr;
+  cudaGraph_t hgraph1 = nullptr;      // fused update: the first launch of an inner solve
+  cudaGraphExec_t hexec1 = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // around the first iteration's kernels
   int kernels_per_iter = 0;
   rd_stats stats{};
@@ -405,23 +407,31 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   return RD_OK;
 }
 
-// RD_LOOP_HOST: one graph of graph_k PDHG iterations (profiling events around the first).
-rd_status capture_iter_graph(rd_pdhg* h) {
+// RD_LOOP_HOST: one graph of graph_k PDHG iterations (profiling events around the first).  With
+// the fused update a second graph starts each inner solve: it clears the halo copies and its
+// first iteration launches k_res; the profiling events sit in that graph only.
+rd_status capture_iter_graph(rd_pdhg* h, bool start, cudaGraph_t* graph, cudaGraphExec_t* exec) {
   const int K = h->opts.graph_k;
-  RD_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < K; ++k) {
-    cudaEvent_t* ev = (k == 0 && h->opts.profile) ? h->ev : nullptr;
-    const cudaError_t e = h->dc ? launch_iteration<float>(h->h_desc[1], h->d_state + 1, h->cfg32, h->cap_stream, ev)
-                                : launch_iteration<double>(h->h_desc[0], h->d_state + 0, h->cfg64, h->cap_stream, ev);
-    if (e != cudaSuccess) {
-      cudaGraph_t g = nullptr;
-      cudaStreamEndCapture(h->cap_stream, &g);
-      if (g) cudaGraphDestroy(g);
-      return fail(RD_ERR_CUDA, std::string("kernel launch during capture: ") + cudaGetErrorString(e));
-    }
+  const Desc& dd = h->dc ? h->h_desc[1] : h->h_desc[0];
+  const bool fused = h->dc && dd.fused;
+  cudaStream_t cs = h->cap_stream;
+  RD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  if (fused && start) e = cudaMemsetAsync(h->halo32, 0, h->halo_bytes, cs);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    cudaEvent_t* ev = (k == 0 && h->opts.profile && (start || !fused)) ? h->ev : nullptr;
+    if (fused) e = launch_fused<float>(dd, h->d_state + 1, h->cfg32, cs, ev, start && k == 0);
+    else if (h->dc) e = launch_iteration<float>(dd, h->d_state + 1, h->cfg32, cs, ev);
+    else e = launch_iteration<double>(dd, h->d_state + 0, h->cfg64, cs, ev);
   }
-  RD_CUDA(cudaStreamEndCapture(h->cap_stream, &h->hgraph));
-  RD_CUDA(cudaGraphInstantiate(&h->hexec, h->hgraph, 0));
+  if (e != cudaSuccess) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(cs, &g);
+    if (g) cudaGraphDestroy(g);
+    return fail(RD_ERR_CUDA, std::string("kernel launch during capture: ") + cudaGetErrorString(e));
+  }
+  RD_CUDA(cudaStreamEndCapture(cs, graph));
+  RD_CUDA(cudaGraphInstantiate(exec, *graph, 0));
   return RD_OK;
 }
 
@@ -430,7 +440,11 @@ rd_status capture_graphs(rd_pdhg* h) {
   h->kernels_per_iter = h->dc && h->h_desc[1].fused ? 2 : (lc.transform ? 3 : 2);
   if (h->opts.profile)
     for (int i = 0; i < 4; ++i) RD_CUDA(cudaEventCreate(&h->ev[i]));
-  if (h->opts.solve_loop == RD_LOOP_HOST) return capture_iter_graph(h);
+  if (h->opts.solve_loop == RD_LOOP_HOST) {
+    RD_TRY(capture_iter_graph(h, false, &h->hgraph, &h->hexec));
+    if (h->dc && h->h_desc[1].fused) RD_TRY(capture_iter_graph(h, true, &h->hgraph1, &h->hexec1));
+    return RD_OK;
+  }
   RD_TRY(capture_step_graph(h, true, &h->graph[0], &h->gexec[0]));
   if (h->dc) RD_TRY(capture_step_graph(h, false, &h->graph[1], &h->gexec[1]));
   return RD_OK;
@@ -603,7 +617,7 @@ rd_status autotune_plan(rd_pdhg* h, int H, int transform, int stage_base, int us
   return RD_OK;
 }
 
-// Fused update (opts.fused_update, FP32 defect correction, graph loop): iterations after the
+// Fused update (opts.fused_update, FP32 defect correction, either loop): iterations after the
 // first run k_col + k_updres, which needs a second transform buffer and per-band halo copies of
 // U.  Left off when its block does not fit the device's shared memory, and, with opts.autotune,
 // when a fused iteration is not at least 5% faster than an unfused one on this grid.
@@ -858,7 +872,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
     RD_TRY(h->dc ? autotune_plan<float>(h, H, transform, stage_base, usable)
                  : autotune_plan<double>(h, H, transform, stage_base, usable));
   }
-  if (h->dc && h->opts.fused_update && transform && h->opts.solve_loop == RD_LOOP_GRAPH) {
+  if (h->dc && h->opts.fused_update && transform) {
     const int stage_base = rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT;
     RD_TRY(plan_fused(h, H, stage_base, usable));
   }
@@ -925,18 +939,19 @@ rd_status graph_round(rd_pdhg* h, int which) {
 }
 
 // RD_LOOP_HOST: launch the graph_k-iteration graph, read solve state `which` back and account.
-rd_status iter_round(rd_pdhg* h, int which) {
+rd_status iter_round(rd_pdhg* h, int which, bool start) {
   cudaStream_t s = h->stream;
   const int n_before = h->h_state[which].n;
-  RD_CUDA(cudaGraphLaunch(h->hexec, s));
+  const bool first_graph = start && h->hexec1;
+  RD_CUDA(cudaGraphLaunch(first_graph ? h->hexec1 : h->hexec, s));
   RD_CUDA(cudaMemcpyAsync(h->h_state + which, h->d_state + which, sizeof(State), cudaMemcpyDeviceToHost, s));
   RD_CUDA(cudaStreamSynchronize(s));
   const int updates = h->h_state[which].n - n_before;
   h->stats.graph_launches += 1;
-  h->stats.kernel_launches += (long long)h->opts.graph_k * h->kernels_per_iter;
+  h->stats.kernel_launches += (long long)h->opts.graph_k * h->kernels_per_iter + (first_graph ? 1 : 0);
   h->stats.host_syncs += 1;
   h->stats.pdhg_iterations += updates;
-  if (h->opts.profile) {
+  if (h->opts.profile && (first_graph || !h->hexec1)) {
     float ms = 0.f;
     RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
     h->stats.kernel_ms[0] += ms;
@@ -974,7 +989,7 @@ rd_status step_host(rd_pdhg* h, rd_step_info* info) {
   if (!h->dc) {
     RD_CUDA(cudaMemsetAsync(h->P64[0], 0, h->npts * sizeof(double), s));
     for (int it = 0; it <= max_launch; ++it) {
-      RD_TRY(iter_round(h, 0));
+      RD_TRY(iter_round(h, 0, it == 0));
       if (h->h_state[0].status != ST_ACTIVE) break;
     }
     final_status = h->h_state[0].status;
@@ -992,7 +1007,7 @@ rd_status step_host(rd_pdhg* h, rd_step_info* info) {
       h->stats.host_syncs += 1;
       if (h->h_state[0].status != ST_ACTIVE) break;  // converged, diverged, or out of rounds
       for (int it = 0; it <= max_launch; ++it) {
-        RD_TRY(iter_round(h, 1));
+        RD_TRY(iter_round(h, 1, it == 0));
         if (h->h_state[1].status != ST_ACTIVE) break;
       }
       inner_total += h->h_state[1].n;
@@ -1200,6 +1215,8 @@ void rd_pdhg_destroy(rd_pdhg* h) {
   }
   if (h->hexec) cudaGraphExecDestroy(h->hexec);
   if (h->hgraph) cudaGraphDestroy(h->hgraph);
+  if (h->hexec1) cudaGraphExecDestroy(h->hexec1);
+  if (h->hgraph1) cudaGraphDestroy(h->hgraph1);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

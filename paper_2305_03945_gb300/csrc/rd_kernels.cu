@@ -1,6 +1,7 @@
 // Step-level sm_103a kernels of the PDHG solver (arxiv 2305.03945, Section 2.1, Algorithm 1):
 // the step set-up, the FP64 residual of defect correction, the FP64 update and the mass sum.
-// The per-iteration sweeps live in rd_sweep.cuh (instantiated in rd_sweep_f32.cu / _f64.cu).
+// The per-iteration sweeps live in rd_sweep.cuh (instantiated per equation group in rd_sweep_{f32,f64}_{lap,bih}.cu,
+// rd_fused_{lap,bih}.cu and rd_sweep_col.cu).
 //
 // One PDHG iteration is three launches:
 //   k_res  (row bands)      W = F(U_n) (eq. F(U) rd equation / F(U) CH / Section 3.4.1), the

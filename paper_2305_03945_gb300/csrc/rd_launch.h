@@ -18,6 +18,31 @@ struct LaunchCfg {
   int thr_updres, smem_updres;  // fused update + residual kernel (k_updres)
 };
 
+// Equation keys of the sweep templates (kind_key maps a Desc to one).
+enum KKey {
+  KK_NONE_LAP = 0, KK_AC = 1, KK_CH_IMPL = 2, KK_CH_SPLIT = 3, KK_GS = 4, KK_SCHNAK = 5,
+  KK_NONE_BIH = 6, KK_PCONLY = 7
+};
+
+// Per-key pieces of the sweep, specialised for every (T, K) in the rd_sweep_*.cu units (one unit
+// per group of keys, so that the kernels compile in parallel): one iteration, a k_res launch, and
+// the shared-memory limits of k_res and k_upd.
+template <class T, int K>
+cudaError_t launch_iter_kind(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
+template <class T, int K>
+cudaError_t launch_res(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s);
+template <class T, int K>
+cudaError_t allow_kind(int optin);
+// The fused FP32 iteration of key K and the shared-memory limit of its k_updres (rd_fused_*.cu).
+template <int K>
+cudaError_t launch_fused_kind(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev,
+                              bool first);
+template <int K>
+cudaError_t allow_fused_kind(int optin);
+// The column-transform kernel k_col (pc: the preconditioner-only variant), rd_sweep_col.cu.
+template <class T>
+cudaError_t launch_col(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, bool pc);
+
 // Raise the dynamic shared-memory limit of the PDHG kernels; *usable receives the bytes a launch may ask.
 template <class T> cudaError_t set_kernel_smem_limits(int* usable);
 // One PDHG iteration (k_res, k_col, k_upd) of the solve described by d (passed by value to the

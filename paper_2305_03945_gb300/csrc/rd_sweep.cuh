@@ -22,12 +22,6 @@
 
 namespace rd {
 
-// Equation keys of the sweep templates.
-enum KKey {
-  KK_NONE_LAP = 0, KK_AC = 1, KK_CH_IMPL = 2, KK_CH_SPLIT = 3, KK_GS = 4, KK_SCHNAK = 5,
-  KK_NONE_BIH = 6, KK_PCONLY = 7
-};
-
 __host__ __device__ inline int kind_key(const Desc& d) {
   if (d.mode == MODE_PRECOND_ONLY) return KK_PCONLY;
   if (d.kind == RX_NONE) return d.op == OP_BIHARM ? KK_NONE_BIH : KK_NONE_LAP;
@@ -1168,26 +1162,31 @@ static cudaError_t allow_smem_k(K_ kernel, int optin) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
+// Event-record flags for ev on stream s: inside a stream capture the events become external
+// event-record nodes of the graph; outside one they are ordinary records (the external flag is
+// for capture only).
+static inline cudaError_t record_flags(cudaStream_t s, const cudaEvent_t* ev, unsigned* flags) {
+  *flags = cudaEventRecordDefault;
+  if (!ev) return cudaSuccess;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e == cudaSuccess && cs == cudaStreamCaptureStatusActive) *flags = cudaEventRecordExternal;
+  return e;
+}
+
 template <class T, int K>
 static cudaError_t launch_iter_k(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev) {
   constexpr bool PC = K == KK_PCONLY;
-  // inside a stream capture the events become external event-record nodes of the graph;
-  // outside one they are ordinary records (the external flag is for capture only)
-  unsigned flags = cudaEventRecordDefault;
-  if (ev) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaError_t e = cudaStreamIsCapturing(s, &cs);
-    if (e != cudaSuccess) return e;
-    if (cs == cudaStreamCaptureStatusActive) flags = cudaEventRecordExternal;
-  }
-  cudaError_t e = cudaSuccess;
+  unsigned flags;
+  cudaError_t e = record_flags(s, ev, &flags);
+  if (e != cudaSuccess) return e;
   auto mark = [&](int i) {
     if (ev && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[i], s, flags);
   };
   mark(0);
   k_res<T, K><<<c.grid_bands, c.thr_res, c.smem_res, s>>>(d, st);
   mark(1);
-  if (c.transform) k_col<T, PC><<<c.grid_cols, c.thr_col, c.smem_col, s>>>(d, st);
+  if (c.transform && e == cudaSuccess) e = launch_col<T>(d, st, c, s, PC);
   mark(2);
   k_upd<T, K><<<c.grid_upd ? c.grid_upd : c.grid_bands, c.thr_upd, c.smem_upd, s>>>(d, st);
   mark(3);
@@ -1197,93 +1196,123 @@ static cudaError_t launch_iter_k(const Desc& d, State* st, const LaunchCfg& c, c
 
 // One PDHG iteration with the fused update: first = true launches k_res, k_col and k_updres (the
 // residual of U_0 comes first), first = false k_col and k_updres.  Events as in launch_iter_k.
-template <class T, int K>
+template <int K>
 static cudaError_t launch_fused_k(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev,
                                   bool first) {
-  if constexpr (sizeof(T) != 4 || K == KK_PCONLY) {
-    return cudaErrorNotSupported;
-  } else {
-    unsigned flags = cudaEventRecordDefault;
-    if (ev) {
-      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-      cudaError_t e = cudaStreamIsCapturing(s, &cs);
-      if (e != cudaSuccess) return e;
-      if (cs == cudaStreamCaptureStatusActive) flags = cudaEventRecordExternal;
-    }
-    cudaError_t e = cudaSuccess;
-    auto mark = [&](int i) {
-      if (ev && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[i], s, flags);
-    };
-    mark(0);
-    if (first) k_res<T, K><<<c.grid_bands, c.thr_res, c.smem_res, s>>>(d, st);
-    mark(1);
-    k_col<T, false><<<c.grid_cols, c.thr_col, c.smem_col, s>>>(d, st);
-    mark(2);
-    k_updres<T, K><<<c.grid_upd ? c.grid_upd : c.grid_bands, c.thr_updres, c.smem_updres, s>>>(d, st);
-    mark(3);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+  unsigned flags;
+  cudaError_t e = record_flags(s, ev, &flags);
+  if (e != cudaSuccess) return e;
+  auto mark = [&](int i) {
+    if (ev && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[i], s, flags);
+  };
+  mark(0);
+  if (first && e == cudaSuccess) e = launch_res<float, K>(d, st, c, s);
+  mark(1);
+  if (e == cudaSuccess) e = launch_col<float>(d, st, c, s, false);
+  mark(2);
+  k_updres<float, K><<<c.grid_upd ? c.grid_upd : c.grid_bands, c.thr_updres, c.smem_updres, s>>>(d, st);
+  mark(3);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// The kernels of one equation key K in arithmetic T: its iteration launcher, its k_res launcher
+// (for the fused iteration, whose k_res instance must be the one whose limits were raised) and
+// the shared-memory limits of k_res and k_upd.  One unit per group of keys, compiled in parallel.
+#define RD_SWEEP_KIND(T, K)                                                                            \
+  template <>                                                                                          \
+  cudaError_t launch_iter_kind<T, K>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s,    \
+                                     cudaEvent_t* ev) {                                                \
+    return launch_iter_k<T, K>(d, st, c, s, ev);                                                       \
+  }                                                                                                    \
+  template <>                                                                                          \
+  cudaError_t launch_res<T, K>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s) {         \
+    k_res<T, K><<<c.grid_bands, c.thr_res, c.smem_res, s>>>(d, st);                                    \
+    return cudaGetLastError();                                                                         \
+  }                                                                                                    \
+  template <>                                                                                          \
+  cudaError_t allow_kind<T, K>(int optin) {                                                            \
+    cudaError_t e = allow_smem_k(k_res<T, K>, optin);                                                  \
+    return e != cudaSuccess ? e : allow_smem_k(k_upd<T, K>, optin);                                    \
   }
-}
 
-template <class T, int K>
-static cudaError_t allow_k(int optin) {
-  cudaError_t e;
-  if ((e = allow_smem_k(k_res<T, K>, optin)) != cudaSuccess) return e;
-  if ((e = allow_smem_k(k_upd<T, K>, optin)) != cudaSuccess) return e;
-  if constexpr (sizeof(T) == 4 && K != KK_PCONLY)
-    if ((e = allow_smem_k(k_updres<T, K>, optin)) != cudaSuccess) return e;
-  return cudaSuccess;
-}
+// The fused update kernel of equation key K (FP32 inner solve only).
+#define RD_FUSED_KIND(K)                                                                               \
+  template <>                                                                                          \
+  cudaError_t launch_fused_kind<K>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s,      \
+                                   cudaEvent_t* ev, bool first) {                                      \
+    return launch_fused_k<K>(d, st, c, s, ev, first);                                                  \
+  }                                                                                                    \
+  template <>                                                                                          \
+  cudaError_t allow_fused_kind<K>(int optin) {                                                         \
+    return allow_smem_k(k_updres<float, K>, optin);                                                    \
+  }
 
-#define RD_SWEEP_INSTANTIATE(T)                                                                         \
-  template <>                                                                                            \
-  cudaError_t launch_iteration<T>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s,           \
-                                  cudaEvent_t* ev) {                                                     \
-    switch (kind_key(d)) {                                                                               \
-      case KK_NONE_LAP: return launch_iter_k<T, KK_NONE_LAP>(d, st, c, s, ev);                           \
-      case KK_AC: return launch_iter_k<T, KK_AC>(d, st, c, s, ev);                                       \
-      case KK_CH_IMPL: return launch_iter_k<T, KK_CH_IMPL>(d, st, c, s, ev);                             \
-      case KK_CH_SPLIT: return launch_iter_k<T, KK_CH_SPLIT>(d, st, c, s, ev);                           \
-      case KK_GS: return launch_iter_k<T, KK_GS>(d, st, c, s, ev);                                       \
-      case KK_SCHNAK: return launch_iter_k<T, KK_SCHNAK>(d, st, c, s, ev);                               \
-      case KK_NONE_BIH: return launch_iter_k<T, KK_NONE_BIH>(d, st, c, s, ev);                           \
-      default: return launch_iter_k<T, KK_PCONLY>(d, st, c, s, ev);                                     \
-    }                                                                                                    \
-  }                                                                                                      \
-  template <>                                                                                            \
-  cudaError_t launch_fused<T>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev, \
-                              bool first) {                                                              \
-    switch (kind_key(d)) {                                                                               \
-      case KK_NONE_LAP: return launch_fused_k<T, KK_NONE_LAP>(d, st, c, s, ev, first);                   \
-      case KK_AC: return launch_fused_k<T, KK_AC>(d, st, c, s, ev, first);                               \
-      case KK_CH_IMPL: return launch_fused_k<T, KK_CH_IMPL>(d, st, c, s, ev, first);                     \
-      case KK_CH_SPLIT: return launch_fused_k<T, KK_CH_SPLIT>(d, st, c, s, ev, first);                   \
-      case KK_GS: return launch_fused_k<T, KK_GS>(d, st, c, s, ev, first);                               \
-      case KK_SCHNAK: return launch_fused_k<T, KK_SCHNAK>(d, st, c, s, ev, first);                       \
-      case KK_NONE_BIH: return launch_fused_k<T, KK_NONE_BIH>(d, st, c, s, ev, first);                   \
-      default: return cudaErrorNotSupported;                                                             \
-    }                                                                                                    \
-  }                                                                                                      \
-  template <>                                                                                            \
-  cudaError_t set_kernel_smem_limits<T>(int* usable) {                                                   \
-    int dev = 0, optin = 0;                                                                              \
-    cudaError_t e;                                                                                       \
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;                                              \
+// k_col and the per-key dispatch of arithmetic T.
+#define RD_SWEEP_COMMON(T)                                                                             \
+  template <>                                                                                          \
+  cudaError_t launch_col<T>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, bool pc) {   \
+    if (pc) k_col<T, true><<<c.grid_cols, c.thr_col, c.smem_col, s>>>(d, st);                          \
+    else k_col<T, false><<<c.grid_cols, c.thr_col, c.smem_col, s>>>(d, st);                            \
+    return cudaGetLastError();                                                                         \
+  }                                                                                                    \
+  template <>                                                                                          \
+  cudaError_t launch_iteration<T>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s,         \
+                                  cudaEvent_t* ev) {                                                   \
+    switch (kind_key(d)) {                                                                             \
+      case KK_NONE_LAP: return launch_iter_kind<T, KK_NONE_LAP>(d, st, c, s, ev);                      \
+      case KK_AC: return launch_iter_kind<T, KK_AC>(d, st, c, s, ev);                                  \
+      case KK_CH_IMPL: return launch_iter_kind<T, KK_CH_IMPL>(d, st, c, s, ev);                        \
+      case KK_CH_SPLIT: return launch_iter_kind<T, KK_CH_SPLIT>(d, st, c, s, ev);                      \
+      case KK_GS: return launch_iter_kind<T, KK_GS>(d, st, c, s, ev);                                  \
+      case KK_SCHNAK: return launch_iter_kind<T, KK_SCHNAK>(d, st, c, s, ev);                          \
+      case KK_NONE_BIH: return launch_iter_kind<T, KK_NONE_BIH>(d, st, c, s, ev);                      \
+      default: return launch_iter_kind<T, KK_PCONLY>(d, st, c, s, ev);                                 \
+    }                                                                                                  \
+  }                                                                                                    \
+  template <>                                                                                          \
+  cudaError_t set_kernel_smem_limits<T>(int* usable) {                                                 \
+    int dev = 0, optin = 0;                                                                            \
+    cudaError_t e;                                                                                     \
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;                                            \
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) \
-      return e;                                                                                          \
-    if ((e = allow_k<T, KK_NONE_LAP>(optin)) != cudaSuccess) return e;                                   \
-    if ((e = allow_k<T, KK_AC>(optin)) != cudaSuccess) return e;                                         \
-    if ((e = allow_k<T, KK_CH_IMPL>(optin)) != cudaSuccess) return e;                                    \
-    if ((e = allow_k<T, KK_CH_SPLIT>(optin)) != cudaSuccess) return e;                                   \
-    if ((e = allow_k<T, KK_GS>(optin)) != cudaSuccess) return e;                                         \
-    if ((e = allow_k<T, KK_SCHNAK>(optin)) != cudaSuccess) return e;                                     \
-    if ((e = allow_k<T, KK_NONE_BIH>(optin)) != cudaSuccess) return e;                                   \
-    if ((e = allow_k<T, KK_PCONLY>(optin)) != cudaSuccess) return e;                                     \
-    if ((e = allow_smem_k(k_col<T, false>, optin)) != cudaSuccess) return e;                             \
-    if ((e = allow_smem_k(k_col<T, true>, optin)) != cudaSuccess) return e;                              \
-    if (usable) *usable = optin - 1024;                                                                  \
-    return cudaSuccess;                                                                                  \
+      return e;                                                                                        \
+    if ((e = allow_kind<T, KK_NONE_LAP>(optin)) != cudaSuccess) return e;                              \
+    if ((e = allow_kind<T, KK_AC>(optin)) != cudaSuccess) return e;                                    \
+    if ((e = allow_kind<T, KK_CH_IMPL>(optin)) != cudaSuccess) return e;                               \
+    if ((e = allow_kind<T, KK_CH_SPLIT>(optin)) != cudaSuccess) return e;                              \
+    if ((e = allow_kind<T, KK_GS>(optin)) != cudaSuccess) return e;                                    \
+    if ((e = allow_kind<T, KK_SCHNAK>(optin)) != cudaSuccess) return e;                                \
+    if ((e = allow_kind<T, KK_NONE_BIH>(optin)) != cudaSuccess) return e;                              \
+    if ((e = allow_kind<T, KK_PCONLY>(optin)) != cudaSuccess) return e;                                \
+    if ((e = allow_smem_k(k_col<T, false>, optin)) != cudaSuccess) return e;                           \
+    if ((e = allow_smem_k(k_col<T, true>, optin)) != cudaSuccess) return e;                            \
+    if constexpr (sizeof(T) == 4) {                                                                    \
+      if ((e = allow_fused_kind<KK_NONE_LAP>(optin)) != cudaSuccess) return e;                         \
+      if ((e = allow_fused_kind<KK_AC>(optin)) != cudaSuccess) return e;                               \
+      if ((e = allow_fused_kind<KK_CH_IMPL>(optin)) != cudaSuccess) return e;                          \
+      if ((e = allow_fused_kind<KK_CH_SPLIT>(optin)) != cudaSuccess) return e;                         \
+      if ((e = allow_fused_kind<KK_GS>(optin)) != cudaSuccess) return e;                               \
+      if ((e = allow_fused_kind<KK_SCHNAK>(optin)) != cudaSuccess) return e;                           \
+      if ((e = allow_fused_kind<KK_NONE_BIH>(optin)) != cudaSuccess) return e;                         \
+    }                                                                                                  \
+    if (usable) *usable = optin - 1024;                                                                \
+    return cudaSuccess;                                                                                \
+  }                                                                                                    \
+  template <>                                                                                          \
+  cudaError_t launch_fused<T>(const Desc& d, State* st, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev, \
+                              bool first) {                                                            \
+    if constexpr (sizeof(T) != 4) return cudaErrorNotSupported;                                        \
+    switch (kind_key(d)) {                                                                             \
+      case KK_NONE_LAP: return launch_fused_kind<KK_NONE_LAP>(d, st, c, s, ev, first);                 \
+      case KK_AC: return launch_fused_kind<KK_AC>(d, st, c, s, ev, first);                             \
+      case KK_CH_IMPL: return launch_fused_kind<KK_CH_IMPL>(d, st, c, s, ev, first);                   \
+      case KK_CH_SPLIT: return launch_fused_kind<KK_CH_SPLIT>(d, st, c, s, ev, first);                 \
+      case KK_GS: return launch_fused_kind<KK_GS>(d, st, c, s, ev, first);                             \
+      case KK_SCHNAK: return launch_fused_kind<KK_SCHNAK>(d, st, c, s, ev, first);                     \
+      case KK_NONE_BIH: return launch_fused_kind<KK_NONE_BIH>(d, st, c, s, ev, first);                 \
+      default: return cudaErrorNotSupported;                                                           \
+    }                                                                                                  \
   }
 
 }  // namespace rd

@@ -336,17 +336,22 @@ def test_defect_correction_outer_round_limit():
     assert info["outer_rounds"] == 2 and info["iterations"] > 0
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_dc"])
+@pytest.mark.parametrize("precision,fused", [("fp64", 0), ("fp32_dc", 0), ("fp32_dc", 1)])
 @pytest.mark.parametrize("kind,op,p,bc,shape", [STEP_CASES[1], STEP_CASES[3], STEP_CASES[4]])
-def test_host_loop_matches_graph_loop(precision, kind, op, p, bc, shape):
-    """The host-relaunched loop (plain graphs, for profilers) runs the same kernels as the
-    device-side WHILE loop (unfused): bit-identical steps and the same iteration and round
-    counts."""
+def test_host_loop_matches_graph_loop(precision, fused, kind, op, p, bc, shape):
+    """The host-relaunched loop (plain graphs, for profilers) runs the same kernels in the same
+    order as the device-side WHILE loop, unfused or with the fused update: bit-identical steps
+    and the same iteration and round counts."""
+    rd = _rd()
     pb = _problem(kind, op, p, bc, *shape)
     uk = _state(pb, 13)
     res = []
     for loop in ("graph", "host"):
-        U, info, U_ref, _ = _compare_step(pb, uk, precision=precision, solve_loop=loop, fused_update=0)
+        with rd.Solver(pb, precision=precision, solve_loop=loop, fused_update=fused) as s:
+            assert s.stats()["fused_update"] == fused
+            out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+            info = s.step(dev(uk), out)
+            U = host(out)
         assert info["status"] == 0, info
         res.append((U, info["iterations"], info["outer_rounds"]))
     assert np.array_equal(res[0][0], res[1][0])
