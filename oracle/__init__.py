@@ -11,6 +11,7 @@ Modules
   dense      dense matrices written out from the paper's block forms (Section 2.1, Remark 1),
              dense Newton for the implicit step; used only as pins
   theory     closed forms of Theorem 1 / Corollary 1 / Appendix A
+  adapt      the adaptive time step size of Section 2.2 on top of rd_oracle's implicit step
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` (dense matrices, eigenmodes, closed-form iteration recurrences,
