@@ -446,6 +446,12 @@ def run_ours(args, rank, world, local_rank):
                   "max_rel_vs_oracle": float(np.max(np.abs(got - U_ref)) / np.max(np.abs(U_ref)))}
 
     sv.close()
+
+    # ---- adaptive time step size (Section 2.2) on the same workload ----
+    adaptive = None
+    if rank == 0 and not args.no_adaptive:
+        adaptive = adaptive_leg(pb, w, args, dev, stream)
+
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_leg(args.serving_requests, 5000, args.serving_rates, args.serving_budget_gb * 2**30,
@@ -473,11 +479,46 @@ def run_ours(args, rank, world, local_rank):
                    "fused_update": st.get("fused_update", 0),
                    "fft_unrolled": args.fft_unrolled},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "parity_full_size": parity, "fp64_plain": fp64,
-        "serving": serving,
+        "adaptive": adaptive, "serving": serving,
         "gpu_launches": st["kernel_launches"], "clocks": clk.summary(), "source_hash": shash,
     }
     print(json.dumps(line))
     return 0
+
+
+def adaptive_leg(pb, w, args, dev, stream):
+    """Adaptive time step size (Section 2.2) through rd_pdhg_solve_adaptive on the workload's grid:
+    from u0 over the span of the timed steps (steps x dt), starting at h_t^0 = factor x dt,
+    N^* = 30, N_* = 12, eta = 1/2.  Reports attempts, rejected steps, wall time, PDHG
+    point-iterations per second over all attempts, and the cost of one rd_pdhg_set_dt."""
+    import dataclasses
+    import torch
+    from paper_2305_03945_gb300 import rd
+    q = dataclasses.replace(pb, dt=pb.dt * args.adaptive_dt_factor)
+    t_end = pb.dt * args.steps
+    sv = rd.Solver(q, precision=args.precision, autotune=args.autotune, fused_update=args.fused_update)
+    # cost of a step-size change: descriptor update + re-capture of the step graphs
+    t0 = time.perf_counter()
+    for k in range(10):
+        sv.set_dt(q.dt * (0.5 if k % 2 == 0 else 1.0))
+    set_dt_ms = (time.perf_counter() - t0) * 1e3 / 10
+    u = torch.from_numpy(w.u0.copy()).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    log, t_reached, status = sv.solve_adaptive(u, t_end, 30, 12, 0.5, max_attempts=4 * args.steps + 64,
+                                               allow=(rd.RD_OK, rd.RD_ERR_NOT_CONVERGED))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    sv.close()
+    its = sum(e["iterations"] for e in log)
+    acc = [e for e in log if e["accepted"]]
+    dts = [e["dt"] for e in acc]
+    return {"h_t0": q.dt, "t_end": t_end, "n_hi": 30, "n_lo": 12, "eta": 0.5, "status": int(status),
+            "t_reached": t_reached, "attempts": len(log), "accepted": len(acc), "rejected": len(log) - len(acc),
+            "dt_min": min(dts) if dts else None, "dt_max": max(dts) if dts else None,
+            "step_size_changes": sum(1 for a, b in zip(log, log[1:]) if a["dt"] != b["dt"]),
+            "wall_s": wall, "value": pb.ncomp * pb.nx * pb.ny * its / wall / 1e9, "unit": "Gpoint-iter/s",
+            "set_dt_ms": set_dt_ms}
 
 
 def main():
@@ -514,6 +555,9 @@ def main():
     ap.add_argument("--fft-buffers", type=int, default=0, choices=(0, 1, 2),
                     help="shared-memory transforms: 0 chosen per kernel, 1 in place, 2 two buffers")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true")
+    ap.add_argument("--adaptive-dt-factor", type=float, default=16.0,
+                    help="adaptive leg: h_t^0 as a multiple of the workload's dt")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-rates", type=float, nargs="*", default=[0.5, 1.0])
     ap.add_argument("--serving-budget-gb", type=float, default=8.0)

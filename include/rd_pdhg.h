@@ -225,6 +225,47 @@ RD_API rd_status rd_pdhg_solve(rd_pdhg *h, double *u, int nsteps, rd_step_info *
 /* As rd_pdhg_solve, for a HOST array u: copies it to the device, solves, copies it back. */
 RD_API rd_status rd_pdhg_solve_host(rd_pdhg *h, double *u_host, int nsteps, rd_step_info *per_step);
 
+/* Change the physical time step h_t of a live handle (dt finite, > 0).  Every quantity that
+ * depends on h_t (the residual and adjoint coefficients, the preconditioner symbol
+ * (1 + c1 mu + c2 mu^2)^2) is re-derived and the step graphs are captured again, so a change
+ * costs about one graph capture; the tile plan and the workspaces are kept.  Synchronises the
+ * handle's stream.  RD_ERR_INVALID_ARG leaves the handle unchanged. */
+RD_API rd_status rd_pdhg_set_dt(rd_pdhg *h, double dt);
+
+/* Adaptive time step size (Section 2.2, "Adaptive time stepsize").  After each accepted step
+ * that took M PDHG iterations (DC: summed over inner solves) the next h_t is
+ *     eta h_t  if M > n_hi;   h_t / eta  if M < n_lo and h_t / eta <= h_t^0;   else h_t,
+ * with h_t^0 the handle's dt on entry (the upper bound).  A step whose solve fails
+ * (RD_ERR_NOT_CONVERGED or RD_ERR_DIVERGED) is not accepted: it is taken again from the same
+ * state with eta h_t.  The last step is shortened to end at t_end (the rule keeps acting on the
+ * nominal h_t). */
+typedef struct {
+    double t_end;       /* integrate from t = 0 to t_end (finite, > 0)                          */
+    int n_hi;           /* N^*: more iterations than this shrink h_t                             */
+    int n_lo;           /* N_*: fewer iterations than this enlarge h_t; 0 <= n_lo <= n_hi         */
+    double eta;         /* rescaling coefficient, 0 < eta < 1                                     */
+    int max_attempts;   /* bound on accepted + rejected steps (> 0)                               */
+} rd_adapt;
+
+typedef struct {
+    double t;           /* time at the start of the attempt                                       */
+    double dt;          /* step size used                                                         */
+    int iterations;     /* PDHG iterations of the attempt (DC: summed over inner solves)          */
+    int outer_rounds;   /* DC outer rounds; 0 for plain FP64                                      */
+    int status;         /* rd_status of the attempt's step                                        */
+    int accepted;       /* 1 when the step converged and the state advanced                       */
+} rd_adapt_step;
+
+/* Run the adaptive loop in place on u (device, ncomp*ny*nx doubles: U at t = 0 in, U at the
+ * reached time out).  log (host, may be NULL when log_cap = 0) receives the first log_cap
+ * attempts in order; *n_attempts (may be NULL) the number of attempts and *t_reached (may be
+ * NULL) the time reached.  Returns RD_OK when t_end - t <= 1e-12 t_end, RD_ERR_NOT_CONVERGED
+ * when max_attempts ran out first (u holds the last accepted state), or the first error that is
+ * not a failed solve (RD_ERR_CUDA, RD_ERR_TIMEOUT, ...).  The handle's dt is h_t^0 again on
+ * return. */
+RD_API rd_status rd_pdhg_solve_adaptive(rd_pdhg *h, double *u, const rd_adapt *a, rd_adapt_step *log,
+                                        int log_cap, int *n_attempts, double *t_reached);
+
 /* W <- F(U) for U^k = u_k (all device, FP64): the residual map of the handle's equation
  * (eq. F(U) rd equation / F(U) CH / Section 3.4.1). */
 RD_API rd_status rd_pdhg_residual(rd_pdhg *h, const double *u, const double *u_k, double *w);

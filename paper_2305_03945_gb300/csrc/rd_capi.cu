@@ -439,7 +439,8 @@ rd_status capture_graphs(rd_pdhg* h) {
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
   h->kernels_per_iter = h->dc && h->h_desc[1].fused ? 2 : (lc.transform ? 3 : 2);
   if (h->opts.profile)
-    for (int i = 0; i < 4; ++i) RD_CUDA(cudaEventCreate(&h->ev[i]));
+    for (int i = 0; i < 4; ++i)
+      if (!h->ev[i]) RD_CUDA(cudaEventCreate(&h->ev[i]));
   if (h->opts.solve_loop == RD_LOOP_HOST) {
     RD_TRY(capture_iter_graph(h, false, &h->hgraph, &h->hexec));
     if (h->dc && h->h_desc[1].fused) RD_TRY(capture_iter_graph(h, true, &h->hgraph1, &h->hexec1));
@@ -448,6 +449,38 @@ rd_status capture_graphs(rd_pdhg* h) {
   RD_TRY(capture_step_graph(h, true, &h->graph[0], &h->gexec[0]));
   if (h->dc) RD_TRY(capture_step_graph(h, false, &h->graph[1], &h->gexec[1]));
   return RD_OK;
+}
+
+void destroy_graphs(rd_pdhg* h) {
+  for (int k = 0; k < 2; ++k) {
+    if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+    if (h->graph[k]) cudaGraphDestroy(h->graph[k]);
+    h->gexec[k] = nullptr;
+    h->graph[k] = nullptr;
+  }
+  if (h->hexec) cudaGraphExecDestroy(h->hexec);
+  if (h->hgraph) cudaGraphDestroy(h->hgraph);
+  if (h->hexec1) cudaGraphExecDestroy(h->hexec1);
+  if (h->hgraph1) cudaGraphDestroy(h->hgraph1);
+  h->hexec = h->hexec1 = nullptr;
+  h->hgraph = h->hgraph1 = nullptr;
+}
+
+// A new time step h_t: the descriptors' dt and preconditioner symbol coefficients (everything
+// else that depends on h_t is formed from them in the kernels), then the graphs, which hold the
+// descriptors by value, are captured again.
+rd_status set_dt_impl(rd_pdhg* h, double dt) {
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(RD_ERR_INVALID_ARG, "dt must be finite and > 0");
+  if (dt == h->dt) return RD_OK;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  h->dt = dt;
+  for (int i = 0; i < 3; ++i) {
+    h->h_desc[i].dt = dt;
+    symbol_coefficients(h, h->h_desc[i]);
+  }
+  RD_CUDA(cudaMemcpy(h->d_desc, h->h_desc, 3 * sizeof(Desc), cudaMemcpyHostToDevice));
+  destroy_graphs(h);
+  return capture_graphs(h);
 }
 
 rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* rx, double dt, double tau,
@@ -1165,6 +1198,79 @@ rd_status rd_pdhg_solve_host(rd_pdhg* h, double* u_host, int nsteps, rd_step_inf
   return s;
 }
 
+rd_status rd_pdhg_set_dt(rd_pdhg* h, double dt) {
+  if (!h) return fail(RD_ERR_INVALID_ARG, "NULL handle");
+  return set_dt_impl(h, dt);
+}
+
+namespace {
+// The step-size rule of Section 2.2 after an accepted step of m PDHG iterations.
+double next_dt(double dt, int m, double dt0, const rd_adapt* a) {
+  if (m > a->n_hi) return a->eta * dt;
+  if (m < a->n_lo) {
+    const double up = dt / a->eta;
+    return up <= dt0 ? up : dt;
+  }
+  return dt;
+}
+}  // namespace
+
+rd_status rd_pdhg_solve_adaptive(rd_pdhg* h, double* u, const rd_adapt* a, rd_adapt_step* log, int log_cap,
+                                 int* n_attempts, double* t_reached) {
+  if (n_attempts) *n_attempts = 0;
+  if (t_reached) *t_reached = 0.0;
+  if (!h || !u || !a) return fail(RD_ERR_INVALID_ARG, "NULL handle, buffer or parameters");
+  if (!(a->t_end > 0.0) || !std::isfinite(a->t_end) || !(a->eta > 0.0 && a->eta < 1.0) || a->n_lo < 0 ||
+      a->n_lo > a->n_hi || a->max_attempts <= 0 || log_cap < 0 || (log_cap > 0 && !log))
+    return fail(RD_ERR_INVALID_ARG, "bad adaptive step parameters");
+  const size_t bytes = h->npts * sizeof(double);
+  const double dt0 = h->dt;
+  double dt = dt0, t = 0.0;
+  int n = 0;
+  rd_status result = RD_OK;
+  while (a->t_end - t > 1e-12 * a->t_end) {
+    if (n == a->max_attempts) {
+      result = fail(RD_ERR_NOT_CONVERGED, "adaptive time stepping ran out of attempts");
+      break;
+    }
+    const double rem = a->t_end - t;
+    const double step = dt < rem ? dt : rem;
+    rd_status s = set_dt_impl(h, step);
+    if (s == RD_OK) {
+      const cudaError_t e = cudaMemcpyAsync(h->U64, u, bytes, cudaMemcpyDeviceToDevice, h->stream);
+      if (e != cudaSuccess) s = fail(RD_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    }
+    rd_step_info inf{};
+    if (s == RD_OK) s = step_impl(h, &inf);
+    if (s != RD_OK && s != RD_ERR_NOT_CONVERGED && s != RD_ERR_DIVERGED) {
+      result = s;
+      break;
+    }
+    const bool ok = s == RD_OK;
+    if (n < log_cap) log[n] = rd_adapt_step{t, step, inf.iterations, inf.outer_rounds, (int)s, ok ? 1 : 0};
+    ++n;
+    if (ok) {
+      const cudaError_t e = cudaMemcpyAsync(u, h->U64, bytes, cudaMemcpyDeviceToDevice, h->stream);
+      if (e != cudaSuccess) {
+        result = fail(RD_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+        break;
+      }
+      t = t + step;
+      dt = next_dt(dt, inf.iterations, dt0, a);
+    } else {
+      dt = a->eta * dt;
+    }
+  }
+  if (n_attempts) *n_attempts = n;
+  if (t_reached) *t_reached = t;
+  const std::string keep = g_last_error;
+  const rd_status r = set_dt_impl(h, dt0);
+  if (result == RD_OK && r != RD_OK) return r;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  g_last_error = keep;
+  return result;
+}
+
 rd_status rd_pdhg_residual(rd_pdhg* h, const double* u, const double* u_k, double* w) {
   if (!h || !u || !u_k || !w) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
   const int nb = point_blocks(h->nx, h->ny);
@@ -1209,14 +1315,7 @@ void rd_pdhg_destroy(rd_pdhg* h) {
   for (int i = 0; i < 4; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (int k = 0; k < 2; ++k) {
-    if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
-    if (h->graph[k]) cudaGraphDestroy(h->graph[k]);
-  }
-  if (h->hexec) cudaGraphExecDestroy(h->hexec);
-  if (h->hgraph) cudaGraphDestroy(h->hgraph);
-  if (h->hexec1) cudaGraphExecDestroy(h->hexec1);
-  if (h->hgraph1) cudaGraphDestroy(h->hgraph1);
+  destroy_graphs(h);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

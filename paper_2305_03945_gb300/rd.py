@@ -26,6 +26,7 @@ PREC = {"fp64": 0, "fp32_dc": 1}
 EXPORTS = ("rd_opts_default", "rd_pdhg_create", "rd_pdhg_step", "rd_pdhg_solve", "rd_pdhg_solve_host",
            "rd_pdhg_residual", "rd_pdhg_apply_precond", "rd_pdhg_get_stats", "rd_pdhg_reset_stats",
            "rd_pdhg_destroy", "rd_status_string", "rd_last_error", "rd_apply_precond_static",
+           "rd_pdhg_set_dt", "rd_pdhg_solve_adaptive",
            "rd_batch_create", "rd_batch_submit", "rd_batch_poll", "rd_batch_get_stats", "rd_batch_destroy")
 
 
@@ -71,6 +72,19 @@ class rd_stats(ctypes.Structure):
 class rd_step_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_rounds", ctypes.c_int), ("converged", ctypes.c_int),
                 ("status", ctypes.c_int), ("residual", ctypes.c_double), ("mass", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rd_adapt(ctypes.Structure):
+    _fields_ = [("t_end", ctypes.c_double), ("n_hi", ctypes.c_int), ("n_lo", ctypes.c_int),
+                ("eta", ctypes.c_double), ("max_attempts", ctypes.c_int)]
+
+
+class rd_adapt_step(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("iterations", ctypes.c_int),
+                ("outer_rounds", ctypes.c_int), ("status", ctypes.c_int), ("accepted", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -131,6 +145,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rd_pdhg_get_stats.restype = ctypes.c_int
     lib.rd_pdhg_reset_stats.argtypes = [vp]
     lib.rd_pdhg_reset_stats.restype = ctypes.c_int
+    lib.rd_pdhg_set_dt.argtypes = [vp, ctypes.c_double]
+    lib.rd_pdhg_set_dt.restype = ctypes.c_int
+    lib.rd_pdhg_solve_adaptive.argtypes = [vp, vp, P(rd_adapt), P(rd_adapt_step), ctypes.c_int,
+                                           P(ctypes.c_int), P(ctypes.c_double)]
+    lib.rd_pdhg_solve_adaptive.restype = ctypes.c_int
     lib.rd_pdhg_destroy.argtypes = [vp]
     lib.rd_pdhg_destroy.restype = None
     lib.rd_apply_precond_static.argtypes = [P(rd_grid), ctypes.c_int, ctypes.c_int, P(rd_reaction),
@@ -266,6 +285,21 @@ class Solver:
         s = load().rd_pdhg_solve_host(self.h, ctypes.c_void_p(u_np.ctypes.data), nsteps, infos)
         _check(s, allow)
         return [infos[k].as_dict() for k in range(nsteps)], s
+
+    def set_dt(self, dt):
+        _check(load().rd_pdhg_set_dt(self.h, dt))
+
+    def solve_adaptive(self, u, t_end, n_hi, n_lo, eta, max_attempts=1000, allow=(RD_OK,)):
+        """Adaptive time step size (Section 2.2) in place on u from t = 0 to t_end, with
+        h_t^0 = the solver's dt.  Returns (log, t_reached, status)."""
+        a = rd_adapt(t_end, n_hi, n_lo, eta, max_attempts)
+        log = (rd_adapt_step * max_attempts)()
+        n = ctypes.c_int()
+        t = ctypes.c_double()
+        s = load().rd_pdhg_solve_adaptive(self.h, self._ptr(u), ctypes.byref(a), log, max_attempts,
+                                          ctypes.byref(n), ctypes.byref(t))
+        _check(s, allow)
+        return [log[k].as_dict() for k in range(min(n.value, max_attempts))], t.value, s
 
     def residual(self, u, uk, w):
         _check(load().rd_pdhg_residual(self.h, self._ptr(u), self._ptr(uk), self._ptr(w)))
