@@ -71,6 +71,8 @@ def linear_part(pb, L=None):
         return [I - pb.p[0] * pb.dt * L, I - pb.p[1] * pb.dt * L]
     if pb.op == "laplacian":
         return [I - pb.a * pb.dt * L]
+    if pb.op == "functionalized":   # I - dt Lap (a Lap - (2b - a) I) a Lap (Section 3.3's G root)
+        return [I - pb.dt * L @ (pb.a * L - (2 * pb.b - pb.a) * I) @ (pb.a * L)]
     return [I + pb.a * pb.dt * (L @ L)]
 
 
@@ -89,6 +91,11 @@ def residual(pb, U, Uk, L=None):
             return A @ U - Uk - dt * b * (L @ (U ** 3 - U))
         if pb.kind == "ch_split":
             return A @ U - Uk - dt * b * (L @ U ** 3) + dt * b * (L @ Uk)
+        if pb.kind == "fch":        # U - U^k - dt Lap (a Lap - b W'' + a)(a Lap U - b W')
+            I = np.eye(N2)
+            mu = a * (L @ U) - b * (U ** 3 - U)
+            Am = (a * L - b * np.diag(3 * U ** 2 - 1) + a * I) @ mu
+            return U - Uk - dt * (L @ Am)
     u, v = U[:N2], U[N2:]
     uk, vk = Uk[:N2], Uk[N2:]
     Au, Av = linear_part(pb, L)
@@ -120,6 +127,13 @@ def jacobian(pb, U, L=None):
             return A - dt * b * L @ np.diag(3 * U ** 2 - 1)
         if pb.kind == "ch_split":
             return A - dt * b * L @ np.diag(3 * U ** 2)
+        if pb.kind == "fch":        # product rule on Lap A(U) mu(U)
+            a = pb.a
+            I = np.eye(N2)
+            mu = a * (L @ U) - b * (U ** 3 - U)
+            Amat = a * L - b * np.diag(3 * U ** 2 - 1) + a * I
+            Bmat = a * L - b * np.diag(3 * U ** 2 - 1)
+            return I - dt * L @ (Amat @ Bmat - b * np.diag(6 * U * mu))
     u, v = U[:N2], U[N2:]
     Au, Av = linear_part(pb, L)
     if pb.kind == "gray_scott":

@@ -90,6 +90,23 @@ def check_problem(pb):
         raise ValueError("%s needs op='laplacian'" % pb.kind)
     if pb.kind in ("ch_implicit", "ch_split") and pb.op != "neg_biharmonic":
         raise ValueError("%s needs op='neg_biharmonic'" % pb.kind)
+    if (pb.kind == "fch") != (pb.op == "functionalized"):
+        raise ValueError("kind 'fch' goes with op='functionalized' and only with it")
+
+
+# Sixth-order functionalized Cahn-Hilliard (Section 3.3, eq. 6thorder) with a = eps^2 and b
+# scaling the double well W(u) = (u^2 - 1)^2 / 4:
+#   mu(U) = a Lap U - b W'(U)                  (W' = u^3 - u)
+#   A(U)  = a Lap - b diag(W''(U)) + a I       (W'' = 3u^2 - 1: the paper prints 3u^2, but its
+#                                               own remark that W'' is about 2 at u = +-1 fixes
+#                                               the minus one; W^(3) = 6u)
+#   F(U)  = U - U^k - dt Lap A(U) mu(U)
+def _fch_mu(pb, U):
+    return pb.a * lap(U, pb) - pb.b * (U ** 3 - U)
+
+
+def _fch_A(pb, U, x):
+    return pb.a * lap(x, pb) - pb.b * (3 * U ** 2 - 1) * x + pb.a * x
 
 
 def residual(pb, U, Uk):
@@ -113,6 +130,8 @@ def residual(pb, U, Uk):
         Fu = u - Uk[0] - dt * (Du * L(u) - u * v * v + Ff * (1 - u))
         Fv = v - Uk[1] - dt * (Dv * L(v) + u * v * v - (Ff + k) * v)
         return np.stack([Fu, Fv])
+    if pb.kind == "fch":                              # Section 3.3, F(U) of the 6th-order flow
+        return U - Uk - dt * L(_fch_A(pb, U, _fch_mu(pb, U)))
     if pb.kind == "schnakenberg":                     # Section 3.4.1, F_u and F_v
         D1, D2, kap, a_s, b_s = pb.p
         u, v = U[0], U[1]
@@ -144,6 +163,14 @@ def grad_F_T(pb, U, Pt):
         gu = P - dt * Du * L(P) + dt * (v * v + Ff) * P - dt * v * v * Q
         gv = Q - dt * Dv * L(Q) + 2 * dt * u * v * P - dt * (2 * u * v - (Ff + k)) * Q
         return np.stack([gu, gv])
+    if pb.kind == "fch":
+        # dF = I - dt Lap (A(U) B(U) - b diag(W^(3)(U) mu)) with B = a Lap - b diag(W''(U)), so
+        # dF^T P = P - dt B A Lap P + dt b mu W^(3) Lap P (Lap, A and B are symmetric): the
+        # U-update of Section 3.3
+        q = L(Pt)
+        r = _fch_A(pb, U, q)
+        s = a * L(r) - b * (3 * U ** 2 - 1) * r
+        return Pt - dt * s + dt * b * _fch_mu(pb, U) * (6 * U) * q
     if pb.kind == "schnakenberg":                     # Section 3.4.1 U_{n+1}, V_{n+1} updates
         D1, D2, kap, a_s, b_s = pb.p
         u, v = U[0], U[1]
@@ -160,6 +187,8 @@ def ghat(pb):
     G = A_lin^2 with A_lin the linear, constant-coefficient part of F:
       laplacian op      A_lin = I - D dt Lap    ->  g = (1 + D dt mu)^2   (D = a, or per species)
       neg_biharmonic    A_lin = I + a dt Lap^2  ->  g = (1 + a dt mu^2)^2
+      functionalized    A_lin = I - dt Lap (a Lap - (2b - a) I) a Lap, W'' replaced by its value
+                        2b at u = +-1 (Section 3.3)  ->  g = (1 + dt a mu^2 (a mu + 2b - a))^2
     precond 'none' gives G = I (plain linearised PDHG, eqs. illustrate pdhg dynamic 1-3).
     """
     if pb.precond == "none":
@@ -171,6 +200,8 @@ def ghat(pb):
         return np.stack([(1 + d1 * dt * mu) ** 2, (1 + d2 * dt * mu) ** 2])
     if pb.op == "laplacian":
         return ((1 + pb.a * dt * mu) ** 2)[None]
+    if pb.op == "functionalized":
+        return ((1 + dt * pb.a * mu ** 2 * (pb.a * mu + 2 * pb.b - pb.a)) ** 2)[None]
     return ((1 + pb.a * dt * mu ** 2) ** 2)[None]
 
 

@@ -26,10 +26,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # reaction kinds, boundary conditions, operators, preconditioners and stopping rules.
-KINDS = ("none", "allen_cahn", "ch_implicit", "ch_split", "gray_scott", "schnakenberg")
+KINDS = ("none", "allen_cahn", "ch_implicit", "ch_split", "gray_scott", "schnakenberg", "fch")
 TWO_SPECIES = ("gray_scott", "schnakenberg")
 BCS = ("periodic", "neumann")
-OPS = ("laplacian", "neg_biharmonic")
+OPS = ("laplacian", "neg_biharmonic", "functionalized")
 PRECONDS = ("none", "linear")
 TOL_KINDS = ("res_abs", "f_rel")
 
@@ -263,6 +263,23 @@ def config_seven_circles(n: int = 128) -> Workload:
                  kind="ch_implicit", a=0.01, b=1.0, dt=1 / 200, tau_u=0.5, tau_p=0.5,
                  tol=1e-7, tol_kind="res_abs")
     return Workload("seven_circles_%d" % n, pb, seven_circles(n), 6000)
+
+
+def fch_initial(n: int) -> np.ndarray:
+    """Initial data of the sixth-order example of Section 3.3 (eq. 6th order initial) on [0,2pi)^2:
+    u0 = 2 exp(sin x + sin y - 2) + 2.2 exp(-sin x - sin y - 2) - 1."""
+    x = cell_centres(n, 2 * np.pi, "periodic")
+    X, Y = np.meshgrid(x, x)
+    s = np.sin(X) + np.sin(Y)
+    return (2 * np.exp(s - 2) + 2.2 * np.exp(-s - 2) - 1)[None]
+
+
+def config_fch(n: int = 128) -> Workload:
+    """Functionalized (sixth-order) Cahn-Hilliard of Section 3.3: [0,2pi)^2 periodic, eps = 0.18
+    (a = eps^2, b = 1), dt = 1/1000, tau_u = tau_p = 0.58, delta = 0.5e-5, 20000 steps."""
+    pb = Problem(nx=n, ny=n, lx=2 * np.pi, ly=2 * np.pi, bc="periodic", op="functionalized", kind="fch",
+                 a=0.18 ** 2, b=1.0, dt=1e-3, tau_u=0.58, tau_p=0.58, tol=0.5e-5, tol_kind="res_abs")
+    return Workload("fch_%d" % n, pb, fch_initial(n), 20000)
 
 
 def scaled(w: Workload, n: int, nsteps: int | None = None) -> Workload:

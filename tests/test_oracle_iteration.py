@@ -157,10 +157,16 @@ NEWTON_CASES = [
     ("ch_split", "neg_biharmonic", (), "neumann"),
     ("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06), "periodic"),
     ("schnakenberg", "laplacian", (0.05, 1.0, 100.0, 0.1305, 0.7695), "neumann"),
+    ("fch", "functionalized", (), "periodic"),
+    ("fch", "functionalized", (), "neumann"),
 ]
 
 
 def _newton_problem(kind, op, p, bc):
+    if kind == "fch":   # Section 3.3's parameters on a 16^2 grid of [0,2pi]^2: eps = 0.18, h_t = 1e-3
+        return WL.Problem(nx=16, ny=16, lx=2 * np.pi, ly=2 * np.pi, bc=bc, op=op, kind=kind, dt=1e-3,
+                          a=0.18 ** 2, b=1.0, tau_u=0.58, tau_p=0.58, tol=1e-14, tol_kind="f_rel",
+                          max_iter=20000)
     ch = op == "neg_biharmonic"
     return WL.Problem(nx=16, ny=16, lx=1.0, ly=1.0, bc=bc, op=op, kind=kind, p=p,
                       dt=1e-5 if ch else 2e-3, a=4e-4 if ch else 0.02, b=1.0 if ch else 30.0,
@@ -281,3 +287,21 @@ def test_stopping_rule_checked_with_dense_residual(tol_kind, tol):
         return f / pb.dt if tol_kind == "res_abs" else f / np.linalg.norm(uk)
 
     assert meas(U) <= tol < meas(Uprev)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+def test_functionalized_ch_conserves_mass_and_symbol_is_positive(bc):
+    """Sixth-order functionalized CH (Section 3.3): F = U - U^k - dt Lap(...), and the sum of
+    Lap(.) vanishes on both grids, so converged steps keep h^2 sum U to 1e-12; the preconditioner
+    symbol (1 + dt a mu^2 (a mu + 2b - a))^2 is >= 1 with 1 exactly at the constant mode."""
+    w = WL.config_fch(16)
+    pb = w.problem.replace(bc=bc, tol=1e-13, tol_kind="f_rel", max_iter=20000)
+    g = O.ghat(pb)
+    assert g.min() == 1.0 and g[0, 0, 0] == 1.0
+    U = w.u0
+    m0 = O.mass(pb, U)
+    for _ in range(3):
+        Un, info = O.pdhg_step(pb, U)
+        assert info["status"] == O.OK
+        assert abs(O.mass(pb, Un) - m0) <= 1e-12 * max(1.0, abs(m0))
+        U = Un

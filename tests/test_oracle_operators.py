@@ -96,12 +96,14 @@ def test_oracle_neumann_basis_is_dct2():
     ("ch_implicit", "neg_biharmonic", ()),
     ("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06)),
     ("schnakenberg", "laplacian", (0.05, 1.0, 100.0, 0.1305, 0.7695)),
+    ("fch", "functionalized", ()),
 ])
 def test_ginv_matches_dense_solve(bc, kind, op, p):
     """G^{-1} W through the spectral symbol equals a dense Cholesky solve with
     G = A_lin^2 assembled from the paper's dense Laplacian."""
     import scipy.linalg as sla
-    pb = _pb(16, bc, op=op, kind=kind, p=p, dt=2e-3 if op == "laplacian" else 1e-5, a=0.2)
+    dt = {"laplacian": 2e-3, "neg_biharmonic": 1e-5, "functionalized": 1e-8}[op]
+    pb = _pb(16, bc, op=op, kind=kind, p=p, dt=dt, a=0.2)
     W = WL.rng(11).standard_normal(pb.shape)
     got = O.apply_ginv(pb, W).ravel()
     G = dense.preconditioner(pb)
@@ -118,6 +120,7 @@ def test_ginv_matches_dense_solve(bc, kind, op, p):
     ("ch_split", "neg_biharmonic", ()),
     ("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06)),
     ("schnakenberg", "laplacian", (0.05, 1.0, 100.0, 0.1305, 0.7695)),
+    ("fch", "functionalized", ()),
 ])
 def test_residual_matches_dense_form(bc, kind, op, p):
     """The stencil-based F(U) equals F written with the paper's dense matrices."""
@@ -139,6 +142,7 @@ def test_residual_matches_dense_form(bc, kind, op, p):
     ("ch_split", "neg_biharmonic", ()),
     ("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06)),
     ("schnakenberg", "laplacian", (0.05, 1.0, 100.0, 0.1305, 0.7695)),
+    ("fch", "functionalized", ()),
 ])
 def test_adjoint_jacobian_by_complex_step(bc, kind, op, p):
     """<grad_F_T(U) P, V> = <P, J V> with J V from the complex-step derivative of F
