@@ -59,7 +59,8 @@ typedef enum { RD_BC_PERIODIC = 0, RD_BC_NEUMANN = 1 } rd_bc;
 /* Linear diffusion operator L of the equation u_t = L u + R(u) (Section 1, eq. rd equ). */
 typedef enum {
     RD_OP_LAPLACIAN = 0,       /* L = a Lap            (Allen-Cahn, Gray-Scott, Schnakenberg)   */
-    RD_OP_NEG_BIHARMONIC = 1   /* L = -a Lap^2         (Cahn-Hilliard, Section 3.2)             */
+    RD_OP_NEG_BIHARMONIC = 1,  /* L = -a Lap^2         (Cahn-Hilliard, Section 3.2)             */
+    RD_OP_FUNCTIONALIZED = 2   /* sixth order, with RD_RX_FCH only (Section 3.3)               */
 } rd_operator;
 
 /* Reaction term R and the residual map F it defines (dt = h_t):
@@ -74,15 +75,21 @@ typedef enum {
  *   RD_RX_SCHNAKENBERG  ncomp = 2, p = {D1, D2, kappa, a_s, b_s}       (Section 3.4.1)
  *                       F_u = U - U^k - dt (D1 Lap U + kappa (a_s - U + U^2 V))
  *                       F_v = V - V^k - dt (D2 Lap V + kappa (b_s - U^2 V))
- * The allowed operator is RD_OP_LAPLACIAN for AC / Gray-Scott / Schnakenberg and
- * RD_OP_NEG_BIHARMONIC for both Cahn-Hilliard kinds; RD_RX_NONE takes either. */
+ *   RD_RX_FCH           sixth-order functionalized Cahn-Hilliard (Section 3.3), a = eps^2:
+ *                       F = U - U^k - dt Lap (a Lap - b W''(U) + a)(a Lap U - b W'(U)),
+ *                       W' = U^3 - U, W'' = 3U^2 - 1; G = (I - dt Lap (a Lap - (2b - a)) a Lap)^2.
+ *                       RD_PREC_FP64 only (RD_ERR_UNSUPPORTED otherwise), not batched.
+ * The allowed operator is RD_OP_LAPLACIAN for AC / Gray-Scott / Schnakenberg,
+ * RD_OP_NEG_BIHARMONIC for both Cahn-Hilliard kinds, RD_OP_FUNCTIONALIZED for RD_RX_FCH (and
+ * only for it); RD_RX_NONE takes the first two. */
 typedef enum {
     RD_RX_NONE = 0,
     RD_RX_ALLEN_CAHN = 1,
     RD_RX_CH_IMPLICIT = 2,
     RD_RX_CH_SPLIT = 3,
     RD_RX_GRAY_SCOTT = 4,
-    RD_RX_SCHNAKENBERG = 5
+    RD_RX_SCHNAKENBERG = 5,
+    RD_RX_FCH = 6
 } rd_reaction_kind;
 
 typedef struct {
@@ -137,7 +144,9 @@ typedef struct {
     int precision;        /* rd_precision, default RD_PREC_FP64                                 */
     double dc_inner_rtol; /* DC inner tolerance factor, default 1e-5: the FP32 solve of a round
                              stops at max(dc_inner_rtol ||r||, half the outer threshold)        */
-    int dc_max_outer;     /* DC outer rounds per step, default 12                                */
+    int dc_max_outer;     /* DC outer rounds per step before RD_ERR_NOT_CONVERGED, default 64
+                             (the paper's seven-circle Cahn-Hilliard example at tau = 0.5 takes
+                             about 16 rounds of a few inner iterations each)                    */
     int graph_k;          /* PDHG iterations per trip of the device-side loop (a WHILE node of the
                              step's CUDA graph), default 2                                      */
     int band_rows;        /* rows per CTA of the stencil sweeps (k_res and k_upd); 0 = chosen at

@@ -807,6 +807,8 @@ rd_status rd_batch_submit(rd_batch* b, const rd_request* req, double* u_out_host
     if (!(r.grid.length[k] > 0)) return bfail(RD_ERR_INVALID_ARG, "lengths must be > 0");
   }
   if (r.bc != RD_BC_PERIODIC && r.bc != RD_BC_NEUMANN) return bfail(RD_ERR_INVALID_ARG, "bad boundary condition");
+  if (r.reaction.kind == RD_RX_FCH || r.op == RD_OP_FUNCTIONALIZED)
+    return bfail(RD_ERR_UNSUPPORTED, "batch: the sixth-order equation is not batched");
   if (r.reaction.ncomp != 1 || group_of(key_of(r)) < 0)
     return bfail(RD_ERR_UNSUPPORTED, "batch: scalar kinds only (none, Allen-Cahn, Cahn-Hilliard)");
   if (r.op != RD_OP_LAPLACIAN && r.op != RD_OP_NEG_BIHARMONIC) return bfail(RD_ERR_INVALID_ARG, "bad operator");

@@ -214,6 +214,9 @@ struct rd_pdhg {
   float* u32 = nullptr;
   cx<float>* tw32[4] = {nullptr, nullptr, nullptr, nullptr};
   double* partials = nullptr;
+  // sixth-order functionalized Cahn-Hilliard (FP64 only): its own stencil passes (rd_fch.cu)
+  int fch = 0;
+  FchBuffers fchb{};
   Desc* d_desc = nullptr;   // [0] FP64 plain / outer, [1] FP32 inner, [2] FP64 precond-only
   State* d_state = nullptr; // [0] plain / outer, [1] inner, [2] misc
   State* h_state = nullptr; // pinned mirror
@@ -292,9 +295,15 @@ void symbol_coefficients(const rd_pdhg* h, Desc& d) {
   for (int c = 0; c < 2; ++c) {
     double D = h->rx.a;
     if (h->kind == RD_RX_GRAY_SCOTT || h->kind == RD_RX_SCHNAKENBERG) D = h->rx.p[c < h->nc ? c : 0];
+    d.gc3[c] = 0.0;
     if (h->op == RD_OP_LAPLACIAN) {
       d.gc1[c] = D * h->dt;
       d.gc2[c] = 0.0;
+    } else if (h->op == RD_OP_FUNCTIONALIZED) {
+      // G = (I - dt Lap (a Lap - (2b - a) I) a Lap)^2: 1 + dt a (2b - a) mu^2 + dt a^2 mu^3
+      d.gc1[c] = 0.0;
+      d.gc2[c] = h->dt * h->rx.a * (2.0 * h->rx.b - h->rx.a);
+      d.gc3[c] = h->dt * h->rx.a * h->rx.a;
     } else {
       d.gc1[c] = 0.0;
       d.gc2[c] = h->rx.a * h->dt;
@@ -310,6 +319,13 @@ rd_status status_of(int st) {
     case ST_DIVERGED: return RD_ERR_DIVERGED;
     default: return RD_ERR_NOT_CONVERGED;
   }
+}
+
+// One PDHG iteration of the sixth-order equation (FP64): its stencil passes around the
+// preconditioner-only transform kernels, which read and write P64[1] (h_desc[2].X).
+cudaError_t fch_iteration(rd_pdhg* h, cudaStream_t s, cudaEvent_t* ev) {
+  const int cap = 2 * std::max(std::max(h->h_desc[0].nbands, h->ny / 2 + 1), point_blocks(h->nx, h->ny));
+  return launch_fch_iteration(h->h_desc[0], h->h_desc[2], h->d_state + 0, h->d_state + 2, h->cfgpc, h->fchb, cap, s, ev);
 }
 
 // Capture one step graph.  Layout (FP64 plain, first = true):
@@ -336,6 +352,7 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
   const Desc dd = h->dc ? h->h_desc[1] : h->h_desc[0];
   auto iteration = [&](cudaStream_t st, cudaEvent_t* ev, bool first_it) {
+    if (h->fch) return fch_iteration(h, st, ev);
     if (h->dc && dd.fused) return launch_fused<float>(dd, sti, h->cfg32, st, ev, first_it);
     return h->dc ? launch_iteration<float>(dd, sti, h->cfg32, st, ev) : launch_iteration<double>(dd, sti, h->cfg64, st, ev);
   };
@@ -420,7 +437,8 @@ rd_status capture_iter_graph(rd_pdhg* h, bool start, cudaGraph_t* graph, cudaGra
   if (fused && start) e = cudaMemsetAsync(h->halo32, 0, h->halo_bytes, cs);
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
     cudaEvent_t* ev = (k == 0 && h->opts.profile && (start || !fused)) ? h->ev : nullptr;
-    if (fused) e = launch_fused<float>(dd, h->d_state + 1, h->cfg32, cs, ev, start && k == 0);
+    if (h->fch) e = fch_iteration(h, cs, ev);
+    else if (fused) e = launch_fused<float>(dd, h->d_state + 1, h->cfg32, cs, ev, start && k == 0);
     else if (h->dc) e = launch_iteration<float>(dd, h->d_state + 1, h->cfg32, cs, ev);
     else e = launch_iteration<double>(dd, h->d_state + 0, h->cfg64, cs, ev);
   }
@@ -437,7 +455,7 @@ rd_status capture_iter_graph(rd_pdhg* h, bool start, cudaGraph_t* graph, cudaGra
 
 rd_status capture_graphs(rd_pdhg* h) {
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
-  h->kernels_per_iter = h->dc && h->h_desc[1].fused ? 2 : (lc.transform ? 3 : 2);
+  h->kernels_per_iter = h->fch ? (lc.transform ? 10 : 7) : (h->dc && h->h_desc[1].fused ? 2 : (lc.transform ? 3 : 2));
   if (h->opts.profile)
     for (int i = 0; i < 4; ++i)
       if (!h->ev[i]) RD_CUDA(cudaEventCreate(&h->ev[i]));
@@ -494,11 +512,16 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
     if (!(grid->length[k] > 0) || !std::isfinite(grid->length[k])) return fail(RD_ERR_INVALID_ARG, "lengths must be > 0");
   }
   if (bc != RD_BC_PERIODIC && bc != RD_BC_NEUMANN) return fail(RD_ERR_INVALID_ARG, "bad boundary condition");
-  if (op != RD_OP_LAPLACIAN && op != RD_OP_NEG_BIHARMONIC) return fail(RD_ERR_INVALID_ARG, "bad operator");
+  if (op != RD_OP_LAPLACIAN && op != RD_OP_NEG_BIHARMONIC && op != RD_OP_FUNCTIONALIZED)
+    return fail(RD_ERR_INVALID_ARG, "bad operator");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(RD_ERR_INVALID_ARG, "dt must be > 0");
   if (!(tau > 0) || !(sigma > 0) || !std::isfinite(tau) || !std::isfinite(sigma))
     return fail(RD_ERR_INVALID_ARG, "tau and sigma must be > 0");
-  if (rx->kind < RD_RX_NONE || rx->kind > RD_RX_SCHNAKENBERG) return fail(RD_ERR_INVALID_ARG, "bad reaction kind");
+  if (rx->kind < RD_RX_NONE || rx->kind > RD_RX_FCH) return fail(RD_ERR_INVALID_ARG, "bad reaction kind");
+  if ((rx->kind == RD_RX_FCH) != (op == RD_OP_FUNCTIONALIZED))
+    return fail(RD_ERR_INVALID_ARG, "RD_RX_FCH goes with RD_OP_FUNCTIONALIZED and only with it");
+  if (rx->kind == RD_RX_FCH && o && o->precision != RD_PREC_FP64)
+    return fail(RD_ERR_UNSUPPORTED, "the sixth-order equation is built for RD_PREC_FP64 only");
   const bool two = rx->kind == RD_RX_GRAY_SCOTT || rx->kind == RD_RX_SCHNAKENBERG;
   if (rx->ncomp != (two ? 2 : 1)) return fail(RD_ERR_INVALID_ARG, "ncomp does not match the reaction kind");
   if (!(rx->a >= 0) || !(rx->b >= 0)) return fail(RD_ERR_INVALID_ARG, "a and b must be >= 0");
@@ -740,7 +763,8 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   RD_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   RD_CUDA(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
 
-  const int H = op == RD_OP_NEG_BIHARMONIC ? 2 : 1;
+  const int H = op == RD_OP_NEG_BIHARMONIC ? 2 : 1;  // the sixth-order kind plans only the preconditioner
+  h->fch = rx->kind == RD_RX_FCH;
   const int transform = h->precond != RD_PC_NONE;
 
   Desc base{};
@@ -790,6 +814,12 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   RD_TRY(dalloc(h, &h->partials, (size_t)2 * std::max(std::max(nb_any, point_blocks(h->nx, h->ny)), 1) * sizeof(double)));
   RD_TRY(dalloc(h, &h->d_desc, 3 * sizeof(Desc)));
   RD_TRY(dalloc(h, &h->d_state, 3 * sizeof(State)));
+  if (h->fch) {
+    RD_TRY(dalloc(h, &h->fchb.Pt, n * sizeof(double)));
+    RD_TRY(dalloc(h, &h->fchb.M, n * sizeof(double)));
+    RD_TRY(dalloc(h, &h->fchb.N, n * sizeof(double)));
+    RD_TRY(dalloc(h, &h->fchb.Q, n * sizeof(double)));
+  }
   RD_CUDA(cudaMallocHost(&h->h_state, 3 * sizeof(State)));
 
   std::vector<double> twx, dcx, twy, dcy, mx, my;
@@ -900,7 +930,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
   if (std::max(lc.smem_res, std::max(lc.smem_col, lc.smem_upd)) > usable)
     return fail(RD_ERR_UNSUPPORTED, "the grid needs more shared memory per block than this device offers");
-  if (h->opts.autotune && h->opts.band_rows == 0 && h->opts.col_width == 0 && h->opts.upd_rows == 0) {
+  if (h->opts.autotune && !h->fch && h->opts.band_rows == 0 && h->opts.col_width == 0 && h->opts.upd_rows == 0) {
     const int stage_base = h->dc && (rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT);
     RD_TRY(h->dc ? autotune_plan<float>(h, H, transform, stage_base, usable)
                  : autotune_plan<double>(h, H, transform, stage_base, usable));
@@ -1110,7 +1140,7 @@ void rd_opts_default(rd_opts* o) {
   o->omega = 1.0;
   o->precision = RD_PREC_FP64;
   o->dc_inner_rtol = 1e-5;
-  o->dc_max_outer = 12;
+  o->dc_max_outer = 64;
   o->graph_k = 2;
   o->band_rows = 0;
   o->col_width = 0;
@@ -1275,6 +1305,11 @@ rd_status rd_pdhg_residual(rd_pdhg* h, const double* u, const double* u_k, doubl
   if (!h || !u || !u_k || !w) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
   const int nb = point_blocks(h->nx, h->ny);
   RD_CUDA(launch_begin(h->d_desc + 0, h->d_state + 2, u_k, h->rhs64, 0.0, 0, nb, h->stream));
+  if (h->fch) {
+    RD_CUDA(launch_fch_residual(h->h_desc[0], nullptr, h->fchb, u, h->rhs64, w, 1, h->stream));
+    RD_CUDA(cudaStreamSynchronize(h->stream));
+    return RD_OK;
+  }
   RD_CUDA(launch_resid64(h->h_desc[0], h->d_desc + 0, h->d_state + 2, h->d_state + 2, u, h->rhs64, w, nullptr,
                          nullptr, nullptr, nullptr, 0, 0.0, 0, nb, h->stream));
   RD_CUDA(cudaStreamSynchronize(h->stream));

@@ -7,8 +7,8 @@
 namespace rd {
 
 enum Bc { BC_PERIODIC = 0, BC_NEUMANN = 1 };
-enum Op { OP_LAP = 0, OP_BIHARM = 1 };
-enum Kind { RX_NONE = 0, RX_AC = 1, RX_CH_IMPL = 2, RX_CH_SPLIT = 3, RX_GS = 4, RX_SCHNAK = 5 };
+enum Op { OP_LAP = 0, OP_BIHARM = 1, OP_FCH = 2 };
+enum Kind { RX_NONE = 0, RX_AC = 1, RX_CH_IMPL = 2, RX_CH_SPLIT = 3, RX_GS = 4, RX_SCHNAK = 5, RX_FCH = 6 };
 enum Mode { MODE_PDHG = 0, MODE_PRECOND_ONLY = 1 };
 
 // per-solve status kept on the device
@@ -55,8 +55,9 @@ struct Desc {
   const void* scale; // unused by the sweeps (kept for layout); see mux / muy
   const void* mux;   // nx entries of T: 4/h_x^2 sin^2(pi kx / (d nx)), d = 1 periodic, 2 Neumann
   const void* muy;   // ny entries of T
-  double gc1[2];     // per component: g_hat = (1 + gc1 mu + gc2 mu^2)^2, mu = mux + muy
+  double gc1[2];     // per component: g_hat = (1 + gc1 mu + gc2 mu^2 + gc3 mu^3)^2, mu = mux + muy
   double gc2[2];
+  double gc3[2];     // + gc3 mu^3 (sixth-order functionalized Cahn-Hilliard; 0 otherwise)
   double inv_nn;     // 1 / (nx ny): normalisation of the unnormalised transform pair
   const void* twx;   // nx complex T: exp(-2 pi i k / nx)
   const void* twy;   // ny complex T

@@ -65,6 +65,24 @@ cudaError_t launch_resid64(const Desc& hd, const Desc* d64, State* outer, State*
                            const double* rhs, double* w64, float* r32, float* u32, float* z0, float* z1, int decide,
                            double rtol, int max_outer, int nblocks, cudaStream_t s);
 
+// Work arrays of the sixth-order functionalized Cahn-Hilliard iteration (rd_fch.cu): P~, mu(U),
+// A(U) mu / A(U) Lap P~, Lap P~; each ny * nx doubles.
+struct FchBuffers {
+  double* Pt;
+  double* M;
+  double* N;
+  double* Q;
+};
+// W = F(U) of that equation (st != NULL: also the stopping decision of the solve st, on at most
+// max_blocks blocks of d.partials).
+cudaError_t launch_fch_residual(const Desc& d, State* st, const FchBuffers& b, const double* U, const double* Uk,
+                                double* W, int max_blocks, cudaStream_t s);
+// One PDHG iteration of that equation on d (X = U, rhs = U^k, P[0] = P); dpc is the
+// preconditioner-only descriptor whose X holds W (and then G^{-1} W), run on st_pc with cpc.
+// Events ev[0..3] (may be NULL) around the residual, the preconditioner solve and the update.
+cudaError_t launch_fch_iteration(const Desc& d, const Desc& dpc, State* st, State* st_pc, const LaunchCfg& cpc,
+                                 const FchBuffers& b, int max_blocks, cudaStream_t s, cudaEvent_t* ev);
+
 // Set the thread-local detail string returned by rd_last_error().
 void set_last_error(const char* msg);
 

@@ -111,6 +111,7 @@ extern "C" RD_API rd_status rd_apply_precond_static(const rd_grid* grid, rd_bc b
   }
   if (bc != RD_BC_PERIODIC && bc != RD_BC_NEUMANN) return nofail(RD_ERR_INVALID_ARG, "bad boundary condition");
   if (op != RD_OP_LAPLACIAN && op != RD_OP_NEG_BIHARMONIC) return nofail(RD_ERR_INVALID_ARG, "bad operator");
+  if (reaction->kind == RD_RX_FCH) return nofail(RD_ERR_UNSUPPORTED, "the sixth-order equation has no static solve");
   if (!(dt > 0)) return nofail(RD_ERR_INVALID_ARG, "dt must be > 0");
   const bool two = reaction->kind == RD_RX_GRAY_SCOTT || reaction->kind == RD_RX_SCHNAKENBERG;
   const int nc = two ? 2 : 1;

@@ -570,12 +570,12 @@ __device__ __forceinline__ void col_body(const Desc& d, State* __restrict__ st, 
   const cx<T>* dcy;
   cx<T>* buf = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, d.twy, d.dcy, ny, true, !per, twy, dcy));
   cx<T>* scr = (d.fft_pp & 2) ? buf + nl * ls : buf;
-  // spectral symbol 1 / (g_hat nx ny), g_hat = (1 + c1 mu + c2 mu^2)^2, mu = mu_x(kx) + mu_y(ky)
+  // spectral symbol 1 / (g_hat nx ny), g_hat = (1 + c1 mu + c2 mu^2 + c3 mu^3)^2, mu = mu_x(kx) + mu_y(ky)
   const T* mux = static_cast<const T*>(d.mux);
   const T* muy = static_cast<const T*>(d.muy);
-  const T c1 = T(d.gc1[c]), c2 = T(d.gc2[c]), inn = T(d.inv_nn);
+  const T c1 = T(d.gc1[c]), c2 = T(d.gc2[c]), c3 = T(d.gc3[c]), inn = T(d.inv_nn);
   auto sym = [&](T mu) -> T {
-    const T g = T(1) + mu * (c1 + c2 * mu);
+    const T g = T(1) + mu * (c1 + mu * (c2 + c3 * mu));
     if constexpr (sizeof(T) == 4) return inn * __frcp_rn(g * g);
     else return inn / (g * g);
   };

@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(HERE, "librd_pdhg.so")
 RD_OK, RD_ERR_INVALID_ARG, RD_ERR_UNSUPPORTED, RD_ERR_OOM, RD_ERR_CUDA = 0, 1, 2, 3, 4
 RD_ERR_NOT_CONVERGED, RD_ERR_DIVERGED, RD_ERR_TIMEOUT, RD_ERR_BUSY = 5, 6, 7, 8
 BC = {"periodic": 0, "neumann": 1}
-OP = {"laplacian": 0, "neg_biharmonic": 1}
-KIND = {"none": 0, "allen_cahn": 1, "ch_implicit": 2, "ch_split": 3, "gray_scott": 4, "schnakenberg": 5}
+OP = {"laplacian": 0, "neg_biharmonic": 1, "functionalized": 2}
+KIND = {"none": 0, "allen_cahn": 1, "ch_implicit": 2, "ch_split": 3, "gray_scott": 4, "schnakenberg": 5,
+        "fch": 6}
 PRECOND = {"none": 0, "linear": 1}
 TOL = {"res_abs": 0, "f_rel": 1}
 PREC = {"fp64": 0, "fp32_dc": 1}
@@ -186,7 +187,7 @@ def _check(status, ok=(RD_OK,)):
 
 
 def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_inner_rtol=None,
-                 dc_max_outer=12, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1, autotune=0, upd_rows=0, dc_stall_window=None, fused_update=1):
+                 dc_max_outer=None, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1, autotune=0, upd_rows=0, dc_stall_window=None, fused_update=1):
     """C structs for a ``workloads.Problem``."""
     g = rd_grid()
     g.ndim = 2
@@ -211,7 +212,8 @@ def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_i
     o.col_width = col_width
     if dc_inner_rtol is not None:
         o.dc_inner_rtol = dc_inner_rtol
-    o.dc_max_outer = dc_max_outer
+    if dc_max_outer is not None:
+        o.dc_max_outer = dc_max_outer
     o.profile = profile
     o.fft_buffers = fft_buffers
     o.solve_loop = {"graph": 0, "host": 1}[solve_loop]
@@ -322,12 +324,14 @@ class Batch:
     come back through ``poll``, final states in the host arrays returned by ``submit``."""
 
     def __init__(self, hbm_budget_bytes, max_slots, graph_k=8, max_iter=10000, dc_inner_rtol=None,
-                 dc_max_outer=12, stream=None):
+                 dc_max_outer=None, stream=None):
         import torch
         lib = load()
         o = rd_opts()
         lib.rd_opts_default(ctypes.byref(o))
-        o.graph_k, o.max_iter, o.dc_max_outer = graph_k, max_iter, dc_max_outer
+        o.graph_k, o.max_iter = graph_k, max_iter
+        if dc_max_outer is not None:
+            o.dc_max_outer = dc_max_outer
         if dc_inner_rtol is not None:
             o.dc_inner_rtol = dc_inner_rtol
         if stream is None:

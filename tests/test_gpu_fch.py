@@ -1,0 +1,139 @@
+"""GPU parity for the sixth-order functionalized Cahn-Hilliard equation (Section 3.3): residual
+map, preconditioner symbol with its mu^3 term, single steps and a short run, against the CPU
+oracle; the FP64-only and not-batched limits."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import rd_oracle as O
+from paper_2305_03945_gb300 import workloads as WL
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_03945_gb300 import build
+    build.build()
+
+
+def _rd():
+    from paper_2305_03945_gb300 import rd
+    return rd
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _pb(n, m=None, bc="periodic", **kw):
+    """The paper's parameters (eps = 0.18, dt = 1e-3, tau = 0.58) on an n x m grid of [0,2pi)^2."""
+    m = n if m is None else m
+    base = dict(nx=m, ny=n, lx=2 * np.pi, ly=2 * np.pi * n / m, bc=bc, op="functionalized", kind="fch",
+                a=0.18 ** 2, b=1.0, dt=1e-3, tau_u=0.58, tau_p=0.58, tol=1e-11, tol_kind="f_rel", max_iter=20000)
+    base.update(kw)
+    return WL.Problem(**base)
+
+
+def _u0(pb, seed):
+    x = WL.fch_initial(pb.nx)[0][:pb.ny, :] if pb.nx == pb.ny else np.zeros((pb.ny, pb.nx))
+    return (x + 0.2 * WL.rng(seed).uniform(-1, 1, (pb.ny, pb.nx)))[None]
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("shape", [(2, 2), (8, 16), (32, 32), (64, 128)])
+def test_residual_matches_oracle(bc, shape):
+    """W = F(U) of the sixth-order equation (three nested Laplacians with the W', W'' factors)."""
+    rd = _rd()
+    pb = _pb(*shape, bc=bc)
+    U, Uk = _u0(pb, 1), _u0(pb, 2)
+    with rd.Solver(pb) as s:
+        w = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        s.residual(dev(U), dev(Uk), w)
+        got = host(w)
+    assert rel_max(got, O.residual(pb, U, Uk)) <= 1e-12
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("shape", [(16, 16), (32, 64), (128, 128)])
+def test_preconditioner_symbol_with_cubic_term(bc, shape):
+    """G^{-1} W with g = (1 + dt a mu^2 (a mu + 2b - a))^2 (the mu^3 term of this equation)."""
+    rd = _rd()
+    pb = _pb(*shape, bc=bc, dt=0.05)
+    W = WL.rng(5).standard_normal(pb.shape)
+    with rd.Solver(pb) as s:
+        y = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        s.apply_precond(dev(W), y)
+        got = host(y)
+    assert rel_max(got, O.apply_ginv(pb, W)) <= 1e-12
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("shape", [(16, 16), (32, 64)])
+@pytest.mark.parametrize("loop", ["graph", "host"])
+def test_step_matches_oracle(bc, shape, loop):
+    """One implicit step in FP64: the oracle's iteration count (ties aside) and <= 1e-10 max
+    relative error; the host-relaunched loop gives the same step bit for bit."""
+    rd = _rd()
+    pb = _pb(*shape, bc=bc)
+    uk = _u0(pb, 3)
+    U_ref, info_ref = O.pdhg_step(pb, uk)
+    with rd.Solver(pb, solve_loop=loop) as s:
+        out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+        info = s.step(dev(uk), out)
+        U = host(out)
+    assert info_ref["status"] == O.OK and info["status"] == 0
+    assert abs(info["iterations"] - info_ref["iterations"]) <= 1
+    assert rel_max(U, U_ref) <= 1e-10
+
+
+def test_paper_example_steps_match_oracle():
+    """The paper's initial data and parameters (Section 3.3) on 64^2, 10 steps through
+    rd_pdhg_solve: per-step iteration counts within one of the oracle's and the state within
+    1e-9; mass conserved."""
+    rd = _rd()
+    w = WL.config_fch(64)
+    pb = dataclasses.replace(w.problem, tol=1e-9, tol_kind="f_rel")
+    U_ref, infos_ref = O.solve(pb, w.u0, 10)
+    u = dev(w.u0)
+    with rd.Solver(pb) as s:
+        infos, st = s.solve(u, 10)
+    U = host(u)
+    assert st == 0 and all(i["status"] == O.OK for i in infos_ref)
+    assert all(abs(a["iterations"] - b["iterations"]) <= 1 for a, b in zip(infos, infos_ref))
+    assert rel_max(U, U_ref) <= 1e-9
+    assert abs(O.mass(pb, U) - O.mass(pb, w.u0)) <= 1e-10
+
+
+def test_set_dt_and_limits():
+    """set_dt re-derives the mu^3 symbol term (equal to a fresh handle); defect correction and
+    batching of this equation are refused with RD_ERR_UNSUPPORTED."""
+    rd = _rd()
+    pb = _pb(32)
+    uk = _u0(pb, 4)
+    outs = []
+    for how in ("set", "fresh"):
+        q = pb if how == "set" else dataclasses.replace(pb, dt=2.5e-4)
+        with rd.Solver(q) as s:
+            if how == "set":
+                s.set_dt(2.5e-4)
+            out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+            info = s.step(dev(uk), out)
+            outs.append((host(out), info["iterations"]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+    with pytest.raises(rd.RDError) as e:
+        rd.Solver(pb, precision="fp32_dc")
+    assert e.value.status == rd.RD_ERR_UNSUPPORTED
