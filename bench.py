@@ -27,7 +27,8 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
-WORKLOADS = ("allen_cahn_neumann_1024", "cahn_hilliard_split_512", "gray_scott_2048", "allen_cahn_periodic_64")
+WORKLOADS = ("allen_cahn_neumann_1024", "cahn_hilliard_split_512", "gray_scott_2048", "allen_cahn_periodic_64",
+             "fch_128")
 
 
 def workload(name):
@@ -40,6 +41,8 @@ def workload(name):
         return WL.config_gray_scott()
     if name == "allen_cahn_periodic_64":
         return WL.config_allen_cahn_periodic()
+    if name == "fch_128":
+        return WL.config_fch(128)
     raise SystemExit("unknown workload " + name)
 
 
@@ -127,6 +130,10 @@ def kernel_bytes(pb, precision):
     unknown and P."""
     es = 4 if precision == "fp32_dc" else 8
     npts = pb.ncomp * pb.nx * pb.ny
+    if pb.kind == "fch":
+        # sixth-order equation (FP64 stencil chains): residual mu, A mu, F = 2 + 3 + 4 touches;
+        # preconditioner-only transforms 2 + 2 + 2; update dual, Lap P~, A Lap P~, U = 4 + 2 + 3 + 6
+        return {"fch_residual": 9 * es * npts, "precond": 6 * es * npts, "fch_update": 15 * es * npts}
     base = 1 if (precision == "fp32_dc" and pb.kind != "none") else 0
     # k_updres (fused update): k_upd's touches plus the right-hand side read and the transformed
     # residual written (the unknown is read and written once for both)
@@ -355,6 +362,8 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = load_peaks()
     kb = kernel_bytes(pb, args.precision)
     names = ("k_res", "k_col", "k_updres" if st.get("fused_update") else "k_upd")
+    if pb.kind == "fch":
+        names = ("fch_residual", "precond", "fch_update")
     per = {}
     for i, nm in enumerate(names):
         n = st["kernel_samples"][i]
@@ -450,7 +459,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- adaptive time step size (Section 2.2) on the same workload ----
     adaptive = None
     if rank == 0 and not args.no_adaptive:
-        adaptive = adaptive_leg(pb, w, args, dev, stream)
+        adaptive = adaptive_leg(pb, w, args, dev, stream, its / args.steps)
 
     serving = None
     if rank == 0 and not args.no_serving:
@@ -486,15 +495,18 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
-def adaptive_leg(pb, w, args, dev, stream):
+def adaptive_leg(pb, w, args, dev, stream, its_per_step):
     """Adaptive time step size (Section 2.2) through rd_pdhg_solve_adaptive on the workload's grid:
     from u0 over the span of the timed steps (steps x dt), starting at h_t^0 = factor x dt,
-    N^* = 30, N_* = 12, eta = 1/2.  Reports attempts, rejected steps, wall time, PDHG
+    N^* = 2 M and N_* = M (M the mean iterations per step of the fixed-step run), eta = 1/2,
+    each attempt capped at 10 M + 200 iterations.  Reports attempts, rejected steps, wall time, PDHG
     point-iterations per second over all attempts, and the cost of one rd_pdhg_set_dt."""
     import dataclasses
     import torch
     from paper_2305_03945_gb300 import rd
-    q = dataclasses.replace(pb, dt=pb.dt * args.adaptive_dt_factor)
+    m = max(1, int(round(its_per_step)))
+    n_hi, n_lo = 2 * m, m
+    q = dataclasses.replace(pb, dt=pb.dt * args.adaptive_dt_factor, max_iter=10 * m + 200)
     t_end = pb.dt * args.steps
     sv = rd.Solver(q, precision=args.precision, autotune=args.autotune, fused_update=args.fused_update)
     # cost of a step-size change: descriptor update + re-capture of the step graphs
@@ -505,7 +517,7 @@ def adaptive_leg(pb, w, args, dev, stream):
     u = torch.from_numpy(w.u0.copy()).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    log, t_reached, status = sv.solve_adaptive(u, t_end, 30, 12, 0.5, max_attempts=4 * args.steps + 64,
+    log, t_reached, status = sv.solve_adaptive(u, t_end, n_hi, n_lo, 0.5, max_attempts=2 * args.steps + 16,
                                                allow=(rd.RD_OK, rd.RD_ERR_NOT_CONVERGED))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -513,7 +525,8 @@ def adaptive_leg(pb, w, args, dev, stream):
     its = sum(e["iterations"] for e in log)
     acc = [e for e in log if e["accepted"]]
     dts = [e["dt"] for e in acc]
-    return {"h_t0": q.dt, "t_end": t_end, "n_hi": 30, "n_lo": 12, "eta": 0.5, "status": int(status),
+    return {"h_t0": q.dt, "t_end": t_end, "n_hi": n_hi, "n_lo": n_lo, "eta": 0.5, "max_iter": q.max_iter,
+            "status": int(status),
             "t_reached": t_reached, "attempts": len(log), "accepted": len(acc), "rejected": len(log) - len(acc),
             "dt_min": min(dts) if dts else None, "dt_max": max(dts) if dts else None,
             "step_size_changes": sum(1 for a, b in zip(log, log[1:]) if a["dt"] != b["dt"]),
@@ -566,6 +579,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.workload == "fch_128" and args.precision == "fp32_dc":
+        args.precision = "fp64"   # the sixth-order equation is built in FP64 only
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
