@@ -95,12 +95,13 @@ __device__ __forceinline__ void dft_reg(cx<T>* v) {
 }
 
 // Values each FFT thread holds per Stockham pass (radix 8), and the block-size cap of the sweep
-// kernels: FP32 blocks of <= 256 threads at <= 85 registers (three blocks per SM, no spills),
+// kernels: FP32 blocks of <= 256 threads at <= 128 registers (two blocks per SM: the sweep
+// grids put at most two blocks on an SM, and at 80 registers the transform passes spilled),
 // FP64 blocks of <= 512 threads at <= 128 registers.  One line of length N needs N/8 threads,
 // so rows and columns are limited to 2048 points in FP32 and 4096 in FP64.
 template <class T> struct FftRadix { static constexpr int value = 8; };
 template <class T> struct MaxThreads { static constexpr int value = sizeof(T) == 4 ? 256 : 512; };
-template <class T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
+template <class T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
 
 // Threads needed to transform ONE line of length N in one go.
 template <class T>
