@@ -137,3 +137,20 @@ def test_set_dt_and_limits():
     with pytest.raises(rd.RDError) as e:
         rd.Solver(pb, precision="fp32_dc")
     assert e.value.status == rd.RD_ERR_UNSUPPORTED
+
+
+def test_paper_example_full_size_step_meets_the_stopping_rule():
+    """The paper's 128^2 example as bench.py runs it (fch_128): two steps from u0, each meeting
+    the stopping rule ||F|| / dt <= 0.5e-5 with F evaluated by the oracle."""
+    rd = _rd()
+    w = WL.config_fch(128)
+    pb = w.problem
+    u = dev(w.u0)
+    with rd.Solver(pb) as s:
+        for _ in range(2):
+            uk = host(u)
+            info = s.step(u, u)
+            U = host(u)
+            assert info["status"] == 0, info
+            r, thr = O.measure(pb, O.residual(pb, U, uk), uk)
+            assert r <= thr * (1 + 1e-6), (r, thr)

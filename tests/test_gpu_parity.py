@@ -463,3 +463,23 @@ def test_fused_update_twenty_steps_match_unfused():
         assert st == 0
         outs.append(host(u))
     assert rel_max(outs[1], outs[0]) <= 1e-9
+
+
+@pytest.mark.parametrize("name", ["allen_cahn_neumann_1024", "cahn_hilliard_split_512", "gray_scott_2048"])
+def test_benchmark_workloads_in_the_bench_launch_configuration(name):
+    """The benchmarked workloads at full size in the configuration bench.py times (tiles and the
+    fused update chosen by the autotuner, the device-side loop): three steps from the initial
+    state, each meeting the stopping rule with F evaluated by the oracle from the GPU's U^k and
+    U^{k+1}, and the iteration counts reported per step."""
+    rd = _rd()
+    w = BENCH_WORKLOADS[name]()
+    pb = w.problem
+    u = dev(w.u0)
+    with rd.Solver(pb, precision="fp32_dc", autotune=1, fused_update=1) as s:
+        for _ in range(3):
+            uk = host(u)
+            info = s.step(u, u)
+            U = host(u)
+            assert info["status"] == 0 and info["iterations"] > 0, info
+            r, thr = O.measure(pb, O.residual(pb, U, uk), uk)
+            assert r <= thr * (1 + 1e-6), (r, thr)
