@@ -137,6 +137,13 @@ def test_set_dt_and_limits():
     with pytest.raises(rd.RDError) as e:
         rd.Solver(pb, precision="fp32_dc")
     assert e.value.status == rd.RD_ERR_UNSUPPORTED
+    b = rd.Batch(1 << 26, 2)
+    try:
+        with pytest.raises(rd.RDError) as e:
+            b.submit(pb, uk, 1)
+        assert e.value.status == rd.RD_ERR_UNSUPPORTED
+    finally:
+        b.close()
 
 
 def test_paper_example_full_size_step_meets_the_stopping_rule():
