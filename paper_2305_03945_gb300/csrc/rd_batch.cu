@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(256) k_step_b(const Desc* __restrict__ d64s, S
     for (int c = 0; c < nc; ++c) tot += sqrt(sum_partials(d.partials + c * d.nbands, d.nbands, red));
     if (threadIdx.x == 0) {
       const double meas = d.meas_div_dt ? tot / d.dt : tot;
+      const double prev = outer->r;
       outer->ticket = 0u;
       outer->r = meas;
       const int n = outer->n;
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(256) k_step_b(const Desc* __restrict__ d64s, S
         sl->phase = PH_FAILED;
       } else {
         State* in = &sl->inner;
+        in->stall_mul = next_stall_mul(n, meas, prev, in->stall_mul);
         in->n = 0;
         in->r = 0.0;
         in->r0 = 0.0;

@@ -92,7 +92,18 @@ struct State {
   unsigned int ticket;
   int total;         // defect-correction outer state: PDHG updates of this step's inner solves
   int launches;      // defect-correction outer state: k_res launches of this step's inner solves
+  int stall_mul;     // inner solve: its stall window is Desc::stall_window times this (0 = 1);
+                     // the outer rule doubles it after a round that did not halve the residual
 };
+
+// Stall-window factor of the next inner solve: doubled (up to 64) after an outer round whose FP64
+// residual `meas` did not halve from the previous round's `prev` (the inner solve was cut off by
+// its stall rule before it made progress, as in slowly converging steps), else back to 1.
+__host__ __device__ inline int next_stall_mul(int n, double meas, double prev, int mul) {
+  if (mul < 1) mul = 1;
+  if (n >= 1 && !(meas <= 0.5 * prev)) return mul < 64 ? 2 * mul : 64;
+  return 1;
+}
 
 // Phases of one slot of a batch (device-side control of FP64 defect correction and time steps).
 enum Phase {

@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(256)
     for (int c = 0; c < nc; ++c) tot += sqrt(sum_partials(d.partials + c * nb, nb, red));
     if (threadIdx.x == 0) {
       const double meas = d.meas_div_dt ? tot / d.dt : tot;
+      const double prev = outer->r;
       outer->ticket = 0u;
       outer->r = meas;
       const int n = outer->n;
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(256)
       } else if (n >= max_outer) {
         outer->status = ST_NOT_CONVERGED;
       } else {
+        inner->stall_mul = next_stall_mul(n, meas, prev, inner->stall_mul);
         inner->n = 0;
         inner->trips = 0u;
         inner->r = 0.0;

@@ -239,7 +239,7 @@ __device__ inline void finalize_measure(const Desc& d, State* st, double* red, S
     st->status = ST_CONVERGED;
   } else if (!isfinite(meas) || meas > kDivergeFactor * r0) {
     st->status = ST_DIVERGED;
-  } else if (d.stall_window > 0 && n - st->best_n >= d.stall_window) {
+  } else if (d.stall_window > 0 && n - st->best_n >= d.stall_window * (st->stall_mul > 1 ? st->stall_mul : 1)) {
     st->status = ST_CONVERGED;  // stalled at the rounding floor of this precision
   } else if (n >= st->max_iter) {
     st->status = ST_NOT_CONVERGED;

@@ -483,3 +483,29 @@ def test_benchmark_workloads_in_the_bench_launch_configuration(name):
             assert info["status"] == 0 and info["iterations"] > 0, info
             r, thr = O.measure(pb, O.residual(pb, U, uk), uk)
             assert r <= thr * (1 + 1e-6), (r, thr)
+
+
+def test_defect_correction_stall_window_escalates():
+    """A request of the serving mix (Allen-Cahn Neumann 64^2, 49 steps, ||F|| <= 1e-6 ||U^k||)
+    whose step 47 converges slowly: with a fixed stall window the FP32 inner solves were cut off
+    before they made progress and the step ran out of outer rounds.  The window now doubles after
+    an outer round that does not halve the FP64 residual, so every step converges, alone and in a
+    batch, and the result agrees with the plain FP64 solve to the tolerance."""
+    rd = _rd()
+    pb, u0, n = WL.serving_requests(456, 5000)[455]
+    assert (pb.kind, pb.bc, pb.nx, n) == ("allen_cahn", "neumann", 64, 49)
+    outs = {}
+    for prec in ("fp32_dc", "fp64"):
+        u = dev(u0)
+        with rd.Solver(pb, precision=prec) as s:
+            infos, st = s.solve(u, n)
+        assert st == 0 and all(i["status"] == 0 for i in infos)
+        outs[prec] = host(u)
+    assert np.linalg.norm(outs["fp32_dc"] - outs["fp64"]) <= 1e-5 * np.linalg.norm(outs["fp64"])
+    with rd.Batch(1 << 28, 4) as b:
+        rid, out = b.submit(pb, u0, n)
+        res = []
+        while not res:
+            res = b.poll(timeout=5.0)
+    assert res[0]["status"] == 0 and res[0]["steps"] == n, res[0]
+    assert np.linalg.norm(out - outs["fp64"]) <= 1e-5 * np.linalg.norm(outs["fp64"])
