@@ -11,7 +11,7 @@ eta in (0, 1):
   * N_* <= M <= N^*     ->  h_t unchanged
   * M < N_*             ->  h_t <- h_t / eta if h_t / eta <= h_t^0, else unchanged
 
-Readings where the paper is silent (each is listed in the design doc):
+Readings where the paper is silent:
   * a step whose PDHG solve fails (not converged within max_iter, or diverged) is not accepted:
     it is taken again from U^k with eta h_t (the first rule applied to a step that needed more
     than any N^* iterations);

@@ -18,7 +18,7 @@ Everything is written for readability against the paper (arxiv 2305.03945):
                           Algorithm 1, initial guess U_0 = U^k, P_0 = 0, extrapolation omega,
                           stopping rule ||Res(U_n)||_2 <= delta (Section 2.1 "Stopping criterion")
 
-Conventions and readings of the paper (each is listed in the design doc):
+Conventions, and readings of the paper where it is silent or inconsistent:
   * arrays are ``[ncomp, ny, nx]``, x fastest; h_x = lx/nx, h_y = ly/ny for BOTH boundary
     conditions (Neumann nodes are cell centres, as in the paper's examples);
   * Cahn-Hilliard: F(U) = (I + a dt Lap^2) U - U^k - b dt Lap W'(U), G = (I + a dt Lap^2)^2

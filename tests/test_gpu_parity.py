@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the CPU FP64 oracle, element by element,
 on the same seeded inputs.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (from the arithmetic of each path):
   * single operators (F, G^{-1}) in FP64: 1e-12 relative to the largest magnitude;
   * a converged FP64 step: the same iteration count as the oracle (ties within 1e-9 of delta
     excepted) and max |U_gpu - U_ref| <= 1e-10 max |U_ref|;

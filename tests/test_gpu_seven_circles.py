@@ -7,11 +7,11 @@ tau_u = tau_p = 0.5, and reports that u at (pi/2, pi/2) changes sign at a time T
 
 With the parameters as printed, the implicit five-point scheme changes sign earlier at the first
 point and later at the second: the oracle's independent fixed-point solver
-(tests/golden/seven_circles_fd.json, written by make_seven_circles_fd.py) and a spectral
-Laplacian alike give T1 near 5.58 and T2 near 27.05 (5.54 and 26.87 spectrally), so the paper's interval is not reproduced
-by this scheme (the reading is recorded in the design doc).  The pin is therefore the scheme's own
-crossing steps from the oracle: the CUDA path, through the C ABI, must change sign at exactly
-the same steps, 1117 and 5410."""
+(tests/golden/seven_circles_fd.json, written by make_seven_circles_fd.py) gives T1 near 5.58
+and T2 near 27.05, and a spectral Laplacian 5.54 and 26.87, so the paper's intervals are not
+reproduced by this scheme.  The pin is therefore the scheme's own crossing steps from the
+oracle: the CUDA path, through the C ABI, must change sign at exactly the same steps, 1117 and
+5410."""
 import json
 import os
 
