@@ -1306,7 +1306,7 @@ rd_status rd_pdhg_residual(rd_pdhg* h, const double* u, const double* u_k, doubl
   const int nb = point_blocks(h->nx, h->ny);
   RD_CUDA(launch_begin(h->d_desc + 0, h->d_state + 2, u_k, h->rhs64, 0.0, 0, nb, h->stream));
   if (h->fch) {
-    RD_CUDA(launch_fch_residual(h->h_desc[0], nullptr, h->fchb, u, h->rhs64, w, 1, h->stream));
+    RD_CUDA(launch_fch_residual(h->h_desc[0], nullptr, h->fchb, u, h->rhs64, w, 2 * nb, h->stream));
     RD_CUDA(cudaStreamSynchronize(h->stream));
     return RD_OK;
   }
