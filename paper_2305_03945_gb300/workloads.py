@@ -182,13 +182,15 @@ def cosine_mode(pb: Problem, kx: int, ky: int) -> np.ndarray:
     return np.broadcast_to(m, (pb.ncomp, pb.ny, pb.nx)).copy()
 
 
-def seven_circles(n: int) -> np.ndarray:
-    """Cahn-Hilliard seven-circle initial data of Section 3.2.1 (Table 1), on [0,2pi)^2."""
+def seven_circles(n: int, node_offset: float = 0.0, mollifier_eps: float = 0.1) -> np.ndarray:
+    """Cahn-Hilliard seven-circle initial data of Section 3.2.1 (Table 1), on [0,2pi)^2, at the
+    periodic nodes (j + node_offset) h, h = 2 pi / n, with the mollifier width eps of that
+    section (0.1)."""
     xs = np.array([np.pi / 2, np.pi / 4, np.pi / 2, np.pi, 3 * np.pi / 2, np.pi, 3 * np.pi / 2])
     ys = np.array([np.pi / 2, 3 * np.pi / 4, 5 * np.pi / 4, np.pi / 4, np.pi / 4, np.pi, 3 * np.pi / 2])
     rs = np.array([np.pi / 5, 2 * np.pi / 15, np.pi / 15, np.pi / 10, np.pi / 10, np.pi / 4, np.pi / 4])
-    eps = 0.1
-    x = cell_centres(n, 2 * np.pi, "periodic")
+    eps = mollifier_eps
+    x = cell_centres(n, 2 * np.pi, "periodic") + node_offset * 2 * np.pi / n
     X, Y = np.meshgrid(x, x)
     u = -np.ones((n, n))
     for xi, yi, ri in zip(xs, ys, rs):
