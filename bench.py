@@ -1,17 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 PDHG solver for implicit reaction-diffusion steps.
 
-Workload (default): Allen-Cahn, Neumann, 1024 x 1024 cell-centred grid on [0,1]^2, eps = 0.01
-(a = eps, b = 1/eps), dt = 1e-4, u0 = tanh of seeded smoothed Gaussian noise, each implicit
-step solved to ||F||_2 <= 1e-11 ||U^k||_2 with FP32 PDHG sweeps inside FP64 defect correction.
-One benchmark step = one implicit time step (every PDHG iteration of it, the FP64 residual
-passes and the defect-correction updates) continuing from the previous step's state.
+Workload (default): two-species Gray-Scott, periodic 2 x 2048 x 2048 grid on [0,2.5)^2,
+Du = 2e-5, Dv = 1e-5, F = 0.04, k = 0.06, dt = 1, u = 1, v = 0 with ten seeded square patches
+and 1% noise, each implicit step solved to ||F||_2 <= 1e-11 ||U^k||_2 with FP32 PDHG sweeps
+inside FP64 defect correction (the largest configuration, and the one whose working set exceeds
+L2).  ``--workload`` selects the others (Allen-Cahn Neumann 1024^2, Cahn-Hilliard split 512^2,
+Allen-Cahn periodic 64^2, the sixth-order example 128^2).  One benchmark step = one implicit
+time step (every PDHG iteration of it, the FP64 residual passes and the defect-correction
+updates) continuing from the previous step's state.
 
 Metric: PDHG Gpoint-iterations/s = sum over timed steps of (grid points x components x PDHG
 iterations) / device time.  L2 is flushed (256 MiB write) between timed steps.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU FP64 oracle instead (the
-paper has no code; its method restated plainly is the reference arm).
+paper has no code; its method restated plainly is the reference arm): the plain C++ oracle on
+all host cores, each bench step a bounded sample of PDHG iterations of the full-size workload.
 """
 from __future__ import annotations
 
@@ -174,16 +178,35 @@ def read_traffic(name, kernel, shash=None):
 # --------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # --------------------------------------------------------------------------------------------
-def oracle_steps(w, nsteps):
-    from oracle import rd_oracle as O
-    U = w.u0.copy()
+def oracle_iterations(pb, uk, iters, threads):
+    """Time the first `iters` PDHG iterations of one implicit step from uk with the C++ oracle
+    on `threads` host threads (0 = all).  Returns (iterations done, seconds, threads used)."""
+    from oracle import cpp_oracle as C
+    used = C.set_threads(threads)
+    q = pb.replace(max_iter=iters)
     t0 = time.perf_counter()
-    its = 0
-    for _ in range(nsteps):
-        U, info = O.pdhg_step(w.problem, U)
-        its += info["iterations"]
+    _, info = C.pdhg_step(q, uk)
     dt = time.perf_counter() - t0
-    return U, its, dt
+    C.set_threads(0)
+    return info["iterations"], dt, used
+
+
+def cpu_sample_iters(pb, uk, threads, budget_s):
+    """PDHG iterations of the full-size workload that fill about budget_s seconds of oracle time
+    (from a two-iteration probe), at least 1."""
+    its, dt, _ = oracle_iterations(pb, uk, 2, threads)
+    per = dt / max(its, 1)
+    return max(1, min(pb.max_iter, int(budget_s / max(per, 1e-6))))
+
+
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def run_reference(args, rank, world):
@@ -192,24 +215,26 @@ def run_reference(args, rank, world):
     w = workload(args.workload)
     pb = w.problem
     npts = pb.ncomp * pb.nx * pb.ny
-    from oracle import rd_oracle as O
-    U = w.u0.copy()
+    iters = args.ref_iters if args.ref_iters > 0 else cpu_sample_iters(pb, w.u0, 0, 4.0)
     for _ in range(args.warmup):
-        U, _ = O.pdhg_step(pb, U)
-    its, tot = 0, 0.0
+        oracle_iterations(pb, w.u0, iters, 0)
+    its, tot, used = 0, 0.0, 0
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        U, info = O.pdhg_step(pb, U)
-        tot += time.perf_counter() - t0
-        its += info["iterations"]
+        n, dt, used = oracle_iterations(pb, w.u0, iters, 0)
+        its += n
+        tot += dt
     v = npts * its / tot / 1e9
+    sample = ("each bench step: the first %d PDHG iterations of the first implicit step of the full-size "
+              "workload (C++ FP64 oracle, %d threads)" % (iters, used))
     line = {"impl": "reference", "metric": "PDHG Gpoint-iters/s", "value": v, "unit": "Gpoint-iter/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "grid": "%dx%d" % (pb.nx, pb.ny),
-                                            "solver": "CPU FP64 oracle (numpy), one implicit step per bench step"},
-            "cpu_baseline": {"value": v, "unit": "Gpoint-iter/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d implicit steps after %d warm-up steps" % (args.steps, args.warmup)},
+            "data": "synthetic", "config": {"workload": args.workload, "grid": "%dx%dx%d" % (pb.ncomp, pb.ny, pb.nx),
+                                            "bc": pb.bc, "kind": pb.kind, "dt": pb.dt,
+                                            "tol": "%s %g" % (pb.tol_kind, pb.tol),
+                                            "solver": "CPU FP64 oracle (plain C++, OpenMP over rows)"},
+            "cpu_baseline": {"value": v, "unit": "Gpoint-iter/s", "cores": used, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": v, "unit": "Gpoint-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -441,18 +466,31 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ns = args.cpu_steps
-        U_ref, its_ref, dt_ref = oracle_steps(w, ns)
-        cpu = {"value": npts * its_ref / dt_ref / 1e9, "unit": "Gpoint-iter/s", "cores": 1, "kind": "oracle",
-               "sample": "first %d implicit steps of the full workload from u0 (%d PDHG iterations, %.1f s)"
-                         % (ns, its_ref, dt_ref)}
-        up = torch.from_numpy(w.u0.copy()).to(dev)
-        sp = rd.Solver(pb, precision=args.precision)
-        infos_p, _ = sp.solve(up, ns)
-        sp.close()
-        got = up.cpu().numpy()
-        parity = {"steps": ns, "rel_l2_vs_oracle": float(np.linalg.norm(got - U_ref) / np.linalg.norm(U_ref)),
-                  "max_rel_vs_oracle": float(np.max(np.abs(got - U_ref)) / np.max(np.abs(U_ref)))}
+        # the C++ oracle on all host cores, then on one, each over a bounded sample of PDHG
+        # iterations of the first implicit step of the full-size workload
+        n_all = cpu_sample_iters(pb, w.u0, 0, args.cpu_seconds)
+        its_a, dt_a, used = oracle_iterations(pb, w.u0, n_all, 0)
+        n_one = cpu_sample_iters(pb, w.u0, 1, args.cpu_seconds / 2)
+        its_1, dt_1, _ = oracle_iterations(pb, w.u0, n_one, 1)
+        cpu = {"value": npts * its_a / dt_a / 1e9, "unit": "Gpoint-iter/s", "cores": used, "kind": "oracle",
+               "sample": "the first %d PDHG iterations of the first implicit step of the full-size workload "
+                         "(C++ FP64 oracle, %d threads, %.1f s)" % (its_a, used, dt_a),
+               "cpu": cpu_model(), "nproc": os.cpu_count(),
+               "single_thread": {"value": npts * its_1 / dt_1 / 1e9, "iterations": its_1, "seconds": dt_1}}
+        ns = args.parity_steps
+        if ns > 0:
+            from oracle import cpp_oracle as C
+            C.set_threads(0)
+            U_ref = w.u0.copy()
+            for _ in range(ns):
+                U_ref, _ = C.pdhg_step(pb, U_ref)
+            up = torch.from_numpy(w.u0.copy()).to(dev)
+            sp = rd.Solver(pb, precision=args.precision)
+            infos_p, _ = sp.solve(up, ns)
+            sp.close()
+            got = up.cpu().numpy()
+            parity = {"steps": ns, "rel_l2_vs_oracle": float(np.linalg.norm(got - U_ref) / np.linalg.norm(U_ref)),
+                      "max_rel_vs_oracle": float(np.max(np.abs(got - U_ref)) / np.max(np.abs(U_ref)))}
 
     sv.close()
 
@@ -540,10 +578,15 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="allen_cahn_neumann_1024", choices=WORKLOADS)
+    ap.add_argument("--workload", default="gray_scott_2048", choices=WORKLOADS)
     ap.add_argument("--precision", default="fp32_dc", choices=("fp32_dc", "fp64"))
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--cpu-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=16.0,
+                    help="oracle time of the all-core CPU baseline sample (the single-thread one gets half)")
+    ap.add_argument("--parity-steps", type=int, default=1,
+                    help="implicit steps of the full-size GPU-vs-oracle sample (0: skip)")
+    ap.add_argument("--ref-iters", type=int, default=0,
+                    help="reference arm: PDHG iterations per bench step (0: about 4 s of oracle time)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -573,10 +616,17 @@ def main():
                     help="adaptive leg: h_t^0 as a multiple of the workload's dt")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-rates", type=float, nargs="*", default=[0.5, 1.0])
+    ap.add_argument("--serving-full", action="store_true",
+                    help="the whole serving configuration: 4000 requests, Poisson rates 0.25..1.25 x saturation, "
+                         "per-request plain FP64 on every request")
     ap.add_argument("--serving-budget-gb", type=float, default=8.0)
     ap.add_argument("--serving-slots", type=int, default=32)
     ap.add_argument("--serving-fp64-sample", type=int, default=16)
     args = ap.parse_args()
+    if args.serving_full:
+        args.serving_requests = 4000
+        args.serving_rates = [0.25, 0.5, 0.75, 1.0, 1.25]
+        args.serving_fp64_sample = 4000
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.workload == "fch_128" and args.precision == "fp32_dc":

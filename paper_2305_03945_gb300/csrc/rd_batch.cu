@@ -652,8 +652,17 @@ void retire(rd_batch* b, int s, const Slot& ctl) {
       b->outputs.erase(it);
     }
   }
-  if (out) cudaMemcpyAsync(out, sh.d64.X, sh.npts * 8, cudaMemcpyDeviceToHost, b->stream);
-  cudaStreamSynchronize(b->stream);
+  // the result copy and the wait for it: a failure of either reports the request as RD_ERR_CUDA
+  // (its host output would hold stale data) and is kept as the worker's error
+  cudaError_t ce = cudaSuccess;
+  if (out) ce = cudaMemcpyAsync(out, sh.d64.X, sh.npts * 8, cudaMemcpyDeviceToHost, b->stream);
+  const cudaError_t se = cudaStreamSynchronize(b->stream);
+  if (ce == cudaSuccess) ce = se;
+  std::string copy_error;
+  if (ce != cudaSuccess) {
+    res.status = RD_ERR_CUDA;
+    copy_error = std::string("result copy of request ") + std::to_string(sh.id) + ": " + cudaGetErrorString(ce);
+  }
   res.t_submit = sh.t_submit;
   res.t_admit = sh.t_admit;
   res.t_done = now_s();
@@ -663,6 +672,7 @@ void retire(rd_batch* b, int s, const Slot& ctl) {
   sh = SlotHost{};
   b->stats.completed += 1;
   std::lock_guard<std::mutex> lk(b->mu);
+  if (!copy_error.empty()) b->worker_error = copy_error;
   b->done.push_back(res);
   b->cv.notify_all();
 }

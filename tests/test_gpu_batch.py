@@ -82,6 +82,48 @@ def test_same_result_alone_and_in_the_mix():
     assert next(iter(res_alone.values()))["iterations"] == res_mix[ids[2]]["iterations"]
 
 
+def _long_request(k):
+    """A 256^2 Allen-Cahn run of 40 steps: still on the GPU when the probe arrives."""
+    pb = WL.Problem(nx=256, ny=256, lx=1.0, ly=1.0, bc="periodic" if k % 2 == 0 else "neumann", op="laplacian",
+                    kind="allen_cahn", dt=2e-3, a=0.05, b=20.0, tau_u=1.0, tau_p=1.0, tol=1e-11, tol_kind="f_rel")
+    return pb, WL.uniform_field(70 + k, pb.shape, -0.5, 0.5), 40
+
+
+@pytest.mark.parametrize("slots", [8, 2])
+def test_request_arriving_while_others_run(slots):
+    """Continuous batching: the probe is submitted only once the batch's graph is running the
+    other requests (slots = 8: admitted beside them at once; slots = 2: queued until a running
+    request frees its slot).  Its result and iteration count are bit-identical to the same
+    request served alone."""
+    from paper_2305_03945_gb300 import rd
+    probe = _requests()[2]
+    _, res_alone, out_alone, _ = _run([probe])
+    alone = next(iter(res_alone.values()))
+    results = {}
+    with rd.Batch(1 << 30, slots) as b:
+        others = [b.submit(*_long_request(k), tag=k)[0] for k in range(2)]
+        t0 = time.time()
+        while b.stats()["graph_launches"] < 3 and time.time() - t0 < 60:
+            time.sleep(0.002)
+        st = b.stats()
+        assert st["graph_launches"] >= 3 and st["completed"] == 0, st
+        pid, pout = b.submit(*probe, tag=99)
+        while len(results) < 3 and time.time() - t0 < 120:
+            for r in b.poll(timeout=1.0):
+                results[r["id"]] = r
+    assert len(results) == 3 and all(r["status"] == 0 for r in results.values()), results
+    p = results[pid]
+    # the probe was admitted while the other requests were running
+    assert all(p["t_admit"] < results[o]["t_done"] for o in others) or slots == 2
+    if slots == 2:
+        # no free slot at submission: admitted only after one of the running requests finished
+        assert p["t_admit"] >= min(results[o]["t_done"] for o in others) - 1e-3
+        assert p["t_admit"] > p["t_submit"]
+    assert p["t_admit"] < max(results[o]["t_done"] for o in others)
+    assert np.array_equal(pout, next(iter(out_alone.values())))
+    assert p["iterations"] == alone["iterations"] and p["outer_rounds"] == alone["outer_rounds"]
+
+
 def test_admission_under_a_small_budget():
     """A budget that holds only a couple of 128^2 slots still serves every request."""
     reqs = [r for r in _requests() if r[0].nx <= 128][:4] * 2

@@ -8,6 +8,7 @@ import pytest
 
 from oracle import rd_oracle as O
 from paper_2305_03945_gb300 import workloads as WL
+from parity_util import assert_same_iterations
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -90,30 +91,53 @@ def test_step_matches_oracle(bc, shape, loop):
     rd = _rd()
     pb = _pb(*shape, bc=bc)
     uk = _u0(pb, 3)
-    U_ref, info_ref = O.pdhg_step(pb, uk)
+    U_ref, info_ref = O.pdhg_step(pb, uk, history=True)
     with rd.Solver(pb, solve_loop=loop) as s:
         out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
         info = s.step(dev(uk), out)
         U = host(out)
     assert info_ref["status"] == O.OK and info["status"] == 0
-    assert abs(info["iterations"] - info_ref["iterations"]) <= 1
+
+    def measure_at(m):
+        with rd.Solver(pb.replace(max_iter=m), solve_loop=loop) as s:
+            o = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+            i = s.step(dev(uk), o, allow=(rd.RD_OK, rd.RD_ERR_NOT_CONVERGED))
+        return i["residual"]
+    assert_same_iterations(info["iterations"], info_ref, pb, uk, measure_at)
     assert rel_max(U, U_ref) <= 1e-10
 
 
 def test_paper_example_steps_match_oracle():
     """The paper's initial data and parameters (Section 3.3) on 64^2, 10 steps through
-    rd_pdhg_solve: per-step iteration counts within one of the oracle's and the state within
-    1e-9; mass conserved."""
+    rd_pdhg_solve: per-step iteration counts equal to the oracle's (a rounding tie at the
+    threshold aside, checked on the GPU's own iterate) and the state within 1e-9; mass
+    conserved."""
     rd = _rd()
     w = WL.config_fch(64)
     pb = dataclasses.replace(w.problem, tol=1e-9, tol_kind="f_rel")
-    U_ref, infos_ref = O.solve(pb, w.u0, 10)
+    U_ref, infos_ref = O.solve(pb, w.u0, 10, history=True)
     u = dev(w.u0)
+    states = [host(u)]
+    infos = []
     with rd.Solver(pb) as s:
-        infos, st = s.solve(u, 10)
+        for _ in range(10):
+            infos.append(s.step(u, u))
+            states.append(host(u))
     U = host(u)
-    assert st == 0 and all(i["status"] == O.OK for i in infos_ref)
-    assert all(abs(a["iterations"] - b["iterations"]) <= 1 for a, b in zip(infos, infos_ref))
+    assert all(i["status"] == 0 for i in infos) and all(i["status"] == O.OK for i in infos_ref)
+    for k, (a, b) in enumerate(zip(infos, infos_ref)):
+        if a["iterations"] == b["iterations"]:
+            continue
+        # a tie: compare the two measures of the same iterate of step k from the GPU's U^k
+        uk = states[k]
+        _, b = O.pdhg_step(pb, uk, history=True)
+
+        def measure_at(m, uk=uk):
+            with rd.Solver(pb.replace(max_iter=m)) as s:
+                o = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
+                i = s.step(dev(uk), o, allow=(rd.RD_OK, rd.RD_ERR_NOT_CONVERGED))
+            return i["residual"]
+        assert_same_iterations(a["iterations"], b, pb, uk, measure_at)
     assert rel_max(U, U_ref) <= 1e-9
     assert abs(O.mass(pb, U) - O.mass(pb, w.u0)) <= 1e-10
 

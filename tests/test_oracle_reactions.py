@@ -13,15 +13,27 @@ the oracle's PDHG step against
     -Lap of the mode, up to O(eps^2) relative (the quadratic terms land in the mean and in the
     doubled mode, not in the mode itself).
 A sign, index or coefficient mistake in any reaction term (u v^2 against F(1 - u), the split's
-+b dt Lap U^k, D_u against D_v) moves one of these by far more than its tolerance.
++b dt Lap U^k, D_u against D_v) moves one of these by far more than its tolerance.  Every test
+runs against both oracles (numpy and C++).
 """
 import math
 
 import numpy as np
 import pytest
 
-from oracle import rd_oracle as O
+from oracle import cpp_oracle, rd_oracle
 from paper_2305_03945_gb300 import workloads as WL
+
+
+@pytest.fixture(params=["numpy", "cpp"])
+def O(request):
+    """Both oracles: the numpy restatement and the plain C++ one."""
+    if request.param == "cpp":
+        cpp_oracle.set_threads(1)
+        yield cpp_oracle
+        cpp_oracle.set_threads(0)
+    else:
+        yield rd_oracle
 
 TIGHT = dict(tol=1e-14, tol_kind="f_rel", max_iter=20000)
 
@@ -71,7 +83,7 @@ def _gs(bc, n=16, dt=1.0, p=(2e-5, 1e-5, 0.04, 0.06)):
 
 @pytest.mark.parametrize("bc", ["periodic", "neumann"])
 @pytest.mark.parametrize("dt", [0.5, 1.0])
-def test_gray_scott_uniform_step_is_the_ode_step(bc, dt):
+def test_gray_scott_uniform_step_is_the_ode_step(bc, dt, O):
     pb = _gs(bc, dt=dt)
     Du, Dv, Ff, k = pb.p
     uk, vk = 0.7, 0.2
@@ -83,7 +95,7 @@ def test_gray_scott_uniform_step_is_the_ode_step(bc, dt):
     assert np.max(np.abs(U[0] - us)) <= 1e-12 and np.max(np.abs(U[1] - vs)) <= 1e-12
 
 
-def test_gray_scott_steady_states_are_fixed_points():
+def test_gray_scott_steady_states_are_fixed_points(O):
     """(1, 0) and, for F = 0.04, k = 0.05, the two uniform roots of u v = F + k,
     F (1 - u) = (F + k) v (a quadratic in v) are steady: F(U) = 0 at U = U^k."""
     pb = _gs("periodic", p=(2e-5, 1e-5, 0.04, 0.05))
@@ -99,7 +111,7 @@ def test_gray_scott_steady_states_are_fixed_points():
 
 
 @pytest.mark.parametrize("bc,kx,ky", [("periodic", 3, 1), ("neumann", 2, 5)])
-def test_gray_scott_mode_on_the_trivial_state_decays_per_species(bc, kx, ky):
+def test_gray_scott_mode_on_the_trivial_state_decays_per_species(bc, kx, ky, O):
     """Around (1, 0) the linearised step is u^ <- u^ / (1 + dt (Du mu + F)) and
     v^ <- v^ / (1 + dt (Dv mu + F + k)): each species' own diffusion and linear reaction."""
     pb = _gs(bc, dt=1.0, p=(2e-3, 1e-3, 0.04, 0.06))
@@ -123,7 +135,7 @@ def _sch(n=8, dt=1 / 5000):
                       p=(0.05, 1.0, 100.0, 0.1305, 0.7695), dt=dt, tau_u=0.9, tau_p=0.9, **TIGHT)
 
 
-def test_schnakenberg_equilibrium_is_a_fixed_point():
+def test_schnakenberg_equilibrium_is_a_fixed_point(O):
     """The equilibrium (a + b, b / (a + b)^2) that Section 3.4.1 perturbs."""
     pb = _sch()
     a_s, b_s = pb.p[3], pb.p[4]
@@ -134,7 +146,7 @@ def test_schnakenberg_equilibrium_is_a_fixed_point():
 
 
 @pytest.mark.parametrize("dt", [1 / 5000, 1 / 1000])
-def test_schnakenberg_uniform_step_is_the_ode_step(dt):
+def test_schnakenberg_uniform_step_is_the_ode_step(dt, O):
     pb = _sch(dt=dt)
     kap, a_s, b_s = pb.p[2], pb.p[3], pb.p[4]
     uk, vk = 1.1, 0.5
@@ -156,7 +168,7 @@ def _ac(bc, n=16, dt=0.01):
 
 
 @pytest.mark.parametrize("uk", [0.3, -0.8, 1.2])
-def test_allen_cahn_uniform_step_is_the_ode_step(uk):
+def test_allen_cahn_uniform_step_is_the_ode_step(uk, O):
     pb = _ac("periodic").replace(tau_u=0.7, tau_p=0.7)
     us = _newton2(lambda u, v: (u - uk + pb.dt * pb.b * (u ** 3 - u), v),
                   lambda u, v: ((1 + pb.dt * pb.b * (3 * u * u - 1), 0.0), (0.0, 1.0)), (uk, 0.0))[0]
@@ -166,7 +178,7 @@ def test_allen_cahn_uniform_step_is_the_ode_step(uk):
 
 @pytest.mark.parametrize("bc,kx,ky", [("periodic", 2, 3), ("neumann", 4, 1)])
 @pytest.mark.parametrize("ubar", [0.0, 1.0, -1.0])
-def test_allen_cahn_mode_on_a_steady_state(bc, kx, ky, ubar):
+def test_allen_cahn_mode_on_a_steady_state(bc, kx, ky, ubar, O):
     """Around the uniform steady states u = 0, +-1: u^ <- u^ / (1 + dt (a mu + b (3 u^2 - 1)))."""
     pb = _ac(bc, dt=0.005)
     phi, mu = _mode(pb, kx, ky)
@@ -189,7 +201,7 @@ def _ch(kind, bc, n=16, dt=1e-5):
 
 @pytest.mark.parametrize("bc,kx,ky", [("periodic", 1, 2), ("neumann", 3, 2)])
 @pytest.mark.parametrize("ubar", [0.0, 0.45])
-def test_cahn_hilliard_split_mode(bc, kx, ky, ubar):
+def test_cahn_hilliard_split_mode(bc, kx, ky, ubar, O):
     """Split step on u = ubar + eps phi:
     (1 + a dt mu^2 + 3 b dt ubar^2 mu) u^ = (1 + b dt mu) u^k^  (ubar = 0 isolates the explicit
     +b dt Lap U^k term, ubar != 0 the implicit U^3 term); the mean stays ubar."""
@@ -205,7 +217,7 @@ def test_cahn_hilliard_split_mode(bc, kx, ky, ubar):
 
 @pytest.mark.parametrize("bc,kx,ky", [("periodic", 1, 2), ("neumann", 3, 2)])
 @pytest.mark.parametrize("ubar", [0.0, 0.45, 0.9])
-def test_cahn_hilliard_implicit_mode(bc, kx, ky, ubar):
+def test_cahn_hilliard_implicit_mode(bc, kx, ky, ubar, O):
     """Fully implicit step: (1 + a dt mu^2 + b dt (3 ubar^2 - 1) mu) u^ = u^k^."""
     pb = _ch("ch_implicit", bc)
     phi, mu = _mode(pb, kx, ky)

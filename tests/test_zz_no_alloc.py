@@ -1,5 +1,6 @@
 """The allocation-free preconditioner solve (rd_apply_precond_static) against the handle-based
-one (rd_pdhg_apply_precond), through the C ABI, on two calls in a row.
+one (rd_pdhg_apply_precond), through the C ABI, on two calls in a row (and, on the same inputs,
+against the oracle's G^{-1}).
 
 This entry point serves callers that cannot allocate device memory when they need G^{-1} W
 (a fixed memory budget they do not own, loops that must not pay cudaMalloc's device-wide
@@ -11,6 +12,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import rd_oracle as O
 from paper_2305_03945_gb300 import workloads as WL
 
 torch = pytest.importorskip("torch")
@@ -23,6 +25,13 @@ CASES = [
     ("ch_split", "neg_biharmonic", (), "neumann", (64, 64)),
     ("gray_scott", "laplacian", (2e-3, 1e-3, 0.04, 0.06), "periodic", (128, 128)),
     ("schnakenberg", "laplacian", (0.05, 1.0, 100.0, 0.1305, 0.7695), "neumann", (256, 256)),
+    # the longest lines the static solve admits (side 2048): row lines of 2048 points, column
+    # lines of 2048 points, and a two-row grid of 2048-point rows
+    ("allen_cahn", "laplacian", (), "periodic", (64, 2048)),
+    ("allen_cahn", "laplacian", (), "neumann", (64, 2048)),
+    ("allen_cahn", "laplacian", (), "periodic", (2048, 64)),
+    ("allen_cahn", "laplacian", (), "neumann", (2048, 64)),
+    ("ch_split", "neg_biharmonic", (), "neumann", (2, 2048)),
 ]
 
 
@@ -64,6 +73,9 @@ def test_static_scratch_solve_matches_handle_solve_twice(kind, op, p, bc, shape)
             torch.cuda.synchronize()
             g, t = got.cpu().numpy(), want.cpu().numpy()
             assert np.max(np.abs(g - t)) <= 1e-12 * np.max(np.abs(t))
+            # and directly against the oracle's FFT / DCT solve of the same G
+            ref = O.apply_ginv(pb, W.cpu().numpy())
+            assert np.max(np.abs(g - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
 def test_static_scratch_rejects_grids_beyond_its_limit():
@@ -72,3 +84,12 @@ def test_static_scratch_rejects_grids_beyond_its_limit():
     W = torch.zeros(pb.shape, dtype=torch.float64, device="cuda")
     assert _static(pb, W, W) == rd.RD_ERR_UNSUPPORTED
     assert b"131072" in rd.load().rd_last_error()
+
+
+@pytest.mark.parametrize("ny,nx", [(2, 4096), (4096, 2)])
+def test_static_scratch_rejects_sides_beyond_2048(ny, nx):
+    from paper_2305_03945_gb300 import rd
+    pb = _pb("allen_cahn", "laplacian", (), "neumann", ny, nx)  # 8192 points: within the point limit
+    W = torch.zeros(pb.shape, dtype=torch.float64, device="cuda")
+    assert _static(pb, W, W) == rd.RD_ERR_UNSUPPORTED
+    assert b"2048" in rd.load().rd_last_error()
