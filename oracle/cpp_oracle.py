@@ -36,7 +36,8 @@ class rdo_problem(ctypes.Structure):
                 ("dt", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double),
                 ("p", ctypes.c_double * 6), ("tau_u", ctypes.c_double), ("tau_p", ctypes.c_double),
                 ("omega", ctypes.c_double), ("precond", ctypes.c_int), ("tol", ctypes.c_double),
-                ("tol_kind", ctypes.c_int), ("max_iter", ctypes.c_int)]
+                ("tol_kind", ctypes.c_int), ("max_iter", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lz", ctypes.c_double)]
 
 
 def up_to_date() -> bool:
@@ -99,6 +100,7 @@ def _problem(pb) -> rdo_problem:
         s.p[k] = v
     s.tau_u, s.tau_p, s.omega = pb.tau_u, pb.tau_p, pb.omega
     s.precond, s.tol, s.tol_kind, s.max_iter = _PC[pb.precond], pb.tol, _TOL[pb.tol_kind], pb.max_iter
+    s.nz, s.lz = pb.nz, pb.lz
     return s
 
 

@@ -57,7 +57,41 @@ def lap_neumann(n, h):
     return M / h ** 2
 
 
+def second_difference(n, h, bc):
+    """1-D second difference (x_{j+1} + x_{j-1} - 2 x_j) / h^2 on n points: circulant (periodic)
+    or with the half-cell mirror ghost x_{-1} = x_0, x_n = x_{n-1} (Neumann, Remark 1)."""
+    m = np.zeros((n, n))
+    for j in range(n):
+        m[j, j] -= 2.0
+        for k in (j - 1, j + 1):
+            if 0 <= k < n:
+                m[j, k] += 1.0
+            elif bc == "periodic":
+                m[j, k % n] += 1.0
+            else:
+                m[j, j] += 1.0
+    return m / h ** 2
+
+
+def lap_kron(pb):
+    """Lap as the Kronecker sum of the 1-D second differences, vectorised l = (z ny + y) nx + x:
+    I_z (x) I_y (x) D_x + I_z (x) D_y (x) I_x [+ D_z (x) I_y (x) I_x on 3-D grids]."""
+    Dx = second_difference(pb.nx, pb.lx / pb.nx, pb.bc)
+    Dy = second_difference(pb.ny, pb.ly / pb.ny, pb.bc)
+    Ix, Iy = np.eye(pb.nx), np.eye(pb.ny)
+    L = np.kron(Iy, Dx) + np.kron(Dy, Ix)
+    if pb.nz > 1:
+        Dz = second_difference(pb.nz, pb.lz / pb.nz, pb.bc)
+        Iz = np.eye(pb.nz)
+        L = np.kron(Iz, L) + np.kron(Dz, np.kron(Iy, Ix))
+    return L
+
+
 def lap_matrix(pb):
+    """The paper's block matrices Lap^P / Lap^N on square 2-D grids; the Kronecker-sum form on
+    3-D grids (the paper prints no 3-D matrix)."""
+    if pb.nz > 1:
+        return lap_kron(pb)
     assert pb.nx == pb.ny and abs(pb.lx - pb.ly) < 1e-15, "dense pins use square grids"
     h = pb.lx / pb.nx
     return lap_periodic(pb.nx, h) if pb.bc == "periodic" else lap_neumann(pb.nx, h)

@@ -21,6 +21,9 @@ Everything is written for readability against the paper (arxiv 2305.03945):
 Conventions, and readings of the paper where it is silent or inconsistent:
   * arrays are ``[ncomp, ny, nx]``, x fastest; h_x = lx/nx, h_y = ly/ny for BOTH boundary
     conditions (Neumann nodes are cell centres, as in the paper's examples);
+  * 3-D grids (nz > 1, arrays ``[ncomp, nz, ny, nx]``; not in the paper, which is 2-D): the same
+    scheme with a third axis -- seven-point Laplacian, the symbol with a third sin^2 term, the
+    transforms over all three axes;
   * Cahn-Hilliard: F(U) = (I + a dt Lap^2) U - U^k - b dt Lap W'(U), G = (I + a dt Lap^2)^2
     (the paper's lambda = -a sign reading of eq. (F(U) CH));
   * the stop test is applied to U_n before each update and ties go to "stop" (r <= delta);
@@ -41,8 +44,13 @@ DIVERGE_FACTOR = 1e8
 # ----------------------------------------------------------------------------------------
 
 def spacing(pb):
-    """(h_x, h_y): side length over number of cells (Algorithm 1 line 2: h_x = L / N_x)."""
+    """(h_x, h_y): side length over number of cells (Algorithm 1: h_x = L / N_x)."""
     return pb.lx / pb.nx, pb.ly / pb.ny
+
+
+def spacing_z(pb):
+    """h_z of a 3-D grid (the same rule along the third axis)."""
+    return pb.lz / pb.nz
 
 
 def _shift(u, axis, step, bc):
@@ -61,10 +69,14 @@ def _shift(u, axis, step, bc):
 
 
 def lap(u, pb):
-    """Five-point Laplacian (x_{i,j+1} + x_{i,j-1} - 2x)/h_x^2 + (x_{i+1,j} + x_{i-1,j} - 2x)/h_y^2."""
+    """Five-point Laplacian (x_{i,j+1} + x_{i,j-1} - 2x)/h_x^2 + (x_{i+1,j} + x_{i-1,j} - 2x)/h_y^2;
+    on a 3-D grid the seven-point one, with (x_{l+1} + x_{l-1} - 2x)/h_z^2 along z added."""
     hx, hy = spacing(pb)
-    return ((_shift(u, -1, 1, pb.bc) + _shift(u, -1, -1, pb.bc) - 2 * u) / hx ** 2
-            + (_shift(u, -2, 1, pb.bc) + _shift(u, -2, -1, pb.bc) - 2 * u) / hy ** 2)
+    out = ((_shift(u, -1, 1, pb.bc) + _shift(u, -1, -1, pb.bc) - 2 * u) / hx ** 2
+           + (_shift(u, -2, 1, pb.bc) + _shift(u, -2, -1, pb.bc) - 2 * u) / hy ** 2)
+    if pb.nz > 1:
+        out = out + (_shift(u, -3, 1, pb.bc) + _shift(u, -3, -1, pb.bc) - 2 * u) / spacing_z(pb) ** 2
+    return out
 
 
 def symbol_mu(pb):
@@ -77,8 +89,12 @@ def symbol_mu(pb):
     kx = np.arange(pb.nx)[None, :]
     ky = np.arange(pb.ny)[:, None]
     d = 1.0 if pb.bc == "periodic" else 2.0
-    return (4 / hx ** 2 * np.sin(np.pi * kx / (d * pb.nx)) ** 2
-            + 4 / hy ** 2 * np.sin(np.pi * ky / (d * pb.ny)) ** 2)
+    mu = (4 / hx ** 2 * np.sin(np.pi * kx / (d * pb.nx)) ** 2
+          + 4 / hy ** 2 * np.sin(np.pi * ky / (d * pb.ny)) ** 2)
+    if pb.nz > 1:   # 3-D: shape [nz, ny, nx], a third sin^2 term along z
+        kz = np.arange(pb.nz)[:, None, None]
+        mu = mu[None] + 4 / spacing_z(pb) ** 2 * np.sin(np.pi * kz / (d * pb.nz)) ** 2
+    return mu
 
 
 # ----------------------------------------------------------------------------------------
@@ -211,10 +227,11 @@ def apply_ginv(pb, W, g=None):
         g = ghat(pb)
     if pb.precond == "none":
         return W.copy()
+    ax = (-3, -2, -1) if pb.nz > 1 else (-2, -1)
     if pb.bc == "periodic":
-        return np.real(np.fft.ifft2(np.fft.fft2(W, axes=(-2, -1)) / g, axes=(-2, -1)))
-    Wh = sfft.dctn(W, type=2, axes=(-2, -1), norm="ortho")
-    return sfft.idctn(Wh / g, type=2, axes=(-2, -1), norm="ortho")
+        return np.real(np.fft.ifftn(np.fft.fftn(W, axes=ax) / g, axes=ax))
+    Wh = sfft.dctn(W, type=2, axes=ax, norm="ortho")
+    return sfft.idctn(Wh / g, type=2, axes=ax, norm="ortho")
 
 
 def measure(pb, W, Uk):
@@ -288,7 +305,8 @@ def solve(pb, u0, nsteps, history=False):
 
 def mass(pb, U):
     hx, hy = spacing(pb)
-    return hx * hy * float(np.sum(U))
+    hz = spacing_z(pb) if pb.nz > 1 else 1.0
+    return hx * hy * hz * float(np.sum(U))
 
 
 def ac_energy(pb, U):

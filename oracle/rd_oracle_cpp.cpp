@@ -60,6 +60,8 @@ typedef struct {
   double tol;
   int tol_kind;
   int max_iter;
+  int nz;              // points along z of a 3-D grid (1: a 2-D grid)
+  double lz;           // side length along z; h_z = lz / nz
 } rdo_problem;
 
 }  // extern "C"
@@ -80,18 +82,29 @@ inline int nb(int i, int s, int n, int bc) {
   return j < 0 ? 0 : n - 1;  // half-cell mirror: U_{-1} = U_0, U_n = U_{n-1}
 }
 
-// out = Lap x on one component (ny * nx values)
+int nzof(const rdo_problem& pb) { return pb.nz > 1 ? pb.nz : 1; }
+size_t npts_of(const rdo_problem& pb) { return (size_t)pb.nx * pb.ny * nzof(pb); }
+
+// out = Lap x on one component (nz * ny * nx values): the five-point Laplacian on each plane,
+// plus the second difference along z on 3-D grids (seven points)
 void lap(const rdo_problem& pb, const double* x, double* out) {
-  const int nx = pb.nx, ny = pb.ny;
+  const int nx = pb.nx, ny = pb.ny, nz = nzof(pb);
   const double hx2 = 1.0 / ((pb.lx / nx) * (pb.lx / nx)), hy2 = 1.0 / ((pb.ly / ny) * (pb.ly / ny));
+  const double hz2 = nz > 1 ? 1.0 / ((pb.lz / nz) * (pb.lz / nz)) : 0.0;
+  const size_t plane = (size_t)nx * ny;
 #pragma omp parallel for schedule(static)
-  for (int i = 0; i < ny; ++i) {
+  for (int r = 0; r < nz * ny; ++r) {
+    const int l = r / ny, i = r - l * ny;
     const int im = nb(i, -1, ny, pb.bc), ip = nb(i, 1, ny, pb.bc);
+    const int lm = nz > 1 ? nb(l, -1, nz, pb.bc) : l, lp = nz > 1 ? nb(l, 1, nz, pb.bc) : l;
+    const double* xp = x + l * plane;
     for (int j = 0; j < nx; ++j) {
       const int jm = nb(j, -1, nx, pb.bc), jp = nb(j, 1, nx, pb.bc);
-      const double c = x[(size_t)i * nx + j];
-      out[(size_t)i * nx + j] = (x[(size_t)i * nx + jp] + x[(size_t)i * nx + jm] - 2.0 * c) * hx2 +
-                                (x[(size_t)ip * nx + j] + x[(size_t)im * nx + j] - 2.0 * c) * hy2;
+      const double c = xp[(size_t)i * nx + j];
+      double v = (xp[(size_t)i * nx + jp] + xp[(size_t)i * nx + jm] - 2.0 * c) * hx2 +
+                 (xp[(size_t)ip * nx + j] + xp[(size_t)im * nx + j] - 2.0 * c) * hy2;
+      if (nz > 1) v += (x[lp * plane + (size_t)i * nx + j] + x[lm * plane + (size_t)i * nx + j] - 2.0 * c) * hz2;
+      out[l * plane + (size_t)i * nx + j] = v;
     }
   }
 }
@@ -99,7 +112,7 @@ void lap(const rdo_problem& pb, const double* x, double* out) {
 using vec = std::vector<double>;
 
 vec lapv(const rdo_problem& pb, const double* x) {
-  vec o((size_t)pb.nx * pb.ny);
+  vec o(npts_of(pb));
   lap(pb, x, o.data());
   return o;
 }
@@ -110,14 +123,14 @@ vec lapv(const rdo_problem& pb, const double* x) {
 
 // Sixth-order equation (Section 3.3): mu(U) = a Lap U - b W'(U), A(U) x = a Lap x - b W''(U) x + a x
 vec fch_mu(const rdo_problem& pb, const double* U) {
-  const size_t n = (size_t)pb.nx * pb.ny;
+  const size_t n = npts_of(pb);
   vec L = lapv(pb, U), m(n);
   for (size_t q = 0; q < n; ++q) m[q] = pb.a * L[q] - pb.b * (U[q] * U[q] * U[q] - U[q]);
   return m;
 }
 
 vec fch_A(const rdo_problem& pb, const double* U, const double* x) {
-  const size_t n = (size_t)pb.nx * pb.ny;
+  const size_t n = npts_of(pb);
   vec L = lapv(pb, x), o(n);
   for (size_t q = 0; q < n; ++q) o[q] = pb.a * L[q] - pb.b * (3.0 * U[q] * U[q] - 1.0) * x[q] + pb.a * x[q];
   return o;
@@ -125,7 +138,7 @@ vec fch_A(const rdo_problem& pb, const double* U, const double* x) {
 
 // W = F(U) for U^k = Uk; arrays component-major [ncomp][ny][nx]
 void residual(const rdo_problem& pb, const double* U, const double* Uk, double* W) {
-  const size_t n = (size_t)pb.nx * pb.ny;
+  const size_t n = npts_of(pb);
   const double dt = pb.dt, a = pb.a, b = pb.b;
   switch (pb.kind) {
     case K_NONE: {
@@ -196,7 +209,7 @@ void residual(const rdo_problem& pb, const double* U, const double* Uk, double* 
 
 // g = dF(U)^T Pt (the derivative taken at the current iterate U_n)
 void grad_F_T(const rdo_problem& pb, const double* U, const double* Pt, double* g) {
-  const size_t n = (size_t)pb.nx * pb.ny;
+  const size_t n = npts_of(pb);
   const double dt = pb.dt, a = pb.a, b = pb.b;
   switch (pb.kind) {
     case K_NONE: {
@@ -317,25 +330,33 @@ void dct3(const double* X, double* x, int n, std::vector<cplx>& buf) {
   for (int j = 0; j < n; ++j) x[j] = 0.5 * buf[j].real();
 }
 
-// eigenvalues mu >= 0 of -Lap on the transform grid (row-major [ny][nx]):
-//   periodic  4/h_x^2 sin^2(pi kx / nx) + 4/h_y^2 sin^2(pi ky / ny)         (Fourier modes)
-//   Neumann   4/h_x^2 sin^2(pi kx / 2nx) + 4/h_y^2 sin^2(pi ky / 2ny)       (DCT-II modes)
+// eigenvalues mu >= 0 of -Lap on the transform grid (row-major [nz][ny][nx]):
+//   periodic  4/h_x^2 sin^2(pi kx / nx) + 4/h_y^2 sin^2(pi ky / ny) [+ 4/h_z^2 sin^2(pi kz / nz)]
+//   Neumann   4/h_x^2 sin^2(pi kx / 2nx) + 4/h_y^2 sin^2(pi ky / 2ny) [+ 4/h_z^2 sin^2(pi kz / 2nz)]
+// (Fourier modes, resp. DCT-II modes; the z term on 3-D grids only)
 vec symbol_mu(const rdo_problem& pb) {
-  const int nx = pb.nx, ny = pb.ny;
+  const int nx = pb.nx, ny = pb.ny, nz = nzof(pb);
   const double hx = pb.lx / nx, hy = pb.ly / ny, d = pb.bc == BC_PERIODIC ? 1.0 : 2.0;
-  vec mu((size_t)nx * ny);
-  for (int i = 0; i < ny; ++i)
-    for (int j = 0; j < nx; ++j) {
-      const double sx = std::sin(kPi * j / (d * nx)), sy = std::sin(kPi * i / (d * ny));
-      mu[(size_t)i * nx + j] = 4.0 / (hx * hx) * sx * sx + 4.0 / (hy * hy) * sy * sy;
-    }
+  const double hz = nz > 1 ? pb.lz / nz : 1.0;
+  vec mu(npts_of(pb));
+  for (int l = 0; l < nz; ++l)
+    for (int i = 0; i < ny; ++i)
+      for (int j = 0; j < nx; ++j) {
+        const double sx = std::sin(kPi * j / (d * nx)), sy = std::sin(kPi * i / (d * ny));
+        double m = 4.0 / (hx * hx) * sx * sx + 4.0 / (hy * hy) * sy * sy;
+        if (nz > 1) {
+          const double sz = std::sin(kPi * l / (d * nz));
+          m += 4.0 / (hz * hz) * sz * sz;
+        }
+        mu[((size_t)l * ny + i) * nx + j] = m;
+      }
   return mu;
 }
 
 // eigenvalues of G = A_lin^2 per component
 vec ghat(const rdo_problem& pb) {
   const int nc = ncomp_of(pb);
-  const size_t n = (size_t)pb.nx * pb.ny;
+  const size_t n = npts_of(pb);
   vec g(nc * n, 1.0);
   if (pb.precond == PC_NONE) return g;
   vec mu = symbol_mu(pb);
@@ -353,56 +374,63 @@ vec ghat(const rdo_problem& pb) {
   return g;
 }
 
-// Y = G^{-1} W on one component: 2-D FFT (periodic) or 2-D orthonormal DCT-II (Neumann), divide
-// by g, inverse transform
+// Apply fn(line) to every line of length len and element stride `stride` of an array of n
+// values (the lines along one axis); fn gets the line's first index.
+template <class Fn>
+void for_lines(size_t n, int len, size_t stride, Fn fn) {
+  const size_t block = (size_t)len * stride, nlines = n / len;
+#pragma omp parallel for schedule(static)
+  for (long long m = 0; m < (long long)nlines; ++m) {
+    const size_t outer = (size_t)m / stride, inner = (size_t)m % stride;
+    fn(outer * block + inner);
+  }
+}
+
+// Y = G^{-1} W on one component: FFT along every axis (periodic) or orthonormal DCT-II along every
+// axis (Neumann), divide by g, inverse transforms
 void ginv_component(const rdo_problem& pb, const double* W, const double* g, double* Y) {
-  const int nx = pb.nx, ny = pb.ny;
-  const size_t n = (size_t)nx * ny;
+  const int nx = pb.nx, ny = pb.ny, nz = nzof(pb);
+  const size_t n = npts_of(pb);
+  const int len[3] = {nx, ny, nz};
+  const size_t str[3] = {1, (size_t)nx, (size_t)nx * ny};
+  const int naxes = nz > 1 ? 3 : 2;
   if (pb.bc == BC_PERIODIC) {
     std::vector<cplx> z(n);
     for (size_t q = 0; q < n; ++q) z[q] = W[q];
-#pragma omp parallel
-    {
-      std::vector<cplx> col(ny);
-#pragma omp for schedule(static)
-      for (int i = 0; i < ny; ++i) fft(z.data() + (size_t)i * nx, nx, -1);
-#pragma omp for schedule(static)
-      for (int j = 0; j < nx; ++j) {
-        for (int i = 0; i < ny; ++i) col[i] = z[(size_t)i * nx + j];
-        fft(col.data(), ny, -1);
-        for (int i = 0; i < ny; ++i) col[i] /= g[(size_t)i * nx + j];
-        fft(col.data(), ny, +1);
-        for (int i = 0; i < ny; ++i) z[(size_t)i * nx + j] = col[i];
-      }
-#pragma omp for schedule(static)
-      for (int i = 0; i < ny; ++i) fft(z.data() + (size_t)i * nx, nx, +1);
-    }
+    auto pass = [&](int ax, int sgn) {
+      for_lines(n, len[ax], str[ax], [&](size_t q0) {
+        std::vector<cplx> line(len[ax]);
+        for (int t = 0; t < len[ax]; ++t) line[t] = z[q0 + t * str[ax]];
+        fft(line.data(), len[ax], sgn);
+        for (int t = 0; t < len[ax]; ++t) z[q0 + t * str[ax]] = line[t];
+      });
+    };
+    for (int ax = 0; ax < naxes; ++ax) pass(ax, -1);
+    for (size_t q = 0; q < n; ++q) z[q] /= g[q];
+    for (int ax = naxes - 1; ax >= 0; --ax) pass(ax, +1);
     for (size_t q = 0; q < n; ++q) Y[q] = z[q].real() / (double)n;
     return;
   }
-  vec t(n);
-#pragma omp parallel
-  {
-    std::vector<cplx> buf;
-    vec a(std::max(nx, ny)), b(std::max(nx, ny));
-#pragma omp for schedule(static)
-    for (int i = 0; i < ny; ++i) dct2(W + (size_t)i * nx, t.data() + (size_t)i * nx, nx, buf);
-#pragma omp for schedule(static)
-    for (int j = 0; j < nx; ++j) {
-      for (int i = 0; i < ny; ++i) a[i] = t[(size_t)i * nx + j];
-      dct2(a.data(), b.data(), ny, buf);
-      for (int i = 0; i < ny; ++i) b[i] /= g[(size_t)i * nx + j];
-      dct3(b.data(), a.data(), ny, buf);
-      for (int i = 0; i < ny; ++i) t[(size_t)i * nx + j] = a[i];
-    }
-#pragma omp for schedule(static)
-    for (int i = 0; i < ny; ++i) dct3(t.data() + (size_t)i * nx, Y + (size_t)i * nx, nx, buf);
-  }
+  vec t(W, W + n);
+  auto pass = [&](int ax, bool fwd) {
+    for_lines(n, len[ax], str[ax], [&](size_t q0) {
+      std::vector<cplx> buf;
+      vec a(len[ax]), b(len[ax]);
+      for (int k = 0; k < len[ax]; ++k) a[k] = t[q0 + k * str[ax]];
+      if (fwd) dct2(a.data(), b.data(), len[ax], buf);
+      else dct3(a.data(), b.data(), len[ax], buf);
+      for (int k = 0; k < len[ax]; ++k) t[q0 + k * str[ax]] = b[k];
+    });
+  };
+  for (int ax = 0; ax < naxes; ++ax) pass(ax, true);
+  for (size_t q = 0; q < n; ++q) t[q] /= g[q];
+  for (int ax = naxes - 1; ax >= 0; --ax) pass(ax, false);
+  std::memcpy(Y, t.data(), n * sizeof(double));
 }
 
 void apply_ginv(const rdo_problem& pb, const double* W, const vec& g, double* Y) {
   const int nc = ncomp_of(pb);
-  const size_t n = (size_t)pb.nx * pb.ny;
+  const size_t n = npts_of(pb);
   if (pb.precond == PC_NONE) {
     std::memcpy(Y, W, nc * n * sizeof(double));
     return;
@@ -412,16 +440,16 @@ void apply_ginv(const rdo_problem& pb, const double* W, const vec& g, double* Y)
 
 // sum of squares of one component, as row partials summed in row order
 double sumsq(const rdo_problem& pb, const double* x) {
-  const int nx = pb.nx, ny = pb.ny;
-  vec rows(ny);
+  const int nx = pb.nx, nrows = pb.ny * nzof(pb);
+  vec rows(nrows);
 #pragma omp parallel for schedule(static)
-  for (int i = 0; i < ny; ++i) {
+  for (int i = 0; i < nrows; ++i) {
     double s = 0.0;
     for (int j = 0; j < nx; ++j) s += x[(size_t)i * nx + j] * x[(size_t)i * nx + j];
     rows[i] = s;
   }
   double s = 0.0;
-  for (int i = 0; i < ny; ++i) s += rows[i];
+  for (int i = 0; i < nrows; ++i) s += rows[i];
   return s;
 }
 
@@ -429,7 +457,7 @@ double sumsq(const rdo_problem& pb, const double* x) {
 // threshold (delta, or tol ||U^k||_2)
 void measure(const rdo_problem& pb, const double* W, const double* Uk, double* r, double* thr) {
   const int nc = ncomp_of(pb);
-  const size_t n = (size_t)pb.nx * pb.ny;
+  const size_t n = npts_of(pb);
   double s = 0.0, uk2 = 0.0;
   for (int c = 0; c < nc; ++c) {
     s += std::sqrt(sumsq(pb, W + c * n));
@@ -492,7 +520,7 @@ void rdo_dct3(const double* X, double* x, int n) {
 void rdo_pdhg_step(const rdo_problem* pbp, const double* Uk, double* U, int* iterations, int* status,
                    double* residual_out, double* history, int hist_cap) {
   const rdo_problem& pb = *pbp;
-  const size_t N = (size_t)ncomp_of(pb) * pb.nx * pb.ny;
+  const size_t N = (size_t)ncomp_of(pb) * npts_of(pb);
   std::memcpy(U, Uk, N * sizeof(double));                 // U_0 = U^k
   vec P(N, 0.0), W(N), Y(N), Pt(N), g(N);                 // P_0 = 0
   const vec gh = ghat(pb);

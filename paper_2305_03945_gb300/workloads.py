@@ -51,6 +51,9 @@ class Problem:
     tol, tol_kind   'res_abs': stop when sum_c ||F_c(U)||_2 / dt <= tol   (Section 2.1 stopping rule)
                     'f_rel'  : stop when sum_c ||F_c(U)||_2 <= tol * ||U^k||_2
     max_iter        cap on PDHG iterations per time step
+    nz, lz          points and side length along z of a 3-D grid (nz = 1: a 2-D grid); the
+                    3-D problem is the paper's scheme with a third axis (7-point Laplacian,
+                    separable 3-D transforms)
     """
 
     nx: int
@@ -71,13 +74,26 @@ class Problem:
     tol: float = 1e-10
     tol_kind: str = "res_abs"
     max_iter: int = 10000
+    nz: int = 1
+    lz: float = 1.0
 
     @property
     def ncomp(self) -> int:
         return 2 if self.kind in TWO_SPECIES else 1
 
     @property
+    def ndim(self) -> int:
+        return 3 if self.nz > 1 else 2
+
+    @property
+    def npoints(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
     def shape(self) -> tuple:
+        """[ncomp, ny, nx] on 2-D grids, [ncomp, nz, ny, nx] on 3-D grids (x fastest)."""
+        if self.nz > 1:
+            return (self.ncomp, self.nz, self.ny, self.nx)
         return (self.ncomp, self.ny, self.nx)
 
     def replace(self, **kw) -> "Problem":
