@@ -45,7 +45,7 @@ extern "C" {
 typedef enum {
     RD_OK = 0,
     RD_ERR_INVALID_ARG = 1,    /* a NULL handle/pointer, n < 2, dt <= 0, tau <= 0, a < 0, ...   */
-    RD_ERR_UNSUPPORTED = 2,    /* valid but not built: e.g. non-power-of-two n, 3-D grids        */
+    RD_ERR_UNSUPPORTED = 2,    /* valid but not built: e.g. non-power-of-two n, 3-D two species  */
     RD_ERR_OOM = 3,            /* cudaMalloc failed                                              */
     RD_ERR_CUDA = 4,           /* another CUDA runtime error (detail in rd_last_error)           */
     RD_ERR_NOT_CONVERGED = 5,  /* max_iter PDHG updates did not meet the stopping rule           */
@@ -92,10 +92,16 @@ typedef enum {
     RD_RX_FCH = 6
 } rd_reaction_kind;
 
+/* Grid.  2-D: sides nx, ny.  3-D (ndim = 3, not in the paper, which is 2-D: its scheme with a
+ * third axis -- seven-point Laplacian, Lap^2 as its square, transforms along x, y and z; scalar
+ * kinds RD_RX_NONE, Allen-Cahn and both Cahn-Hilliard forms; arrays [ncomp][nz][ny][nx]).
+ * Every side is a power of two, at least 2 and at most 2048 for RD_PREC_FP32_DC, 4096 for
+ * RD_PREC_FP64 on 2-D grids (one row or column is transformed by one thread block), at most
+ * 2048 on 3-D grids; longer sides return RD_ERR_UNSUPPORTED. */
 typedef struct {
-    int ndim;            /* 2 (3-D grids return RD_ERR_UNSUPPORTED)                            */
-    int n[3];            /* n[0] = nx (contiguous), n[1] = ny; powers of two, 2 <= n <= 8192   */
-    double length[3];    /* side lengths; h_x = length[0]/nx, h_y = length[1]/ny               */
+    int ndim;            /* 2 or 3                                                             */
+    int n[3];            /* n[0] = nx (contiguous), n[1] = ny, n[2] = nz (3-D)                 */
+    double length[3];    /* side lengths; h_x = length[0]/nx, h_y = length[1]/ny, h_z = length[2]/nz */
 } rd_grid;
 
 typedef struct {

@@ -11,6 +11,7 @@
 #include "../../include/rd_pdhg.h"
 #include "rd_device.cuh"
 #include "rd_launch.h"
+#include "rd_launch3.h"
 
 using namespace rd;
 
@@ -186,7 +187,10 @@ void rd::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
 struct rd_pdhg {
   int nx = 0, ny = 0, nc = 1;
-  size_t npts = 0;  // nc * nx * ny
+  int nz = 1;       // 3-D grids: points along z (1 on a 2-D grid)
+  int nd3 = 0;      // 1: a 3-D grid (the rd_3d.cu kernels)
+  double hz = 0;
+  size_t npts = 0;  // nc * nx * ny * nz
   int bc = 0, op = 0, kind = 0, precond = 1;
   double dt = 0, tau = 0, sigma = 0, hx = 0, hy = 0;
   rd_reaction rx{};
@@ -202,6 +206,10 @@ struct rd_pdhg {
   double* WY64 = nullptr;
   double* mu64[2] = {nullptr, nullptr};  // mu_x, mu_y
   cx<double>* tw64[4] = {nullptr, nullptr, nullptr, nullptr};  // twx, twy, dcx, dcy
+  double* mu64z = nullptr;                                     // 3-D: mu_z, twz, dcz
+  cx<double>* tw64z[2] = {nullptr, nullptr};
+  float* mu32z = nullptr;
+  cx<float>* tw32z[2] = {nullptr, nullptr};
   // FP32 defect-correction workspaces
   float* D32 = nullptr;
   float* P32[2] = {nullptr, nullptr};
@@ -291,6 +299,17 @@ void host_mu(const rd_pdhg* h, std::vector<double>& mx, std::vector<double>& my)
   }
 }
 
+// mu_z(k) of a 3-D grid, the same formula along z
+void host_mu_z(const rd_pdhg* h, std::vector<double>& mz) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double dd = h->bc == RD_BC_PERIODIC ? 1.0L : 2.0L;
+  mz.resize(h->nz);
+  for (int k = 0; k < h->nz; ++k) {
+    const long double sn = sinl(pi * k / (dd * h->nz));
+    mz[k] = (double)(4.0L / ((long double)h->hz * h->hz) * sn * sn);
+  }
+}
+
 void symbol_coefficients(const rd_pdhg* h, Desc& d) {
   for (int c = 0; c < 2; ++c) {
     double D = h->rx.a;
@@ -309,7 +328,7 @@ void symbol_coefficients(const rd_pdhg* h, Desc& d) {
       d.gc2[c] = h->rx.a * h->dt;
     }
   }
-  d.inv_nn = 1.0 / ((double)h->nx * (double)h->ny);
+  d.inv_nn = 1.0 / ((double)h->nx * (double)h->ny * (double)h->nz);
 }
 
 rd_status status_of(int st) {
@@ -337,10 +356,28 @@ cudaError_t fch_iteration(rd_pdhg* h, cudaStream_t s, cudaEvent_t* ev) {
 // k_loop_cond, run after iteration 1 and at the end of every trip, clears it once the solve has
 // ended (or after max_iter + slack k_res launches).  k_axpy_dc, the second k_resid64 and
 // k_mass act only while (resp. once no longer) the outer loop is active.
+// Step-level launches of either grid kind: the step set-up and the FP64 residual.
+cudaError_t begin_any(rd_pdhg* h, State* st, const double* uk, double tol, int tol_kind, int nb, cudaStream_t s) {
+  if (h->nd3) return launch_begin3(h->h_desc[0], h->d_desc + 0, st, uk, h->rhs64, tol, tol_kind, s);
+  return launch_begin(h->d_desc + 0, st, uk, h->rhs64, tol, tol_kind, nb, s);
+}
+
+cudaError_t resid64_any(rd_pdhg* h, State* outer, State* inner, const double* u, double* w64, float* r32, float* u32,
+                        float* z0, float* z1, int decide, int nb, cudaStream_t s) {
+  if (h->nd3)
+    return launch_resid64_3(h->h_desc[0], h->d_desc + 0, outer, inner, u, h->rhs64, w64, r32, u32, z0, z1, decide,
+                            h->opts.dc_inner_rtol, h->opts.dc_max_outer, s);
+  return launch_resid64(h->h_desc[0], h->d_desc + 0, outer, inner, u, h->rhs64, w64, r32, u32, z0, z1, decide,
+                        h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, s);
+}
+
+// Blocks of the step-level kernels (k_begin, k_resid64, k_mass: two points per thread).
+int step_blocks(const rd_pdhg* h) { return point_blocks(h->nx, h->ny * h->nz); }
+
 rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraphExec_t* exec) {
   const int K = h->opts.graph_k;
   cudaStream_t cs = h->cap_stream;
-  const int nb = point_blocks(h->nx, h->ny);
+  const int nb = step_blocks(h);
   const Desc* d64 = h->d_desc + 0;
   State* st0 = h->d_state + 0;
   State* st1 = h->d_state + 1;
@@ -353,6 +390,7 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   const Desc dd = h->dc ? h->h_desc[1] : h->h_desc[0];
   auto iteration = [&](cudaStream_t st, cudaEvent_t* ev, bool first_it) {
     if (h->fch) return fch_iteration(h, st, ev);
+    if (h->nd3) return h->dc ? launch_iteration3<float>(dd, sti, st, ev) : launch_iteration3<double>(dd, sti, st, ev);
     if (h->dc && dd.fused) return launch_fused<float>(dd, sti, h->cfg32, st, ev, first_it);
     return h->dc ? launch_iteration<float>(dd, sti, h->cfg32, st, ev) : launch_iteration<double>(dd, sti, h->cfg64, st, ev);
   };
@@ -365,11 +403,9 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   RD_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   if (first) {
-    e = launch_begin(d64, st0, h->U64, h->rhs64, h->opts.tol, h->opts.tol_kind, nb, cs);
+    e = begin_any(h, st0, h->U64, h->opts.tol, h->opts.tol_kind, nb, cs);
     if (e == cudaSuccess && !h->dc) e = cudaMemsetAsync(h->P64[0], 0, h->npts * sizeof(double), cs);
-    if (e == cudaSuccess && h->dc)
-      e = launch_resid64(h->h_desc[0], d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1,
-                         h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, cs);
+    if (e == cudaSuccess && h->dc) e = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, cs);
     if (e != cudaSuccess) return abort_capture(cs, "step set-up during capture", e);
   }
   // fused update: the per-band halo copies of U start at U_0 = d = 0
@@ -410,9 +446,7 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
     return abort_capture(cs, "ending the loop body capture", e);
   if (h->dc) {
     e = launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, cs);
-    if (e == cudaSuccess)
-      e = launch_resid64(h->h_desc[0], d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1,
-                         h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, cs);
+    if (e == cudaSuccess) e = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, cs);
     if (e == cudaSuccess) e = launch_mass(d64, h->d_state + 2, h->U64, st0, nb, cs);
   } else {
     e = launch_mass(d64, h->d_state + 2, h->U64, nullptr, nb, cs);
@@ -438,6 +472,8 @@ rd_status capture_iter_graph(rd_pdhg* h, bool start, cudaGraph_t* graph, cudaGra
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
     cudaEvent_t* ev = (k == 0 && h->opts.profile && (start || !fused)) ? h->ev : nullptr;
     if (h->fch) e = fch_iteration(h, cs, ev);
+    else if (h->nd3) e = h->dc ? launch_iteration3<float>(dd, h->d_state + 1, cs, ev)
+                               : launch_iteration3<double>(dd, h->d_state + 0, cs, ev);
     else if (fused) e = launch_fused<float>(dd, h->d_state + 1, h->cfg32, cs, ev, start && k == 0);
     else if (h->dc) e = launch_iteration<float>(dd, h->d_state + 1, h->cfg32, cs, ev);
     else e = launch_iteration<double>(dd, h->d_state + 0, h->cfg64, cs, ev);
@@ -455,7 +491,9 @@ rd_status capture_iter_graph(rd_pdhg* h, bool start, cudaGraph_t* graph, cudaGra
 
 rd_status capture_graphs(rd_pdhg* h) {
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
-  h->kernels_per_iter = h->fch ? (lc.transform ? 10 : 7) : (h->dc && h->h_desc[1].fused ? 2 : (lc.transform ? 3 : 2));
+  h->kernels_per_iter = h->fch ? (lc.transform ? 10 : 7)
+                    : h->nd3 ? (lc.transform ? 7 : 2)
+                             : (h->dc && h->h_desc[1].fused ? 2 : (lc.transform ? 3 : 2));
   if (h->opts.profile)
     for (int i = 0; i < 4; ++i)
       if (!h->ev[i]) RD_CUDA(cudaEventCreate(&h->ev[i]));
@@ -504,9 +542,13 @@ rd_status set_dt_impl(rd_pdhg* h, double dt) {
 rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* rx, double dt, double tau,
                    double sigma, const rd_precond* pc, const rd_opts* o) {
   if (!grid || !rx) return fail(RD_ERR_INVALID_ARG, "grid and reaction must not be NULL");
-  if (grid->ndim == 3) return fail(RD_ERR_UNSUPPORTED, "3-D grids are not built");
-  if (grid->ndim != 2) return fail(RD_ERR_INVALID_ARG, "ndim must be 2");
-  for (int k = 0; k < 2; ++k) {
+  if (grid->ndim != 2 && grid->ndim != 3) return fail(RD_ERR_INVALID_ARG, "ndim must be 2 or 3");
+  if (grid->ndim == 3) {
+    if (rx->kind != RD_RX_NONE && rx->kind != RD_RX_ALLEN_CAHN && rx->kind != RD_RX_CH_IMPLICIT &&
+        rx->kind != RD_RX_CH_SPLIT)
+      return fail(RD_ERR_UNSUPPORTED, "3-D grids are built for the scalar kinds (none, Allen-Cahn, Cahn-Hilliard)");
+  }
+  for (int k = 0; k < grid->ndim; ++k) {
     if (grid->n[k] < 2) return fail(RD_ERR_INVALID_ARG, "grid sides need n >= 2");
     if (!pow2(grid->n[k])) return fail(RD_ERR_UNSUPPORTED, "grid sides must be powers of two");
     if (!(grid->length[k] > 0) || !std::isfinite(grid->length[k])) return fail(RD_ERR_INVALID_ARG, "lengths must be > 0");
@@ -745,8 +787,10 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
                       double tau, double sigma, const rd_precond* pc, const rd_opts* o, void* stream) {
   h->nx = grid->n[0];
   h->ny = grid->n[1];
+  h->nd3 = grid->ndim == 3;
+  h->nz = h->nd3 ? grid->n[2] : 1;
   h->nc = rx->ncomp;
-  h->npts = (size_t)h->nc * h->nx * h->ny;
+  h->npts = (size_t)h->nc * h->nx * h->ny * h->nz;
   h->bc = bc;
   h->op = op;
   h->kind = rx->kind;
@@ -757,6 +801,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   h->sigma = sigma;
   h->hx = grid->length[0] / h->nx;
   h->hy = grid->length[1] / h->ny;
+  h->hz = h->nd3 ? grid->length[2] / h->nz : 1.0;
   if (o) h->opts = *o; else rd_opts_default(&h->opts);
   h->dc = h->opts.precision == RD_PREC_FP32_DC;
   h->stream = static_cast<cudaStream_t>(stream);
@@ -786,13 +831,25 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   base.tau_u = tau;
   base.tau_p = sigma;
   base.omega = h->opts.omega;
+  base.nz = h->nz;
+  base.lognz = ilog2(h->nz);
+  base.hz2 = h->nd3 ? 1.0 / (h->hz * h->hz) : 0.0;
 
   std::string why;
   Desc d64 = base, d32 = base;
-  if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, bc == RD_BC_NEUMANN, h->opts.band_rows, h->opts.col_width,
+  if (h->nd3) {
+    // 3-D grids: the rd_3d.cu kernels with their own plan (no band / column tiles, no autotuner,
+    // no fused update)
+    const char* w3 = nullptr;
+    if (!plan3(h->nx, h->ny, h->nz, h->nc, 8, bc == RD_BC_NEUMANN, kSmemLimit, d64, &w3))
+      return fail(RD_ERR_UNSUPPORTED, std::string("FP64 path: ") + w3);
+    if (h->dc && !plan3(h->nx, h->ny, h->nz, h->nc, 4, bc == RD_BC_NEUMANN, kSmemLimit, d32, &w3))
+      return fail(RD_ERR_UNSUPPORTED, std::string("FP32 path: ") + w3);
+    h->cfg64.transform = h->cfg32.transform = transform;
+  } else if (!plan_launch<double>(h->nx, h->ny, h->nc, H, transform, bc == RD_BC_NEUMANN, h->opts.band_rows, h->opts.col_width,
                            h->opts.upd_rows, 0, h->opts.fft_buffers, h->opts.fft_unrolled, d64, h->cfg64, why))
     if (!h->dc) return fail(RD_ERR_UNSUPPORTED, "FP64 path: " + why);
-  if (h->dc) {
+  if (h->dc && !h->nd3) {
     // the FP64 kernels of the defect-correction loop only need the band decomposition
     if (!plan_launch<float>(h->nx, h->ny, h->nc, H, transform, bc == RD_BC_NEUMANN, h->opts.band_rows, h->opts.col_width,
                            h->opts.upd_rows, rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT, h->opts.fft_buffers, h->opts.fft_unrolled, d32, h->cfg32, why))
@@ -811,7 +868,9 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   const int nb = std::max(d64.nbands, d32.nbands);
   // partials: per band (any band height the autotuner may try) or per step-kernel block
   const int nb_any = std::max(nb, h->ny / 2 + 1);
-  RD_TRY(dalloc(h, &h->partials, (size_t)2 * std::max(std::max(nb_any, point_blocks(h->nx, h->ny)), 1) * sizeof(double)));
+  const int nb3 = h->nd3 ? std::max(std::max(d64.blk3, d32.blk3), point_blocks(h->nx, h->ny * h->nz)) : 0;
+  RD_TRY(dalloc(h, &h->partials,
+                (size_t)2 * std::max(std::max(std::max(nb_any, point_blocks(h->nx, h->ny)), nb3), 1) * sizeof(double)));
   RD_TRY(dalloc(h, &h->d_desc, 3 * sizeof(Desc)));
   RD_TRY(dalloc(h, &h->d_state, 3 * sizeof(State)));
   if (h->fch) {
@@ -822,10 +881,14 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   }
   RD_CUDA(cudaMallocHost(&h->h_state, 3 * sizeof(State)));
 
-  std::vector<double> twx, dcx, twy, dcy, mx, my;
+  std::vector<double> twx, dcx, twy, dcy, mx, my, twz, dcz, mz;
   host_twiddles(h->nx, twx, dcx);
   host_twiddles(h->ny, twy, dcy);
   host_mu(h, mx, my);
+  if (h->nd3) {
+    host_twiddles(h->nz, twz, dcz);
+    host_mu_z(h, mz);
+  }
 
   if (!h->dc) {
     RD_TRY(dalloc(h, &h->P64[0], n * sizeof(double)));
@@ -843,6 +906,14 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
     RD_TRY(dalloc(h, &h->mu64[1], (size_t)h->ny * sizeof(double)));
     RD_CUDA(cudaMemcpy(h->mu64[0], mx.data(), mx.size() * sizeof(double), cudaMemcpyHostToDevice));
     RD_CUDA(cudaMemcpy(h->mu64[1], my.data(), my.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (h->nd3) {
+      RD_TRY(dalloc(h, &h->tw64z[0], (size_t)h->nz * sizeof(cx<double>)));
+      RD_TRY(dalloc(h, &h->tw64z[1], (size_t)h->nz * sizeof(cx<double>)));
+      RD_TRY(dalloc(h, &h->mu64z, (size_t)h->nz * sizeof(double)));
+      RD_CUDA(cudaMemcpy(h->tw64z[0], twz.data(), twz.size() * sizeof(double), cudaMemcpyHostToDevice));
+      RD_CUDA(cudaMemcpy(h->tw64z[1], dcz.data(), dcz.size() * sizeof(double), cudaMemcpyHostToDevice));
+      RD_CUDA(cudaMemcpy(h->mu64z, mz.data(), mz.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
   } else {
     RD_TRY(dalloc(h, &h->D32, n * sizeof(float)));
     RD_TRY(dalloc(h, &h->P32[0], n * sizeof(float)));
@@ -867,6 +938,13 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
     RD_CUDA(cudaMemcpy(h->mu32[0], f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
     f.assign(my.begin(), my.end());
     RD_CUDA(cudaMemcpy(h->mu32[1], f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (h->nd3) {
+      RD_TRY(up32(&h->tw32z[0], twz, h->nz));
+      RD_TRY(up32(&h->tw32z[1], dcz, h->nz));
+      RD_TRY(dalloc(h, &h->mu32z, (size_t)h->nz * sizeof(float)));
+      f.assign(mz.begin(), mz.end());
+      RD_CUDA(cudaMemcpy(h->mu32z, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
   }
 
   // descriptors
@@ -887,6 +965,9 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   d64.twy = h->tw64[1];
   d64.dcx = h->tw64[2];
   d64.dcy = h->tw64[3];
+  d64.muz = h->mu64z;
+  d64.twz = h->tw64z[0];
+  d64.dcz = h->tw64z[1];
   d64.partials = h->partials;
 
   d32.dc = 1;
@@ -907,6 +988,9 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   d32.twy = h->tw32[1];
   d32.dcx = h->tw32[2];
   d32.dcy = h->tw32[3];
+  d32.muz = h->mu32z;
+  d32.twz = h->tw32z[0];
+  d32.dcz = h->tw32z[1];
   d32.partials = h->partials;
 
   Desc dpc = d64;
@@ -927,15 +1011,22 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   int usable = 0;
   if (h->dc) RD_CUDA(set_kernel_smem_limits<float>(&usable));
   else RD_CUDA(set_kernel_smem_limits<double>(&usable));
+  if (h->nd3) {
+    int dev = 0, optin = 0;
+    RD_CUDA(cudaGetDevice(&dev));
+    RD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    RD_CUDA(h->dc ? allow3<float>(optin) : allow3<double>(optin));
+    RD_CUDA(allow3<double>(optin));  // the preconditioner-only solve of rd_pdhg_apply_precond
+  }
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
   if (std::max(lc.smem_res, std::max(lc.smem_col, lc.smem_upd)) > usable)
     return fail(RD_ERR_UNSUPPORTED, "the grid needs more shared memory per block than this device offers");
-  if (h->opts.autotune && !h->fch && h->opts.band_rows == 0 && h->opts.col_width == 0 && h->opts.upd_rows == 0) {
+  if (h->opts.autotune && !h->fch && !h->nd3 && h->opts.band_rows == 0 && h->opts.col_width == 0 && h->opts.upd_rows == 0) {
     const int stage_base = h->dc && (rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT);
     RD_TRY(h->dc ? autotune_plan<float>(h, H, transform, stage_base, usable)
                  : autotune_plan<double>(h, H, transform, stage_base, usable));
   }
-  if (h->dc && h->opts.fused_update && transform) {
+  if (h->dc && h->opts.fused_update && transform && !h->nd3) {
     const int stage_base = rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT;
     RD_TRY(plan_fused(h, H, stage_base, usable));
   }
@@ -1041,11 +1132,11 @@ rd_status step_host(rd_pdhg* h, rd_step_info* info) {
   const Desc* d64 = h->d_desc + 0;
   State* st0 = h->d_state + 0;
   State* st1 = h->d_state + 1;
-  const int nb = point_blocks(h->nx, h->ny);
+  const int nb = step_blocks(h);
   const int max_launch = h->opts.max_iter / h->opts.graph_k + 2;
   rd_step_info inf{};
   int final_status;
-  RD_CUDA(launch_begin(d64, st0, h->U64, h->rhs64, h->opts.tol, h->opts.tol_kind, nb, s));
+  RD_CUDA(begin_any(h, st0, h->U64, h->opts.tol, h->opts.tol_kind, nb, s));
   h->stats.kernel_launches += 2;  // k_begin, k_mass
   h->h_state[0].n = 0;
   h->h_state[1].n = 0;
@@ -1062,8 +1153,7 @@ rd_status step_host(rd_pdhg* h, rd_step_info* info) {
   } else {
     int inner_total = 0;
     for (int round = 0; round <= h->opts.dc_max_outer + 1; ++round) {
-      RD_CUDA(launch_resid64(h->h_desc[0], d64, st0, st1, h->U64, h->rhs64, nullptr, h->r32, h->u32, h->D32,
-                             h->P32[0], 1, h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, s));
+      RD_CUDA(resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, s));
       RD_CUDA(cudaMemcpyAsync(h->h_state, h->d_state, 2 * sizeof(State), cudaMemcpyDeviceToHost, s));
       RD_CUDA(cudaStreamSynchronize(s));
       h->stats.kernel_launches += 1;
@@ -1303,15 +1393,14 @@ rd_status rd_pdhg_solve_adaptive(rd_pdhg* h, double* u, const rd_adapt* a, rd_ad
 
 rd_status rd_pdhg_residual(rd_pdhg* h, const double* u, const double* u_k, double* w) {
   if (!h || !u || !u_k || !w) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
-  const int nb = point_blocks(h->nx, h->ny);
-  RD_CUDA(launch_begin(h->d_desc + 0, h->d_state + 2, u_k, h->rhs64, 0.0, 0, nb, h->stream));
+  const int nb = step_blocks(h);
+  RD_CUDA(begin_any(h, h->d_state + 2, u_k, 0.0, 0, nb, h->stream));
   if (h->fch) {
     RD_CUDA(launch_fch_residual(h->h_desc[0], nullptr, h->fchb, u, h->rhs64, w, 2 * nb, h->stream));
     RD_CUDA(cudaStreamSynchronize(h->stream));
     return RD_OK;
   }
-  RD_CUDA(launch_resid64(h->h_desc[0], h->d_desc + 0, h->d_state + 2, h->d_state + 2, u, h->rhs64, w, nullptr,
-                         nullptr, nullptr, nullptr, 0, 0.0, 0, nb, h->stream));
+  RD_CUDA(resid64_any(h, h->d_state + 2, h->d_state + 2, u, w, nullptr, nullptr, nullptr, nullptr, 0, nb, h->stream));
   RD_CUDA(cudaStreamSynchronize(h->stream));
   return RD_OK;
 }
@@ -1320,6 +1409,19 @@ rd_status rd_pdhg_apply_precond(rd_pdhg* h, const double* w, double* y) {
   if (!h || !w || !y) return fail(RD_ERR_INVALID_ARG, "NULL handle or buffer");
   if (h->dc) return fail(RD_ERR_UNSUPPORTED, "apply_precond needs a handle created with RD_PREC_FP64");
   const size_t bytes = h->npts * sizeof(double);
+  if (h->nd3) {
+    // W into the transform buffer; the five transform passes leave Y in P64[1] (h_desc[2].X)
+    if (h->precond == RD_PC_NONE) {
+      RD_CUDA(cudaMemcpyAsync(y, w, bytes, cudaMemcpyDeviceToDevice, h->stream));
+      RD_CUDA(cudaStreamSynchronize(h->stream));
+      return RD_OK;
+    }
+    RD_CUDA(cudaMemcpyAsync(h->WY64, w, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    RD_CUDA(launch_precond3<double>(h->h_desc[2], h->d_state + 2, h->stream));
+    RD_CUDA(cudaMemcpyAsync(y, h->P64[1], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    RD_CUDA(cudaStreamSynchronize(h->stream));
+    return RD_OK;
+  }
   RD_CUDA(cudaMemcpyAsync(h->P64[1], w, bytes, cudaMemcpyDeviceToDevice, h->stream));
   RD_CUDA(launch_iteration<double>(h->h_desc[2], h->d_state + 2, h->cfgpc, h->stream, nullptr));
   RD_CUDA(cudaMemcpyAsync(y, h->P64[1], bytes, cudaMemcpyDeviceToDevice, h->stream));

@@ -295,6 +295,10 @@ __device__ __forceinline__ cx<T>* block_fft_c(cx<T>* buf, cx<T>* scr, int nlines
 // unrolled at compile time for that length; otherwise one looped pass body serves every pass
 // (fewer distinct instructions, more index arithmetic; measured slower on GB300).
 template <class T, int DIR>
+__device__ cx<T>* block_fft_loop(cx<T>* buf, cx<T>* scr, int nlines, int logN, int ls, const cx<T>* __restrict__ tw,
+                                 int tid, int nthreads);
+
+template <class T, int DIR>
 __device__ cx<T>* block_fft(cx<T>* buf, cx<T>* scr, int nlines, int logN, int ls, const cx<T>* __restrict__ tw,
                             int tid, int nthreads, bool unrolled) {
   if (unrolled) switch (logN) {
@@ -306,6 +310,13 @@ __device__ cx<T>* block_fft(cx<T>* buf, cx<T>* scr, int nlines, int logN, int ls
     case 11: return block_fft_c<T, DIR, 11>(buf, scr, nlines, ls, tw, tid, nthreads);
     default: break;
   }
+  return block_fft_loop<T, DIR>(buf, scr, nlines, logN, ls, tw, tid, nthreads);
+}
+
+// The looped form of block_fft: one pass body for every pass of every length.
+template <class T, int DIR>
+__device__ cx<T>* block_fft_loop(cx<T>* buf, cx<T>* scr, int nlines, int logN, int ls, const cx<T>* __restrict__ tw,
+                                 int tid, int nthreads) {
   constexpr int RM = FftRadix<T>::value;
   constexpr int LRM = RM == 8 ? 3 : 4;
   int chunk = (nthreads * RM) >> logN;

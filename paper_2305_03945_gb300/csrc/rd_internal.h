@@ -75,6 +75,18 @@ struct Desc {
   // and read by that block only
   void* WYb[2];
   void* halo;
+  // 3-D grids (nz > 1; 0 or 1 on a 2-D grid): arrays [ncomp][nz][ny][nx], seven-point Laplacian
+  // (the scheme with a third axis), transforms along x, y and z.  Every 3-D kernel runs blk3
+  // blocks per instance in a grid-stride loop (fixed per instance, so that results do not depend
+  // on what else shares a launch); lw3[a] lines of axis a per tile of the transform passes.
+  int nz, lognz;
+  double hz2;        // 1/h_z^2
+  const void* muz;   // nz entries of T
+  const void* twz;   // nz complex T
+  const void* dcz;   // nz complex T
+  int blk3;
+  int lw3[3];
+  int thr3[3];       // threads per block of the transform pass of each axis
 };
 
 struct State {

@@ -82,19 +82,7 @@ __global__ void __launch_bounds__(256) k_begin(const Desc* __restrict__ d64, Sta
   if (last_block(st, gridDim.x)) {
     __threadfence();
     const double tot = sum_partials(d.partials, gridDim.x, red);
-    if (threadIdx.x == 0) {
-      const double nrm = sqrt(tot);
-      st->ticket = 0u;
-      st->aux = nrm;
-      st->thresh = tol_kind == 1 ? tol * nrm : tol;
-      st->n = 0;
-      st->r = 0.0;
-      st->r0 = 0.0;
-      st->trips = 0u;
-      st->total = 0;
-      st->launches = 0;
-      st->status = ST_ACTIVE;
-    }
+    if (threadIdx.x == 0) begin_state(st, tot, tol, tol_kind);
   }
 }
 
@@ -153,34 +141,7 @@ __global__ void __launch_bounds__(256)
     __threadfence();
     double tot = 0.0;
     for (int c = 0; c < nc; ++c) tot += sqrt(sum_partials(d.partials + c * nb, nb, red));
-    if (threadIdx.x == 0) {
-      const double meas = d.meas_div_dt ? tot / d.dt : tot;
-      const double prev = outer->r;
-      outer->ticket = 0u;
-      outer->r = meas;
-      const int n = outer->n;
-      if (n == 0) outer->r0 = meas;
-      const double r0 = n == 0 ? meas : outer->r0;
-      outer->n = n + 1;
-      if (meas <= outer->thresh) {
-        outer->status = ST_CONVERGED;
-      } else if (!isfinite(meas) || meas > kDivergeFactor * r0) {
-        outer->status = ST_DIVERGED;
-      } else if (n >= max_outer) {
-        outer->status = ST_NOT_CONVERGED;
-      } else {
-        inner->stall_mul = next_stall_mul(n, meas, prev, inner->stall_mul);
-        inner->n = 0;
-        inner->trips = 0u;
-        inner->r = 0.0;
-        inner->r0 = 0.0;
-        // rtol of the current FP64 residual, but no tighter than half of what the outer
-        // stopping rule still needs: the last round solves no further than the step requires
-        inner->thresh = fmax(rtol * tot, 0.5 * outer->thresh * (d.meas_div_dt ? d.dt : 1.0));
-        inner->status = ST_ACTIVE;
-        inner->ticket = 0u;
-      }
-    }
+    if (threadIdx.x == 0) outer_decide(d, outer, inner, tot, rtol, max_outer);
   }
 }
 
@@ -230,14 +191,14 @@ __global__ void k_axpy_dc(double* __restrict__ u, const float* __restrict__ dlt,
   }
 }
 
-// h_x h_y sum of u into st->mass; with `gate`, only once `gate` is no longer active.
+// h_x h_y (h_z) sum of u into st->mass; with `gate`, only once `gate` is no longer active.
 __global__ void __launch_bounds__(256) k_mass(const Desc* __restrict__ d64, State* __restrict__ st,
                                               const double* __restrict__ u, const State* __restrict__ gate) {
   if (gate && *((volatile const int*)&gate->status) == ST_ACTIVE) return;
   const Desc& d = *d64;
   __shared__ double red[32];
   const int nc = d.ncomp;
-  const size_t plane = (size_t)d.nx * d.ny;
+  const size_t plane = (size_t)d.nx * d.ny * (d.nz > 1 ? d.nz : 1);  // points per component
   double acc = 0.0;
 #pragma unroll 4
   for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < (plane >> 1); g += (size_t)gridDim.x * blockDim.x)
@@ -252,7 +213,7 @@ __global__ void __launch_bounds__(256) k_mass(const Desc* __restrict__ d64, Stat
     const double tot = sum_partials(d.partials, gridDim.x, red);
     if (threadIdx.x == 0) {
       st->ticket = 0u;
-      st->mass = tot / (sqrt(d.hx2) * sqrt(d.hy2));
+      st->mass = tot / (sqrt(d.hx2) * sqrt(d.hy2) * (d.nz > 1 ? sqrt(d.hz2) : 1.0));
     }
   }
 }

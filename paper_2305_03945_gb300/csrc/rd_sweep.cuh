@@ -252,6 +252,56 @@ __device__ inline void finalize_measure(const Desc& d, State* st, double* red, S
   }
 }
 
+// Step set-up decision (thread 0 of the last block of a begin kernel): ||U^k|| = sqrt(tot), the
+// stopping threshold of the step (tol, or tol ||U^k||), and a fresh solve state.
+__device__ inline void begin_state(State* st, double tot, double tol, int tol_kind) {
+  const double nrm = sqrt(tot);
+  st->ticket = 0u;
+  st->aux = nrm;
+  st->thresh = tol_kind == 1 ? tol * nrm : tol;
+  st->n = 0;
+  st->r = 0.0;
+  st->r0 = 0.0;
+  st->trips = 0u;
+  st->total = 0;
+  st->launches = 0;
+  st->status = ST_ACTIVE;
+}
+
+// Outer stopping rule of defect correction (thread 0 of the last block of an FP64 residual
+// kernel), from tot = sum_c ||W_c|| of W = F(u): evaluation number max_outer (counting from 0)
+// ends the step as not converged; otherwise the inner FP32 solve is armed with the threshold
+// max(rtol tot, half the outer threshold in the same units).
+__device__ inline void outer_decide(const Desc& d, State* outer, State* inner, double tot, double rtol,
+                                    int max_outer) {
+  const double meas = d.meas_div_dt ? tot / d.dt : tot;
+  const double prev = outer->r;
+  outer->ticket = 0u;
+  outer->r = meas;
+  const int n = outer->n;
+  if (n == 0) outer->r0 = meas;
+  const double r0 = n == 0 ? meas : outer->r0;
+  outer->n = n + 1;
+  if (meas <= outer->thresh) {
+    outer->status = ST_CONVERGED;
+  } else if (!isfinite(meas) || meas > kDivergeFactor * r0) {
+    outer->status = ST_DIVERGED;
+  } else if (n >= max_outer) {
+    outer->status = ST_NOT_CONVERGED;
+  } else {
+    inner->stall_mul = next_stall_mul(n, meas, prev, inner->stall_mul);
+    inner->n = 0;
+    inner->trips = 0u;
+    inner->r = 0.0;
+    inner->r0 = 0.0;
+    // rtol of the current FP64 residual, but no tighter than half of what the outer stopping
+    // rule still needs: the last round solves no further than the step requires
+    inner->thresh = fmax(rtol * tot, 0.5 * outer->thresh * (d.meas_div_dt ? d.dt : 1.0));
+    inner->status = ST_ACTIVE;
+    inner->ticket = 0u;
+  }
+}
+
 // 16-byte vectors
 template <class T> struct V16;
 template <> struct V16<float> { using t = float4; static constexpr int n = 4; };

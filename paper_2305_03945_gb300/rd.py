@@ -190,9 +190,10 @@ def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_i
                  dc_max_outer=None, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1, autotune=0, upd_rows=0, dc_stall_window=None, fused_update=1):
     """C structs for a ``workloads.Problem``."""
     g = rd_grid()
-    g.ndim = 2
-    g.n[0], g.n[1], g.n[2] = pb.nx, pb.ny, 1
-    g.length[0], g.length[1], g.length[2] = pb.lx, pb.ly, 1.0
+    nz = getattr(pb, "nz", 1)
+    g.ndim = 3 if nz > 1 else 2
+    g.n[0], g.n[1], g.n[2] = pb.nx, pb.ny, nz
+    g.length[0], g.length[1], g.length[2] = pb.lx, pb.ly, getattr(pb, "lz", 1.0)
     rx = rd_reaction()
     rx.kind = KIND[pb.kind]
     rx.ncomp = pb.ncomp
