@@ -280,7 +280,9 @@ def serving_leg(n_req, seed, rates, budget, slots, fp64_sample):
     ok = all(r["status"] == 0 for r in res_sat.values())
     sat = len(reqs) / wall_sat
     lat = np.array([r["t_done"] - r["t_submit"] for r in res_sat.values()])
-    out = {"requests": n_req, "sides": list(WL.SERVING_SIDES), "kinds": "allen_cahn | ch_split, periodic | neumann",
+    n3 = sum(1 for pb, _, _ in reqs if pb.nz > 1)
+    out = {"requests": n_req, "grids": ["%d^2" % s for s in WL.SERVING_SIDES] + ["%d^3" % WL.SERVING_CUBE],
+           "requests_3d": n3, "kinds": "allen_cahn | ch_split, periodic | neumann",
            "steps": "10-50", "tol": "f_rel 1e-6", "hbm_budget_gb": budget / 2**30, "max_slots": slots,
            "saturation": {"solves_per_s": sat, "wall_s": wall_sat, "all_converged": ok,
                           "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99))},

@@ -29,7 +29,9 @@
 #include <vector>
 
 #include "../../include/rd_pdhg.h"
-#include "rd_sweep.cuh"
+#include "rd_3d.cuh"
+#include "rd_batch3.h"
+#include "rd_launch3.h"
 
 namespace rd {
 
@@ -241,6 +243,8 @@ namespace {
 
 constexpr int kBatchThreads = 256;      // FP32 sweep blocks
 constexpr int kBatchMaxSide = 1024;     // batch grids: sides 4 .. 1024, powers of two
+constexpr int kBatchMaxSide3 = 512;     // 3-D batch grids: sides 4 .. 512
+constexpr int kBatchMaxBlk3 = 2 * 152;  // blocks per 3-D slot (plan3's cap)
 constexpr int kBatchBandRows = 4;
 constexpr int kBatchColWidth = 4;
 constexpr int kBatchGroups = 5;         // scalar equation kinds served
@@ -312,14 +316,25 @@ struct SlotHost {
   size_t mem_bytes = 0;
   size_t npts = 0;
   double t_submit = 0, t_admit = 0;
+  bool nd3 = false;  // a 3-D request (the rd_batch3.cu kernels)
   Desc d32{}, d64{};
 };
 
 size_t slot_bytes(const rd_request& r, size_t* npts_out) {
-  const size_t npts = (size_t)r.reaction.ncomp * r.grid.n[0] * r.grid.n[1];
+  const bool nd3 = r.grid.ndim == 3;
+  const int nz = nd3 ? r.grid.n[2] : 1;
+  const size_t npts = (size_t)r.reaction.ncomp * r.grid.n[0] * r.grid.n[1] * nz;
   if (npts_out) *npts_out = npts;
   const int nx = r.grid.n[0], ny = r.grid.n[1];
   size_t b = 0;
+  if (nd3) {
+    b += Arena::up(npts * 8) * 2;                       // u, rhs (FP64)
+    b += Arena::up(npts * 4) * 5;                       // d, P, WY, r32, u32
+    b += Arena::up((size_t)(nx + ny + nz) * 2 * 8);     // twiddles + rotations (FP32 complex)
+    b += Arena::up((size_t)(nx + ny + nz) * 4);         // mu tables
+    b += Arena::up((size_t)2 * kBatchMaxBlk3 * 8);      // partials
+    return b;
+  }
   b += Arena::up(npts * 8) * 2;                       // u, rhs (FP64)
   b += Arena::up(npts * 4) * 6;                       // d, P0, P1, WY, r32, u32
   b += Arena::up((size_t)(nx + ny) * 2 * 8) * 1;      // twiddles + rotations (FP32 complex)
@@ -346,6 +361,12 @@ struct rd_batch {
   int2* d_col_items[kBatchGroups] = {};
   int n_band[kBatchGroups] = {}, n_col[kBatchGroups] = {};
   std::vector<int2> h_band[kBatchGroups], h_col[kBatchGroups];
+  // 3-D slots: one work list of (slot, block) pairs per group, and the largest transform-pass
+  // block and shared memory any of its slots needs
+  int2* d_items3[kBatchGroups] = {};
+  int n_items3[kBatchGroups] = {};
+  std::vector<int2> h_items3[kBatchGroups];
+  int thr3[kBatchGroups][3] = {}, smem3[kBatchGroups][3] = {};
   std::vector<SlotHost> slots;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -433,6 +454,14 @@ void launch_iteration_all(rd_batch* b, cudaStream_t s) {
       case KK_CH_SPLIT: launch_group<KK_CH_SPLIT>(b, g, s); break;
       default: launch_group<KK_NONE_BIH>(b, g, s); break;
     }
+    if (b->n_items3[g]) {
+      Batch3Launch L{b->d_d32, b->d_d64, b->d_slots, b->d_items3[g], b->n_items3[g], {}, {}};
+      for (int a = 0; a < 3; ++a) {
+        L.thr[a] = b->thr3[g][a];
+        L.smem[a] = b->smem3[g][a];
+      }
+      batch3_launch_group(kGroupKey[g], L, s);
+    }
   }
 }
 
@@ -464,16 +493,35 @@ rd_status rebuild_items(rd_batch* b) {
   for (int g = 0; g < kBatchGroups; ++g) {
     b->h_band[g].clear();
     b->h_col[g].clear();
+    b->h_items3[g].clear();
+    for (int a = 0; a < 3; ++a) b->thr3[g][a] = b->smem3[g][a] = 0;
   }
   for (int s = 0; s < b->max_slots; ++s) {
     const SlotHost& sh = b->slots[s];
     if (!sh.used) continue;
+    if (sh.nd3) {
+      const Desc& d = sh.d32;
+      for (int k = 0; k < d.blk3; ++k) b->h_items3[sh.group].push_back(make_int2(s, k));
+      const int n_ax[3] = {d.nx, d.ny, d.nz};
+      for (int a = 0; a < 3; ++a) {
+        b->thr3[sh.group][a] = std::max(b->thr3[sh.group][a], d.thr3[a]);
+        b->smem3[sh.group][a] = std::max(b->smem3[sh.group][a],
+                                         lines3_smem_bytes<float>(n_ax[a], d.lw3[a], d.bc == BC_NEUMANN));
+      }
+      continue;
+    }
     for (int band = 0; band < sh.d32.nbands; ++band) b->h_band[sh.group].push_back(make_int2(s, band));
     for (int cb = 0; cb < sh.d32.ncomp * sh.d32.ncolblk; ++cb) b->h_col[sh.group].push_back(make_int2(s, cb));
   }
   for (int g = 0; g < kBatchGroups; ++g) {
     b->n_band[g] = (int)b->h_band[g].size();
     b->n_col[g] = (int)b->h_col[g].size();
+    b->n_items3[g] = (int)b->h_items3[g].size();
+    if (b->n_items3[g]) {
+      cudaError_t e = cudaMemcpyAsync(b->d_items3[g], b->h_items3[g].data(), b->n_items3[g] * sizeof(int2),
+                                      cudaMemcpyHostToDevice, b->stream);
+      if (e != cudaSuccess) return bfail(RD_ERR_CUDA, cudaGetErrorString(e));
+    }
     if (b->n_band[g]) {
       cudaError_t e = cudaMemcpyAsync(b->d_band_items[g], b->h_band[g].data(), b->n_band[g] * sizeof(int2),
                                       cudaMemcpyHostToDevice, b->stream);
@@ -487,6 +535,131 @@ rd_status rebuild_items(rd_batch* b) {
   }
   b->graph_dirty = true;
   return RD_OK;
+}
+
+// Set-up of an admitted 3-D request in slot s (arena block mem): arrays, the FP32 and FP64
+// descriptors with the 3-D plan, tables, state and control block.
+void admit3(rd_batch* b, Request& q, int s, char* mem, size_t npts, rd_status* err) {
+  SlotHost& sh = b->slots[s];
+  const rd_request& r = q.req;
+  const int nx = r.grid.n[0], ny = r.grid.n[1], nz = r.grid.n[2];
+  char* p = mem;
+  auto take = [&](size_t n) {
+    char* q2 = p;
+    p += Arena::up(n);
+    return q2;
+  };
+  double* u = (double*)take(npts * 8);
+  double* rhs = (double*)take(npts * 8);
+  float* dl = (float*)take(npts * 4);
+  float* p0 = (float*)take(npts * 4);
+  float* wy = (float*)take(npts * 4);
+  float* r32 = (float*)take(npts * 4);
+  float* u32 = (float*)take(npts * 4);
+  float* tabs = (float*)take((size_t)(nx + ny + nz) * 2 * 8);
+  float* mus = (float*)take((size_t)(nx + ny + nz) * 4);
+  double* parts = (double*)take((size_t)2 * kBatchMaxBlk3 * 8);
+  const double hx = r.grid.length[0] / nx, hy = r.grid.length[1] / ny, hz = r.grid.length[2] / nz;
+  Desc d{};
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.ncomp = 1;
+  d.lognx = ilog2i(nx);
+  d.logny = ilog2i(ny);
+  d.lognz = ilog2i(nz);
+  d.bc = r.bc;
+  d.op = r.op;
+  d.kind = r.reaction.kind;
+  d.precond = 1;
+  d.mode = MODE_PDHG;
+  d.hx2 = 1.0 / (hx * hx);
+  d.hy2 = 1.0 / (hy * hy);
+  d.hz2 = 1.0 / (hz * hz);
+  d.dt = r.dt;
+  d.a = r.reaction.a;
+  d.b = r.reaction.b;
+  for (int k = 0; k < 6; ++k) d.p[k] = r.reaction.p[k];
+  d.tau_u = r.tau;
+  d.tau_p = r.sigma;
+  d.omega = b->opts.omega;
+  d.batched = 1;
+  d.partials = parts;
+  for (int c = 0; c < 2; ++c) {
+    d.gc1[c] = r.op == RD_OP_LAPLACIAN ? r.reaction.a * r.dt : 0.0;
+    d.gc2[c] = r.op == RD_OP_LAPLACIAN ? 0.0 : r.reaction.a * r.dt;
+  }
+  d.inv_nn = 1.0 / ((double)nx * ny * nz);
+  const char* why = nullptr;
+  if (!plan3(nx, ny, nz, 1, 4, r.bc == RD_BC_NEUMANN, 226 * 1024, d, &why)) {
+    *err = bfail(RD_ERR_UNSUPPORTED, std::string("admission: ") + why);
+    return;
+  }
+  Desc d64 = d, d32 = d;
+  d64.dc = 0;
+  d64.meas_div_dt = r.tol_kind == RD_TOL_RES_ABS;
+  d64.X = u;
+  d64.rhs = rhs;
+  d64.f32_d = dl;
+  d64.f32_p0 = p0;
+  d64.f32_r = r32;
+  d64.f32_u = u32;
+  d32.dc = 1;
+  d32.meas_div_dt = 0;
+  d32.stall_window = b->opts.dc_stall_window > 0 ? b->opts.dc_stall_window : 8;
+  d32.X = dl;
+  d32.base = u32;
+  d32.rhs = r32;
+  d32.P[0] = p0;
+  d32.P[1] = p0;
+  d32.WY = wy;
+  cx<float>* twx = reinterpret_cast<cx<float>*>(tabs);
+  cx<float>* dcx = twx + nx;
+  cx<float>* twy = dcx + nx;
+  cx<float>* dcy = twy + ny;
+  cx<float>* twz = dcy + ny;
+  cx<float>* dcz = twz + nz;
+  d32.twx = twx;
+  d32.dcx = dcx;
+  d32.twy = twy;
+  d32.dcy = dcy;
+  d32.twz = twz;
+  d32.dcz = dcz;
+  d32.mux = mus;
+  d32.muy = mus + nx;
+  d32.muz = mus + nx + ny;
+  sh.d32 = d32;
+  sh.d64 = d64;
+  sh.nd3 = true;
+  std::vector<float> tw, dc, mu, all_t, all_mu;
+  const int n_ax[3] = {nx, ny, nz};
+  const double h_ax[3] = {hx, hy, hz};
+  for (int a = 0; a < 3; ++a) {
+    host_tables(n_ax[a], r.bc == RD_BC_NEUMANN, h_ax[a], tw, dc, mu);
+    all_t.insert(all_t.end(), tw.begin(), tw.end());
+    all_t.insert(all_t.end(), dc.begin(), dc.end());
+    all_mu.insert(all_mu.end(), mu.begin(), mu.end());
+  }
+  Slot ctl{};
+  ctl.outer.max_iter = 1 << 30;
+  ctl.inner.max_iter = b->opts.max_iter;
+  ctl.phase = PH_BEGIN;
+  ctl.nsteps = r.nsteps;
+  ctl.max_outer = b->opts.dc_max_outer;
+  ctl.tol = r.tol;
+  ctl.rtol = b->opts.dc_inner_rtol;
+  ctl.tol_kind = r.tol_kind;
+  cudaStream_t st = b->stream;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tabs, all_t.data(), all_t.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mus, all_mu.data(), all_mu.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(u, q.u0.data(), npts * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_d32 + s, &sh.d32, sizeof(Desc), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_d64 + s, &sh.d64, sizeof(Desc), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_slots + s, &ctl, sizeof(Slot), cudaMemcpyHostToDevice, st);
+  // the host vectors above are pageable: wait for the copies before they go out of scope
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) *err = bfail(RD_ERR_CUDA, std::string("admission: ") + cudaGetErrorString(e));
 }
 
 // Try to admit the request into a free slot.  Returns false when no slot or memory is free.
@@ -514,6 +687,12 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   sh.npts = npts;
   sh.t_submit = q.t_submit;
   sh.t_admit = now_s();
+  sh.nd3 = false;
+  if (q.req.grid.ndim == 3) {
+    admit3(b, q, s, mem, npts, err);
+    b->stats.admitted += 1;
+    return true;
+  }
   const rd_request& r = q.req;
   const int nx = r.grid.n[0], ny = r.grid.n[1], nc = r.reaction.ncomp;
   char* p = mem;
@@ -780,7 +959,8 @@ rd_status rd_batch_create(rd_batch** out, size_t hbm_budget_bytes, int max_slots
     return cleanup(bfail(RD_ERR_OOM, cudaGetErrorString(e)));
   for (int g = 0; g < kBatchGroups; ++g) {
     if ((e = cudaMalloc(&b->d_band_items[g], sizeof(int2) * max_items)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_col_items[g], sizeof(int2) * max_items)) != cudaSuccess)
+        (e = cudaMalloc(&b->d_col_items[g], sizeof(int2) * max_items)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_items3[g], sizeof(int2) * max_slots * kBatchMaxBlk3)) != cudaSuccess)
       return cleanup(bfail(RD_ERR_OOM, cudaGetErrorString(e)));
   }
   cudaMemset(b->d_slots, 0, sizeof(Slot) * max_slots);
@@ -792,6 +972,7 @@ rd_status rd_batch_create(rd_batch** out, size_t hbm_budget_bytes, int max_slots
   b->smem_sweep = std::max(res_smem_bytes<float>(1, kBatchBandRows, 2, kBatchMaxSide, 1, 0, tabs),
                            std::max(lines_smem_bytes<float>((kBatchBandRows + 4) / 2, kBatchMaxSide, 0, tabs),
                                     lines_smem_bytes<float>(kBatchColWidth / 2, kBatchMaxSide, 0, tabs)));
+  if ((e = batch3_allow(optin)) != cudaSuccess) return cleanup(bfail(RD_ERR_CUDA, cudaGetErrorString(e)));
   if ((e = allow_batch_kernels<float, KK_NONE_LAP>(optin)) != cudaSuccess ||
       (e = allow_batch_kernels<float, KK_AC>(optin)) != cudaSuccess ||
       (e = allow_batch_kernels<float, KK_CH_IMPL>(optin)) != cudaSuccess ||
@@ -812,10 +993,13 @@ rd_status rd_batch_create(rd_batch** out, size_t hbm_budget_bytes, int max_slots
 rd_status rd_batch_submit(rd_batch* b, const rd_request* req, double* u_out_host, uint64_t* id) {
   if (!b || !req || !req->u0_host) return bfail(RD_ERR_INVALID_ARG, "NULL batch, request or u0");
   const rd_request& r = *req;
-  if (r.grid.ndim != 2) return bfail(RD_ERR_UNSUPPORTED, "batch: 2-D grids only");
-  for (int k = 0; k < 2; ++k) {
+  if (r.grid.ndim != 2 && r.grid.ndim != 3) return bfail(RD_ERR_UNSUPPORTED, "batch: 2-D and 3-D grids only");
+  for (int k = 0; k < r.grid.ndim; ++k) {
     const int n = r.grid.n[k];
-    if (n < 4 || n > kBatchMaxSide || (n & (n - 1))) return bfail(RD_ERR_UNSUPPORTED, "batch: sides must be powers of two in [4, 1024]");
+    if (r.grid.ndim == 2 && (n < 4 || n > kBatchMaxSide || (n & (n - 1))))
+      return bfail(RD_ERR_UNSUPPORTED, "batch: sides must be powers of two in [4, 1024]");
+    if (r.grid.ndim == 3 && (n < 4 || n > kBatchMaxSide3 || (n & (n - 1))))
+      return bfail(RD_ERR_UNSUPPORTED, "batch: 3-D sides must be powers of two in [4, 512]");
     if (!(r.grid.length[k] > 0)) return bfail(RD_ERR_INVALID_ARG, "lengths must be > 0");
   }
   if (r.bc != RD_BC_PERIODIC && r.bc != RD_BC_NEUMANN) return bfail(RD_ERR_INVALID_ARG, "bad boundary condition");
@@ -892,6 +1076,7 @@ void rd_batch_destroy(rd_batch* b) {
   for (int g = 0; g < kBatchGroups; ++g) {
     if (b->d_band_items[g]) cudaFree(b->d_band_items[g]);
     if (b->d_col_items[g]) cudaFree(b->d_col_items[g]);
+    if (b->d_items3[g]) cudaFree(b->d_items3[g]);
   }
   if (b->d_d32) cudaFree(b->d_d32);
   if (b->d_d64) cudaFree(b->d_d64);

@@ -328,30 +328,38 @@ def workload_small(name: str, n: int, nsteps: int, seed: int = 7) -> Workload:
 # --------------------------------------------------------------------------------------
 
 SERVING_SIDES = (64, 128, 256, 512, 1024)
+SERVING_CUBE = 128      # the mix's 3-D grid, 128^3
 
 
 def serving_requests(n: int, seed: int = 5000, min_steps: int = 10, max_steps: int = 50,
-                     sides=SERVING_SIDES, tol: float = 1e-6):
+                     sides=SERVING_SIDES, tol: float = 1e-6, cube=SERVING_CUBE):
     """The serving mix: n seeded requests, each an Allen-Cahn (physics of the 64^2 periodic
-    configuration, domain [0,2pi)^2) or Cahn-Hilliard convex-split (physics of the 512^2
-    configuration, domain [0,1]^2) run of min_steps..max_steps implicit steps on a square grid
-    drawn uniformly from `sides`, periodic or Neumann 50/50, each step solved to
-    ||F||_2 <= tol ||U^k||_2.  Returns a list of (Problem, u0, nsteps)."""
+    configuration, domain [0,2pi)^d) or Cahn-Hilliard convex-split (physics of the 512^2
+    configuration, domain [0,1]^d) run of min_steps..max_steps implicit steps, periodic or
+    Neumann 50/50, each step solved to ||F||_2 <= tol ||U^k||_2, on a grid drawn uniformly from
+    the square grids `sides`^2 and the cube `cube`^3 (cube = None: square grids only).  The 3-D
+    draw comes from its own seeded stream (probability 1 / (len(sides) + 1) per request), so the
+    square-grid requests are the same with and without the cube.  Returns a list of
+    (Problem, u0, nsteps)."""
     r = rng(seed)
+    r3 = rng(seed + 7919)
     out = []
     for k in range(n):
         side = int(r.choice(sides))
         bc = "periodic" if r.random() < 0.5 else "neumann"
         steps = int(r.integers(min_steps, max_steps + 1))
+        three = cube is not None and r3.random() < 1.0 / (len(sides) + 1)
+        g = dict(nx=cube, ny=cube, nz=cube) if three else dict(nx=side, ny=side)
         if r.random() < 0.5:
-            pb = Problem(nx=side, ny=side, lx=2 * np.pi, ly=2 * np.pi, bc=bc, op="laplacian",
+            L = 2 * np.pi
+            pb = Problem(lx=L, ly=L, lz=L, bc=bc, op="laplacian",
                          kind="allen_cahn", a=0.1, b=10.0, dt=0.01, tau_u=1.0, tau_p=1.0,
-                         tol=tol, tol_kind="f_rel")
+                         tol=tol, tol_kind="f_rel", **g)
             u0 = uniform_field(seed + 1 + k, pb.shape, -0.05, 0.05)
         else:
-            pb = Problem(nx=side, ny=side, lx=1.0, ly=1.0, bc=bc, op="neg_biharmonic",
+            pb = Problem(lx=1.0, ly=1.0, lz=1.0, bc=bc, op="neg_biharmonic",
                          kind="ch_split", a=4e-4, b=1.0, dt=1e-5, tau_u=1.0, tau_p=1.0,
-                         tol=tol, tol_kind="f_rel")
+                         tol=tol, tol_kind="f_rel", **g)
             u0 = zero_mean_uniform(seed + 1 + k, pb.shape, 0.1)
         out.append((pb, u0, steps))
     return out

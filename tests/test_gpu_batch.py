@@ -144,3 +144,59 @@ def test_request_larger_than_budget_is_refused():
         with pytest.raises(rd.RDError) as e:
             b.submit(pb, u0, n)
         assert e.value.status == rd.RD_ERR_BUSY
+
+
+def _requests3():
+    """3-D requests (the 7-point scheme) of both kinds and boundary conditions, uneven sizes."""
+    out = []
+    for k, (kind, op, bc, nz, ny, nx) in enumerate([
+        ("allen_cahn", "laplacian", "periodic", 16, 16, 16),
+        ("ch_split", "neg_biharmonic", "neumann", 8, 16, 32),
+        ("allen_cahn", "laplacian", "neumann", 32, 32, 32),
+        ("ch_implicit", "neg_biharmonic", "periodic", 16, 8, 16),
+    ]):
+        ch = op == "neg_biharmonic"
+        pb = WL.Problem(nx=nx, ny=ny, nz=nz, lx=1.0, ly=1.0, lz=1.0, bc=bc, op=op, kind=kind,
+                        dt=1e-5 if ch else 2e-3, a=4e-4 if ch else 0.05, b=1.0 if ch else 20.0,
+                        tau_u=1.0, tau_p=1.0, tol=1e-11, tol_kind="f_rel")
+        out.append((pb, WL.uniform_field(90 + k, pb.shape, -0.5, 0.5), 3 + k % 2))
+    return out
+
+
+def test_batch_with_3d_requests_matches_oracle():
+    """2-D and 3-D requests in one batch: every result against the oracle (<= 1e-9 rel. L2)."""
+    reqs = _requests3() + _requests()[:3]
+    ids, results, outs, stats = _run(reqs)
+    assert len(results) == len(reqs)
+    for rid, (pb, u0, n) in zip(ids, reqs):
+        r = results[rid]
+        assert r["status"] == 0 and r["steps"] == n, r
+        U_ref, _ = O.solve(pb, u0, n)
+        err = np.linalg.norm(outs[rid] - U_ref) / np.linalg.norm(U_ref)
+        assert err <= 1e-9, (pb.kind, pb.bc, pb.nz, pb.ny, pb.nx, err)
+
+
+def test_3d_request_same_alone_and_in_the_mix():
+    reqs = _requests3() + _requests()
+    probe = reqs[1]
+    _, res_alone, out_alone, _ = _run([probe])
+    ids, res_mix, out_mix, _ = _run(reqs)
+    assert np.array_equal(next(iter(out_alone.values())), out_mix[ids[1]])
+    assert next(iter(res_alone.values()))["iterations"] == res_mix[ids[1]]["iterations"]
+
+
+def test_serving_mix_128_cubed_request_matches_plain_fp64():
+    """A 128^3 request of the serving mix, batched, against the plain FP64 solve of the same
+    request to the mix's tolerance (||F|| <= 1e-6 ||U^k||)."""
+    from paper_2305_03945_gb300 import rd
+    reqs = WL.serving_requests(48)
+    k = next(i for i, (pb, _, _) in enumerate(reqs) if pb.nz == 128)
+    pb, u0, n = reqs[k]
+    n = min(n, 5)
+    u = torch.from_numpy(u0.copy()).cuda()
+    with rd.Solver(pb, precision="fp64") as s:
+        s.solve(u, n)
+    ref = u.cpu().numpy()
+    ids, results, outs, _ = _run([(pb, u0, n)])
+    assert results[ids[0]]["status"] == 0
+    assert np.linalg.norm(outs[ids[0]] - ref) <= 1e-5 * np.linalg.norm(ref)
