@@ -182,6 +182,10 @@ typedef struct {
                              per iteration; k_res only before the first update) when its block
                              fits, and with autotune only where it measures faster; 0: never.
                              Fused and unfused inner iterates differ by FP32 rounding only.     */
+    int small_solve;      /* 1 (default): FP32 defect correction on a 2-D grid small enough that
+                             every array of the inner solve fits one thread block's shared memory
+                             (about 8 K points: 64 x 64, 64 x 128, ...) runs each inner solve as ONE
+                             kernel launch, its iterations separated by block barriers; 0: never */
 } rd_opts;
 
 typedef struct {
@@ -206,6 +210,7 @@ typedef struct {
     int plan_col_width;          /* columns per CTA of the column transform chosen at create      */
     int plan_upd_rows;           /* rows per CTA of the update sweep (k_upd) chosen at create    */
     int fused_update;            /* 1 when the fused update + residual kernel (k_updres) runs      */
+    int small_solve;             /* 1 when each inner solve runs in one block (rd_opts.small_solve) */
 } rd_stats;
 
 typedef struct rd_pdhg rd_pdhg;

@@ -32,6 +32,7 @@
 #include "rd_3d.cuh"
 #include "rd_batch3.h"
 #include "rd_launch3.h"
+#include "rd_launch_small.h"
 
 namespace rd {
 
@@ -317,6 +318,7 @@ struct SlotHost {
   size_t npts = 0;
   double t_submit = 0, t_admit = 0;
   bool nd3 = false;  // a 3-D request (the rd_batch3.cu kernels)
+  int small = 0;     // a 2-D request whose inner solves run in one launch (1 one block, 2 a cluster)
   Desc d32{}, d64{};
 };
 
@@ -361,6 +363,19 @@ struct rd_batch {
   int2* d_col_items[kBatchGroups] = {};
   int n_band[kBatchGroups] = {}, n_col[kBatchGroups] = {};
   std::vector<int2> h_band[kBatchGroups], h_col[kBatchGroups];
+  // the step-phase kernels (axpy, step) run over the bands of every 2-D slot; the sweeps
+  // (res, col, upd) over the slots without a one-launch inner solve, which run k_small_*_b on
+  // their own work lists (one entry per slot) in a parallel branch of the graph
+  int2* d_phase_items[kBatchGroups] = {};
+  int n_phase[kBatchGroups] = {};
+  std::vector<int2> h_phase[kBatchGroups];
+  int2* d_small_items[kBatchGroups][2] = {};
+  int n_small[kBatchGroups][2] = {};
+  std::vector<int2> h_small[kBatchGroups][2];
+  int smem_small[kBatchGroups][2] = {};
+  int smem_usable = 0;
+  cudaStream_t fork_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // 3-D slots: one work list of (slot, block) pairs per group, and the largest transform-pass
   // block and shared memory any of its slots needs
   int2* d_items3[kBatchGroups] = {};
@@ -435,14 +450,27 @@ cudaError_t allow_batch_kernels(int optin) {
 
 template <int K>
 void launch_group(rd_batch* b, int g, cudaStream_t s) {
-  const int nb = b->n_band[g], ncl = b->n_col[g];
-  if (nb == 0) return;
+  const int np = b->n_phase[g], nb = b->n_band[g], ncl = b->n_col[g];
+  if (np == 0) return;
   const int smem_res = b->smem_sweep, smem_col = b->smem_sweep;
-  k_axpy_b<<<nb, 256, 0, s>>>(b->d_d64, b->d_slots, b->d_band_items[g]);
-  k_step_b<K><<<nb, 256, 0, s>>>(b->d_d64, b->d_slots, b->d_band_items[g]);
-  k_res_b<float, K><<<nb, kBatchThreads, smem_res, s>>>(b->d_d32, b->d_slots, b->d_band_items[g]);
-  k_col_b<float><<<ncl, kBatchThreads, smem_col, s>>>(b->d_d32, b->d_slots, b->d_col_items[g]);
-  k_upd_b<float, K><<<nb, kBatchThreads, smem_res, s>>>(b->d_d32, b->d_slots, b->d_band_items[g]);
+  k_axpy_b<<<np, 256, 0, s>>>(b->d_d64, b->d_slots, b->d_phase_items[g]);
+  k_step_b<K><<<np, 256, 0, s>>>(b->d_d64, b->d_slots, b->d_phase_items[g]);
+  const bool fork = b->n_small[g][0] + b->n_small[g][1] > 0;
+  if (fork) {
+    // the one-launch inner solves of the small slots, beside the sweeps of the others
+    cudaEventRecord(b->ev_fork, s);
+    cudaStreamWaitEvent(b->fork_stream, b->ev_fork, 0);
+    for (int m = 0; m < 2; ++m)
+      launch_small_batch(K, m + 1, b->d_d32, b->d_slots, b->d_small_items[g][m], b->n_small[g][m], b->smem_small[g][m],
+                         b->fork_stream);
+    cudaEventRecord(b->ev_join, b->fork_stream);
+  }
+  if (nb) {
+    k_res_b<float, K><<<nb, kBatchThreads, smem_res, s>>>(b->d_d32, b->d_slots, b->d_band_items[g]);
+    k_col_b<float><<<ncl, kBatchThreads, smem_col, s>>>(b->d_d32, b->d_slots, b->d_col_items[g]);
+    k_upd_b<float, K><<<nb, kBatchThreads, smem_res, s>>>(b->d_d32, b->d_slots, b->d_band_items[g]);
+  }
+  if (fork) cudaStreamWaitEvent(s, b->ev_join, 0);
 }
 
 void launch_iteration_all(rd_batch* b, cudaStream_t s) {
@@ -493,6 +521,11 @@ rd_status rebuild_items(rd_batch* b) {
   for (int g = 0; g < kBatchGroups; ++g) {
     b->h_band[g].clear();
     b->h_col[g].clear();
+    b->h_phase[g].clear();
+    for (int m = 0; m < 2; ++m) {
+      b->h_small[g][m].clear();
+      b->smem_small[g][m] = 0;
+    }
     b->h_items3[g].clear();
     for (int a = 0; a < 3; ++a) b->thr3[g][a] = b->smem3[g][a] = 0;
   }
@@ -510,6 +543,15 @@ rd_status rebuild_items(rd_batch* b) {
       }
       continue;
     }
+    for (int band = 0; band < sh.d32.nbands; ++band) b->h_phase[sh.group].push_back(make_int2(s, band));
+    if (sh.small) {
+      const Desc& d = sh.d32;
+      const int m = sh.small - 1;
+      b->h_small[sh.group][m].push_back(make_int2(s, 0));
+      b->smem_small[sh.group][m] = std::max(
+          b->smem_small[sh.group][m], small_smem_of(sh.small, d.nx, d.ny, 1, sh.key, d.bc == BC_NEUMANN));
+      continue;
+    }
     for (int band = 0; band < sh.d32.nbands; ++band) b->h_band[sh.group].push_back(make_int2(s, band));
     for (int cb = 0; cb < sh.d32.ncomp * sh.d32.ncolblk; ++cb) b->h_col[sh.group].push_back(make_int2(s, cb));
   }
@@ -517,6 +559,20 @@ rd_status rebuild_items(rd_batch* b) {
     b->n_band[g] = (int)b->h_band[g].size();
     b->n_col[g] = (int)b->h_col[g].size();
     b->n_items3[g] = (int)b->h_items3[g].size();
+    b->n_phase[g] = (int)b->h_phase[g].size();
+    if (b->n_phase[g]) {
+      cudaError_t e = cudaMemcpyAsync(b->d_phase_items[g], b->h_phase[g].data(), b->n_phase[g] * sizeof(int2),
+                                      cudaMemcpyHostToDevice, b->stream);
+      if (e != cudaSuccess) return bfail(RD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    for (int m = 0; m < 2; ++m) {
+      b->n_small[g][m] = (int)b->h_small[g][m].size();
+      if (b->n_small[g][m]) {
+        cudaError_t e = cudaMemcpyAsync(b->d_small_items[g][m], b->h_small[g][m].data(),
+                                        b->n_small[g][m] * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return bfail(RD_ERR_CUDA, cudaGetErrorString(e));
+      }
+    }
     if (b->n_items3[g]) {
       cudaError_t e = cudaMemcpyAsync(b->d_items3[g], b->h_items3[g].data(), b->n_items3[g] * sizeof(int2),
                                       cudaMemcpyHostToDevice, b->stream);
@@ -776,6 +832,8 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   d32.muy = mus + nx;
   sh.d32 = d32;
   sh.d64 = d64;
+  // small grids: each inner solve in one launch (one block, or a cluster of eight)
+  sh.small = b->opts.small_solve ? small_mode(nx, ny, 1, sh.key, r.bc == RD_BC_NEUMANN, b->smem_usable) : 0;
   // tables, state, control block
   std::vector<float> tw, dc, mu, all_t, all_mu;
   host_tables(nx, r.bc == RD_BC_NEUMANN, hx, tw, dc, mu);
@@ -944,7 +1002,10 @@ rd_status rd_batch_create(rd_batch** out, size_t hbm_budget_bytes, int max_slots
     return s;
   };
   cudaError_t e;
-  if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+  if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&b->fork_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess)
     return cleanup(bfail(RD_ERR_CUDA, cudaGetErrorString(e)));
   if ((e = cudaMalloc(&b->arena_mem, hbm_budget_bytes)) != cudaSuccess) {
     cudaGetLastError();
@@ -959,6 +1020,9 @@ rd_status rd_batch_create(rd_batch** out, size_t hbm_budget_bytes, int max_slots
     return cleanup(bfail(RD_ERR_OOM, cudaGetErrorString(e)));
   for (int g = 0; g < kBatchGroups; ++g) {
     if ((e = cudaMalloc(&b->d_band_items[g], sizeof(int2) * max_items)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_phase_items[g], sizeof(int2) * max_items)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_small_items[g][0], sizeof(int2) * max_slots)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_small_items[g][1], sizeof(int2) * max_slots)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_col_items[g], sizeof(int2) * max_items)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_items3[g], sizeof(int2) * max_slots * kBatchMaxBlk3)) != cudaSuccess)
       return cleanup(bfail(RD_ERR_OOM, cudaGetErrorString(e)));
@@ -972,7 +1036,9 @@ rd_status rd_batch_create(rd_batch** out, size_t hbm_budget_bytes, int max_slots
   b->smem_sweep = std::max(res_smem_bytes<float>(1, kBatchBandRows, 2, kBatchMaxSide, 1, 0, tabs),
                            std::max(lines_smem_bytes<float>((kBatchBandRows + 4) / 2, kBatchMaxSide, 0, tabs),
                                     lines_smem_bytes<float>(kBatchColWidth / 2, kBatchMaxSide, 0, tabs)));
-  if ((e = batch3_allow(optin)) != cudaSuccess) return cleanup(bfail(RD_ERR_CUDA, cudaGetErrorString(e)));
+  if ((e = batch3_allow(optin)) != cudaSuccess || (e = allow_small(optin)) != cudaSuccess)
+    return cleanup(bfail(RD_ERR_CUDA, cudaGetErrorString(e)));
+  b->smem_usable = optin - 1024;
   if ((e = allow_batch_kernels<float, KK_NONE_LAP>(optin)) != cudaSuccess ||
       (e = allow_batch_kernels<float, KK_AC>(optin)) != cudaSuccess ||
       (e = allow_batch_kernels<float, KK_CH_IMPL>(optin)) != cudaSuccess ||
@@ -1077,6 +1143,9 @@ void rd_batch_destroy(rd_batch* b) {
     if (b->d_band_items[g]) cudaFree(b->d_band_items[g]);
     if (b->d_col_items[g]) cudaFree(b->d_col_items[g]);
     if (b->d_items3[g]) cudaFree(b->d_items3[g]);
+    if (b->d_phase_items[g]) cudaFree(b->d_phase_items[g]);
+    for (int m = 0; m < 2; ++m)
+      if (b->d_small_items[g][m]) cudaFree(b->d_small_items[g][m]);
   }
   if (b->d_d32) cudaFree(b->d_d32);
   if (b->d_d64) cudaFree(b->d_d64);
@@ -1084,6 +1153,9 @@ void rd_batch_destroy(rd_batch* b) {
   if (b->h_slots) cudaFreeHost(b->h_slots);
   if (b->arena_mem) cudaFree(b->arena_mem);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->fork_stream) cudaStreamDestroy(b->fork_stream);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   delete b;
 }
 

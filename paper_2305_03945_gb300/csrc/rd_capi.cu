@@ -12,6 +12,7 @@
 #include "rd_device.cuh"
 #include "rd_launch.h"
 #include "rd_launch3.h"
+#include "rd_launch_small.h"
 
 using namespace rd;
 
@@ -189,6 +190,7 @@ struct rd_pdhg {
   int nx = 0, ny = 0, nc = 1;
   int nz = 1;       // 3-D grids: points along z (1 on a 2-D grid)
   int nd3 = 0;      // 1: a 3-D grid (the rd_3d.cu kernels)
+  int small = 0;    // every FP32 inner solve in one launch (rd_small.cu): 1 one block, 2 a cluster
   double hz = 0;
   size_t npts = 0;  // nc * nx * ny * nz
   int bc = 0, op = 0, kind = 0, precond = 1;
@@ -371,6 +373,22 @@ cudaError_t resid64_any(rd_pdhg* h, State* outer, State* inner, const double* u,
                         h->opts.dc_inner_rtol, h->opts.dc_max_outer, nb, s);
 }
 
+// The one-block inner solve with the profiling events around it (ev[0..3]; the time lands in
+// kernel_ms[0]).
+cudaError_t small_launch(rd_pdhg* h, cudaStream_t s, cudaEvent_t* ev) {
+  unsigned flags = cudaEventRecordDefault;
+  if (ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusActive) flags = cudaEventRecordExternal;
+  }
+  cudaError_t e = ev ? cudaEventRecordWithFlags(ev[0], s, flags) : cudaSuccess;
+  if (e == cudaSuccess) e = launch_small(h->h_desc[1], h->d_state + 1, h->small, s);
+  for (int i = 1; i < 4 && ev && e == cudaSuccess; ++i) e = cudaEventRecordWithFlags(ev[i], s, flags);
+  return e;
+}
+
 // Blocks of the step-level kernels (k_begin, k_resid64, k_mass: two points per thread).
 int step_blocks(const rd_pdhg* h) { return point_blocks(h->nx, h->ny * h->nz); }
 
@@ -386,9 +404,10 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   RD_CUDA(cudaGraphCreate(&g, 0));
   *out = g;
   cudaGraphConditionalHandle cond = 0;
-  RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  if (!h->small) RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
   const Desc dd = h->dc ? h->h_desc[1] : h->h_desc[0];
   auto iteration = [&](cudaStream_t st, cudaEvent_t* ev, bool first_it) {
+    if (h->small) return small_launch(h, st, ev);
     if (h->fch) return fch_iteration(h, st, ev);
     if (h->nd3) return h->dc ? launch_iteration3<float>(dd, sti, st, ev) : launch_iteration3<double>(dd, sti, st, ev);
     if (h->dc && dd.fused) return launch_fused<float>(dd, sti, h->cfg32, st, ev, first_it);
@@ -411,6 +430,11 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   // fused update: the per-band halo copies of U start at U_0 = d = 0
   if (dd.fused && (e = cudaMemsetAsync(h->halo32, 0, h->halo_bytes, cs)) != cudaSuccess)
     return abort_capture(cs, "clearing the halo copies during capture", e);
+  if (h->small) {
+    // the whole inner solve is one launch: no loop node
+    if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr, true)) != cudaSuccess)
+      return abort_capture(cs, "kernel launch during capture", e);
+  } else {
   if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr, true)) != cudaSuccess ||
       (e = launch_loop_cond(sti, cond, 1u, cs)) != cudaSuccess)
     return abort_capture(cs, "kernel launch during capture", e);
@@ -444,6 +468,7 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   cudaGraph_t body_out = nullptr;
   if ((e = cudaStreamEndCapture(h->body_stream, &body_out)) != cudaSuccess)
     return abort_capture(cs, "ending the loop body capture", e);
+  }
   if (h->dc) {
     e = launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, cs);
     if (e == cudaSuccess) e = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, cs);
@@ -469,9 +494,10 @@ rd_status capture_iter_graph(rd_pdhg* h, bool start, cudaGraph_t* graph, cudaGra
   RD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   if (fused && start) e = cudaMemsetAsync(h->halo32, 0, h->halo_bytes, cs);
-  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+  for (int k = 0; k < (h->small ? 1 : K) && e == cudaSuccess; ++k) {
     cudaEvent_t* ev = (k == 0 && h->opts.profile && (start || !fused)) ? h->ev : nullptr;
-    if (h->fch) e = fch_iteration(h, cs, ev);
+    if (h->small) e = small_launch(h, cs, ev);
+    else if (h->fch) e = fch_iteration(h, cs, ev);
     else if (h->nd3) e = h->dc ? launch_iteration3<float>(dd, h->d_state + 1, cs, ev)
                                : launch_iteration3<double>(dd, h->d_state + 0, cs, ev);
     else if (fused) e = launch_fused<float>(dd, h->d_state + 1, h->cfg32, cs, ev, start && k == 0);
@@ -491,7 +517,8 @@ rd_status capture_iter_graph(rd_pdhg* h, bool start, cudaGraph_t* graph, cudaGra
 
 rd_status capture_graphs(rd_pdhg* h) {
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
-  h->kernels_per_iter = h->fch ? (lc.transform ? 10 : 7)
+  h->kernels_per_iter = h->small ? 1
+                    : h->fch ? (lc.transform ? 10 : 7)
                     : h->nd3 ? (lc.transform ? 7 : 2)
                              : (h->dc && h->h_desc[1].fused ? 2 : (lc.transform ? 3 : 2));
   if (h->opts.profile)
@@ -586,6 +613,7 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
     if (o->fft_unrolled != 0 && o->fft_unrolled != 1) return fail(RD_ERR_INVALID_ARG, "fft_unrolled must be 0 or 1");
     if (o->autotune != 0 && o->autotune != 1) return fail(RD_ERR_INVALID_ARG, "autotune must be 0 or 1");
     if (o->fused_update != 0 && o->fused_update != 1) return fail(RD_ERR_INVALID_ARG, "fused_update must be 0 or 1");
+    if (o->small_solve != 0 && o->small_solve != 1) return fail(RD_ERR_INVALID_ARG, "small_solve must be 0 or 1");
     if (o->precision == RD_PREC_FP32_DC && o->dc_stall_window < 1)
       return fail(RD_ERR_INVALID_ARG, "dc_stall_window must be >= 1");
     if (o->upd_rows < 0 || o->band_rows < 0 || o->col_width < 0) return fail(RD_ERR_INVALID_ARG, "negative tile size");
@@ -1021,16 +1049,30 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
   if (std::max(lc.smem_res, std::max(lc.smem_col, lc.smem_upd)) > usable)
     return fail(RD_ERR_UNSUPPORTED, "the grid needs more shared memory per block than this device offers");
-  if (h->opts.autotune && !h->fch && !h->nd3 && h->opts.band_rows == 0 && h->opts.col_width == 0 && h->opts.upd_rows == 0) {
+  // FP32 defect correction on a grid whose whole inner solve fits one block: one launch per
+  // inner solve (no band / column tiles to plan or tune)
+  h->small = h->dc && !h->nd3 && !h->fch && transform && h->opts.small_solve
+                 ? small_mode(h->nx, h->ny, h->nc,
+                              rx->kind == RD_RX_NONE ? (op == RD_OP_NEG_BIHARMONIC ? KK_NONE_BIH : KK_NONE_LAP) : rx->kind,
+                              bc == RD_BC_NEUMANN, usable)
+                 : 0;
+  if (h->small) {
+    int dev = 0, optin = 0;
+    RD_CUDA(cudaGetDevice(&dev));
+    RD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    RD_CUDA(allow_small(optin));
+  }
+  if (h->opts.autotune && !h->fch && !h->nd3 && !h->small && h->opts.band_rows == 0 && h->opts.col_width == 0 && h->opts.upd_rows == 0) {
     const int stage_base = h->dc && (rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT);
     RD_TRY(h->dc ? autotune_plan<float>(h, H, transform, stage_base, usable)
                  : autotune_plan<double>(h, H, transform, stage_base, usable));
   }
-  if (h->dc && h->opts.fused_update && transform && !h->nd3) {
+  if (h->dc && h->opts.fused_update && transform && !h->nd3 && !h->small) {
     const int stage_base = rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT;
     RD_TRY(plan_fused(h, H, stage_base, usable));
   }
   h->stats.fused_update = h->h_desc[1].fused;
+  h->stats.small_solve = h->small;
   h->stats.plan_band_rows = h->h_desc[h->dc ? 1 : 0].band_rows;
   h->stats.plan_upd_rows = h->h_desc[h->dc ? 1 : 0].upd_rows;
   h->stats.plan_col_width = h->h_desc[h->dc ? 1 : 0].col_width;
@@ -1068,6 +1110,17 @@ rd_status graph_round(rd_pdhg* h, int which) {
     h->stats.kernel_launches += 2;  // k_begin, k_mass (the P_0 clear is a memset node)
   }
   h->stats.pdhg_iterations += updates;
+  if (h->small) {
+    // one launch of the one-block inner solve per round graph
+    h->stats.kernel_launches += 1;
+    if (h->opts.profile && sweeps > 0) {
+      float ms = 0.f;
+      RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+      h->stats.kernel_ms[0] += ms;
+      h->stats.kernel_samples[0] += 1;
+    }
+    return RD_OK;
+  }
   // every k_res launch (active or not) is followed by k_col and k_upd in the graph, and
   // k_loop_cond runs after the first and then after every graph_k of them
   h->stats.kernel_launches += (long long)sweeps * h->kernels_per_iter;
@@ -1102,9 +1155,18 @@ rd_status iter_round(rd_pdhg* h, int which, bool start) {
   RD_CUDA(cudaStreamSynchronize(s));
   const int updates = h->h_state[which].n - n_before;
   h->stats.graph_launches += 1;
-  h->stats.kernel_launches += (long long)h->opts.graph_k * h->kernels_per_iter + (first_graph ? 1 : 0);
+  h->stats.kernel_launches += h->small ? 1 : (long long)h->opts.graph_k * h->kernels_per_iter + (first_graph ? 1 : 0);
   h->stats.host_syncs += 1;
   h->stats.pdhg_iterations += updates;
+  if (h->small) {
+    if (h->opts.profile) {
+      float ms = 0.f;
+      RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+      h->stats.kernel_ms[0] += ms;
+      h->stats.kernel_samples[0] += 1;
+    }
+    return RD_OK;
+  }
   if (h->opts.profile && (first_graph || !h->hexec1)) {
     float ms = 0.f;
     RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
@@ -1242,6 +1304,7 @@ void rd_opts_default(rd_opts* o) {
   o->autotune = 0;
   o->dc_stall_window = kDcStallWindow;
   o->fused_update = 1;
+  o->small_solve = 1;
 }
 
 rd_status rd_pdhg_create(rd_pdhg** out, const rd_grid* grid, rd_bc bc, rd_operator op, const rd_reaction* reaction,
@@ -1438,9 +1501,10 @@ rd_status rd_pdhg_get_stats(const rd_pdhg* h, rd_stats* out) {
 rd_status rd_pdhg_reset_stats(rd_pdhg* h) {
   if (!h) return fail(RD_ERR_INVALID_ARG, "NULL handle");
   const int pb = h->stats.plan_band_rows, pc = h->stats.plan_col_width, pu = h->stats.plan_upd_rows;
-  const int fu = h->stats.fused_update;
+  const int fu = h->stats.fused_update, sm = h->stats.small_solve;
   h->stats = rd_stats{};
   h->stats.fused_update = fu;
+  h->stats.small_solve = sm;
   h->stats.plan_band_rows = pb;
   h->stats.plan_col_width = pc;
   h->stats.plan_upd_rows = pu;

@@ -216,12 +216,9 @@ __device__ __forceinline__ void load_desc(Desc& dst, const Desc* src) {
 // block call it): r <= threshold -> converged; non-finite or 1e8-fold growth -> diverged;
 // max_iter updates done -> not converged; otherwise count the coming update.  A batch member
 // hands control back to its slot's defect-correction loop when the solve stops.
-__device__ inline void finalize_measure(const Desc& d, State* st, double* red, Slot* slot = nullptr, int nblk = 0) {
-  __threadfence();
-  const int nb = nblk > 0 ? nblk : d.nbands;
-  double tot = 0.0;
-  for (int c = 0; c < d.ncomp; ++c) tot += sqrt(sum_partials(d.partials + c * nb, nb, red));
-  if (threadIdx.x != 0) return;
+// The stopping rule itself, from tot = sum_c ||F_c(U_n)|| (one thread; st may be a copy in shared
+// memory).
+__device__ inline void measure_decide(const Desc& d, State* st, double tot, Slot* slot) {
   const double meas = d.meas_div_dt ? tot / d.dt : tot;
   st->ticket = 0u;
   st->r = meas;
@@ -250,6 +247,15 @@ __device__ inline void finalize_measure(const Desc& d, State* st, double* red, S
     slot->inner_total += st->n;
     slot->phase = st->status == ST_DIVERGED ? PH_FAILED : PH_AXPY;
   }
+}
+
+__device__ inline void finalize_measure(const Desc& d, State* st, double* red, Slot* slot = nullptr, int nblk = 0) {
+  __threadfence();
+  const int nb = nblk > 0 ? nblk : d.nbands;
+  double tot = 0.0;
+  for (int c = 0; c < d.ncomp; ++c) tot += sqrt(sum_partials(d.partials + c * nb, nb, red));
+  if (threadIdx.x != 0) return;
+  measure_decide(d, st, tot, slot);
 }
 
 // Step set-up decision (thread 0 of the last block of a begin kernel): ||U^k|| = sqrt(tot), the

@@ -52,7 +52,7 @@ class rd_opts(ctypes.Structure):
                 ("upd_rows", ctypes.c_int),
                 ("profile", ctypes.c_int), ("fft_buffers", ctypes.c_int), ("solve_loop", ctypes.c_int),
                 ("fft_unrolled", ctypes.c_int), ("autotune", ctypes.c_int), ("dc_stall_window", ctypes.c_int),
-                ("fused_update", ctypes.c_int)]
+                ("fused_update", ctypes.c_int), ("small_solve", ctypes.c_int)]
 
 
 class rd_stats(ctypes.Structure):
@@ -61,7 +61,7 @@ class rd_stats(ctypes.Structure):
                 ("host_syncs", ctypes.c_longlong), ("kernel_ms", ctypes.c_double * 3),
                 ("kernel_samples", ctypes.c_longlong * 3), ("plan_band_rows", ctypes.c_int),
                 ("plan_col_width", ctypes.c_int), ("plan_upd_rows", ctypes.c_int),
-                ("fused_update", ctypes.c_int)]
+                ("fused_update", ctypes.c_int), ("small_solve", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -187,7 +187,8 @@ def _check(status, ok=(RD_OK,)):
 
 
 def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_inner_rtol=None,
-                 dc_max_outer=None, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1, autotune=0, upd_rows=0, dc_stall_window=None, fused_update=1):
+                 dc_max_outer=None, profile=0, fft_buffers=0, solve_loop="graph", fft_unrolled=1, autotune=0, upd_rows=0, dc_stall_window=None, fused_update=1,
+                 small_solve=1):
     """C structs for a ``workloads.Problem``."""
     g = rd_grid()
     nz = getattr(pb, "nz", 1)
@@ -224,12 +225,13 @@ def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_i
     if dc_stall_window is not None:
         o.dc_stall_window = dc_stall_window
     o.fused_update = fused_update
+    o.small_solve = small_solve
     return g, rx, pc, o
 
 
 class Solver:
     """One ``rd_pdhg`` handle for a ``workloads.Problem``; tensors are float64 CUDA tensors of
-    shape [ncomp, ny, nx] (contiguous)."""
+    the problem's shape ([ncomp, ny, nx], or [ncomp, nz, ny, nx] on 3-D grids; contiguous)."""
 
     def __init__(self, pb, precision="fp64", stream=None, **opts):
         import torch
@@ -325,12 +327,13 @@ class Batch:
     come back through ``poll``, final states in the host arrays returned by ``submit``."""
 
     def __init__(self, hbm_budget_bytes, max_slots, graph_k=8, max_iter=10000, dc_inner_rtol=None,
-                 dc_max_outer=None, stream=None):
+                 dc_max_outer=None, stream=None, small_solve=1):
         import torch
         lib = load()
         o = rd_opts()
         lib.rd_opts_default(ctypes.byref(o))
         o.graph_k, o.max_iter = graph_k, max_iter
+        o.small_solve = small_solve
         if dc_max_outer is not None:
             o.dc_max_outer = dc_max_outer
         if dc_inner_rtol is not None:

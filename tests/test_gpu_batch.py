@@ -200,3 +200,31 @@ def test_serving_mix_128_cubed_request_matches_plain_fp64():
     ids, results, outs, _ = _run([(pb, u0, n)])
     assert results[ids[0]]["status"] == 0
     assert np.linalg.norm(outs[ids[0]] - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("small", [1, 0])
+def test_small_slots_one_launch_inner_solves(small):
+    """Small 2-D slots (one block below 16 points a side, a cluster of eight blocks up to 16 K
+    points) run each inner solve in one launch beside the sweeps of the larger slots: every
+    result against the oracle, and a small request bit-identical alone and in the mix."""
+    reqs = _requests()
+    from paper_2305_03945_gb300 import rd
+    results = {}
+    with rd.Batch(1 << 30, 16, small_solve=small) as b:
+        ids = [b.submit(pb, u0, n, tag=k) for k, (pb, u0, n) in enumerate(reqs)]
+        t0 = time.time()
+        while len(results) < len(ids) and time.time() - t0 < 120:
+            for r in b.poll(timeout=1.0):
+                results[r["id"]] = r
+    for (rid, out), (pb, u0, n) in zip(ids, reqs):
+        r = results[rid]
+        assert r["status"] == 0 and r["steps"] == n, r
+        U_ref, _ = O.solve(pb, u0, n)
+        assert np.linalg.norm(out - U_ref) <= 1e-9 * np.linalg.norm(U_ref), (pb.kind, pb.nx, pb.ny)
+    probe = reqs[0]  # 64^2: the cluster form
+    with rd.Batch(1 << 30, 16, small_solve=small) as b:
+        pid, pout = b.submit(*probe)
+        res = []
+        while not res:
+            res = b.poll(timeout=5.0)
+    assert np.array_equal(pout, ids[0][1]) and res[0]["iterations"] == results[ids[0][0]]["iterations"]
