@@ -302,10 +302,12 @@ RD_API void rd_pdhg_destroy(rd_pdhg *h);
 
 /* ---------------------------------------------------------------------------------------
  * Batched, continuously served solves (no counterpart in the paper: a serving layer over the
- * same method).  Every request is an independent run of nsteps implicit steps of one scalar
- * equation (RD_RX_NONE, Allen-Cahn or Cahn-Hilliard; 2-D, sides powers of two in [4, 1024],
- * either boundary condition) solved with FP32 PDHG sweeps inside FP64 defect correction to the
- * request's tolerance.  The batch owns one device arena of hbm_budget_bytes; a request is
+ * same method).  Every request is an independent run of nsteps implicit steps of one equation
+ * (RD_RX_NONE, Allen-Cahn, Cahn-Hilliard, Gray-Scott or Schnakenberg; 2-D grids with sides powers
+ * of two in [4, 1024], or -- scalar kinds -- 3-D grids with sides in [4, 512]; either boundary
+ * condition) solved with FP32 PDHG sweeps inside FP64 defect correction to the request's
+ * tolerance.  Small 2-D requests (up to 16 K points) run each inner solve in one launch
+ * (rd_opts.small_solve).  The batch owns one device arena of hbm_budget_bytes; a request is
  * admitted when a slot is free and its workspace (about 48 bytes per grid point) fits the
  * arena, its state then stays resident on the GPU across all its steps, and all admitted
  * requests advance together in shared launches (one per equation kind and sweep kernel, over

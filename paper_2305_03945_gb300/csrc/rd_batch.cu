@@ -248,8 +248,8 @@ constexpr int kBatchMaxSide3 = 512;     // 3-D batch grids: sides 4 .. 512
 constexpr int kBatchMaxBlk3 = 2 * 152;  // blocks per 3-D slot (plan3's cap)
 constexpr int kBatchBandRows = 4;
 constexpr int kBatchColWidth = 4;
-constexpr int kBatchGroups = 5;         // scalar equation kinds served
-const int kGroupKey[kBatchGroups] = {KK_NONE_LAP, KK_AC, KK_CH_IMPL, KK_CH_SPLIT, KK_NONE_BIH};
+constexpr int kBatchGroups = 7;         // equation kinds served
+const int kGroupKey[kBatchGroups] = {KK_NONE_LAP, KK_AC, KK_CH_IMPL, KK_CH_SPLIT, KK_NONE_BIH, KK_GS, KK_SCHNAK};
 
 double now_s() {
   using namespace std::chrono;
@@ -387,6 +387,7 @@ struct rd_batch {
   cudaGraphExec_t gexec = nullptr;
   bool graph_dirty = true;
   int smem_sweep = 0;
+  int smem_sweep2 = 0;  // the band kernels of the two-species kinds
   // queues
   std::mutex mu;
   std::condition_variable cv;
@@ -452,7 +453,7 @@ template <int K>
 void launch_group(rd_batch* b, int g, cudaStream_t s) {
   const int np = b->n_phase[g], nb = b->n_band[g], ncl = b->n_col[g];
   if (np == 0) return;
-  const int smem_res = b->smem_sweep, smem_col = b->smem_sweep;
+  const int smem_res = KT<K>::two ? b->smem_sweep2 : b->smem_sweep, smem_col = b->smem_sweep;
   k_axpy_b<<<np, 256, 0, s>>>(b->d_d64, b->d_slots, b->d_phase_items[g]);
   k_step_b<K><<<np, 256, 0, s>>>(b->d_d64, b->d_slots, b->d_phase_items[g]);
   const bool fork = b->n_small[g][0] + b->n_small[g][1] > 0;
@@ -480,6 +481,8 @@ void launch_iteration_all(rd_batch* b, cudaStream_t s) {
       case KK_AC: launch_group<KK_AC>(b, g, s); break;
       case KK_CH_IMPL: launch_group<KK_CH_IMPL>(b, g, s); break;
       case KK_CH_SPLIT: launch_group<KK_CH_SPLIT>(b, g, s); break;
+      case KK_GS: launch_group<KK_GS>(b, g, s); break;
+      case KK_SCHNAK: launch_group<KK_SCHNAK>(b, g, s); break;
       default: launch_group<KK_NONE_BIH>(b, g, s); break;
     }
     if (b->n_items3[g]) {
@@ -549,7 +552,7 @@ rd_status rebuild_items(rd_batch* b) {
       const int m = sh.small - 1;
       b->h_small[sh.group][m].push_back(make_int2(s, 0));
       b->smem_small[sh.group][m] = std::max(
-          b->smem_small[sh.group][m], small_smem_of(sh.small, d.nx, d.ny, 1, sh.key, d.bc == BC_NEUMANN));
+          b->smem_small[sh.group][m], small_smem_of(sh.small, d.nx, d.ny, d.ncomp, sh.key, d.bc == BC_NEUMANN));
       continue;
     }
     for (int band = 0; band < sh.d32.nbands; ++band) b->h_band[sh.group].push_back(make_int2(s, band));
@@ -796,8 +799,9 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   d.omega = b->opts.omega;
   d.batched = 1;
   d.partials = parts;
+  const bool two = r.reaction.kind == RD_RX_GRAY_SCOTT || r.reaction.kind == RD_RX_SCHNAKENBERG;
   for (int c = 0; c < 2; ++c) {
-    const double D = r.reaction.a;
+    const double D = two ? r.reaction.p[c] : r.reaction.a;  // two species: each its own diffusivity
     d.gc1[c] = r.op == RD_OP_LAPLACIAN ? D * r.dt : 0.0;
     d.gc2[c] = r.op == RD_OP_LAPLACIAN ? 0.0 : r.reaction.a * r.dt;
   }
@@ -833,7 +837,7 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   sh.d32 = d32;
   sh.d64 = d64;
   // small grids: each inner solve in one launch (one block, or a cluster of eight)
-  sh.small = b->opts.small_solve ? small_mode(nx, ny, 1, sh.key, r.bc == RD_BC_NEUMANN, b->smem_usable) : 0;
+  sh.small = b->opts.small_solve ? small_mode(nx, ny, nc, sh.key, r.bc == RD_BC_NEUMANN, b->smem_usable) : 0;
   // tables, state, control block
   std::vector<float> tw, dc, mu, all_t, all_mu;
   host_tables(nx, r.bc == RD_BC_NEUMANN, hx, tw, dc, mu);
@@ -1039,7 +1043,11 @@ rd_status rd_batch_create(rd_batch** out, size_t hbm_budget_bytes, int max_slots
   if ((e = batch3_allow(optin)) != cudaSuccess || (e = allow_small(optin)) != cudaSuccess)
     return cleanup(bfail(RD_ERR_CUDA, cudaGetErrorString(e)));
   b->smem_usable = optin - 1024;
-  if ((e = allow_batch_kernels<float, KK_NONE_LAP>(optin)) != cudaSuccess ||
+  b->smem_sweep2 = std::max(res_smem_bytes<float>(2, kBatchBandRows, 1, kBatchMaxSide, 0, 0, tabs),
+                            lines_smem_bytes<float>(2 * ((kBatchBandRows + 2) / 2), kBatchMaxSide, 0, tabs));
+  if ((e = allow_batch_kernels<float, KK_GS>(optin)) != cudaSuccess ||
+      (e = allow_batch_kernels<float, KK_SCHNAK>(optin)) != cudaSuccess ||
+      (e = allow_batch_kernels<float, KK_NONE_LAP>(optin)) != cudaSuccess ||
       (e = allow_batch_kernels<float, KK_AC>(optin)) != cudaSuccess ||
       (e = allow_batch_kernels<float, KK_CH_IMPL>(optin)) != cudaSuccess ||
       (e = allow_batch_kernels<float, KK_CH_SPLIT>(optin)) != cudaSuccess ||
@@ -1071,8 +1079,11 @@ rd_status rd_batch_submit(rd_batch* b, const rd_request* req, double* u_out_host
   if (r.bc != RD_BC_PERIODIC && r.bc != RD_BC_NEUMANN) return bfail(RD_ERR_INVALID_ARG, "bad boundary condition");
   if (r.reaction.kind == RD_RX_FCH || r.op == RD_OP_FUNCTIONALIZED)
     return bfail(RD_ERR_UNSUPPORTED, "batch: the sixth-order equation is not batched");
-  if (r.reaction.ncomp != 1 || group_of(key_of(r)) < 0)
-    return bfail(RD_ERR_UNSUPPORTED, "batch: scalar kinds only (none, Allen-Cahn, Cahn-Hilliard)");
+  const bool two = r.reaction.kind == RD_RX_GRAY_SCOTT || r.reaction.kind == RD_RX_SCHNAKENBERG;
+  if (group_of(key_of(r)) < 0) return bfail(RD_ERR_UNSUPPORTED, "batch: kind not served");
+  if (r.reaction.ncomp != (two ? 2 : 1)) return bfail(RD_ERR_INVALID_ARG, "ncomp does not match the reaction kind");
+  if (two && r.grid.ndim == 3) return bfail(RD_ERR_UNSUPPORTED, "batch: 3-D grids are served for the scalar kinds");
+  if (two && r.op != RD_OP_LAPLACIAN) return bfail(RD_ERR_INVALID_ARG, "two species need RD_OP_LAPLACIAN");
   if (r.op != RD_OP_LAPLACIAN && r.op != RD_OP_NEG_BIHARMONIC) return bfail(RD_ERR_INVALID_ARG, "bad operator");
   if (r.reaction.kind == RD_RX_ALLEN_CAHN && r.op != RD_OP_LAPLACIAN)
     return bfail(RD_ERR_INVALID_ARG, "Allen-Cahn needs RD_OP_LAPLACIAN");

@@ -112,6 +112,8 @@ cudaError_t launch_small_batch(int key, int mode, const Desc* descs, Slot* slots
       case KK_CH_IMPL: k_small_cl_b<KK_CH_IMPL><<<g, kSmallThreads, smem, s>>>(descs, slots, items); break;
       case KK_CH_SPLIT: k_small_cl_b<KK_CH_SPLIT><<<g, kSmallThreads, smem, s>>>(descs, slots, items); break;
       case KK_NONE_BIH: k_small_cl_b<KK_NONE_BIH><<<g, kSmallThreads, smem, s>>>(descs, slots, items); break;
+      case KK_GS: k_small_cl_b<KK_GS><<<g, kSmallThreads, smem, s>>>(descs, slots, items); break;
+      case KK_SCHNAK: k_small_cl_b<KK_SCHNAK><<<g, kSmallThreads, smem, s>>>(descs, slots, items); break;
       default: return cudaErrorNotSupported;
     }
     return cudaGetLastError();
@@ -122,6 +124,8 @@ cudaError_t launch_small_batch(int key, int mode, const Desc* descs, Slot* slots
     case KK_CH_IMPL: k_small_b<KK_CH_IMPL><<<nitems, kSmallThreads, smem, s>>>(descs, slots, items); break;
     case KK_CH_SPLIT: k_small_b<KK_CH_SPLIT><<<nitems, kSmallThreads, smem, s>>>(descs, slots, items); break;
     case KK_NONE_BIH: k_small_b<KK_NONE_BIH><<<nitems, kSmallThreads, smem, s>>>(descs, slots, items); break;
+    case KK_GS: k_small_b<KK_GS><<<nitems, kSmallThreads, smem, s>>>(descs, slots, items); break;
+    case KK_SCHNAK: k_small_b<KK_SCHNAK><<<nitems, kSmallThreads, smem, s>>>(descs, slots, items); break;
     default: return cudaErrorNotSupported;
   }
   return cudaGetLastError();
@@ -152,7 +156,11 @@ cudaError_t allow_small(int optin) {
   if ((e = allow_k(k_small_cl_b<KK_AC>, optin)) != cudaSuccess) return e;
   if ((e = allow_k(k_small_cl_b<KK_CH_IMPL>, optin)) != cudaSuccess) return e;
   if ((e = allow_k(k_small_cl_b<KK_CH_SPLIT>, optin)) != cudaSuccess) return e;
-  return allow_k(k_small_cl_b<KK_NONE_BIH>, optin);
+  if ((e = allow_k(k_small_cl_b<KK_NONE_BIH>, optin)) != cudaSuccess) return e;
+  if ((e = allow_k(k_small_b<KK_GS>, optin)) != cudaSuccess) return e;
+  if ((e = allow_k(k_small_b<KK_SCHNAK>, optin)) != cudaSuccess) return e;
+  if ((e = allow_k(k_small_cl_b<KK_GS>, optin)) != cudaSuccess) return e;
+  return allow_k(k_small_cl_b<KK_SCHNAK>, optin);
 }
 
 }  // namespace rd

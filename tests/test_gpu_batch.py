@@ -228,3 +228,41 @@ def test_small_slots_one_launch_inner_solves(small):
         while not res:
             res = b.poll(timeout=5.0)
     assert np.array_equal(pout, ids[0][1]) and res[0]["iterations"] == results[ids[0][0]]["iterations"]
+
+
+def _requests2():
+    """Two-species requests (Gray-Scott periodic, Schnakenberg Neumann, Section 3.4.1) of uneven
+    sizes, small ones included (one-launch inner solves)."""
+    out = []
+    for k, (kind, p, bc, ny, nx, dt) in enumerate([
+        ("gray_scott", (2e-3, 1e-3, 0.04, 0.06), "periodic", 64, 64, 1.0),
+        ("schnakenberg", (0.05, 1.0, 100.0, 0.1305, 0.7695), "neumann", 128, 128, 1 / 5000),
+        ("gray_scott", (2e-3, 1e-3, 0.04, 0.06), "neumann", 256, 128, 1.0),
+        ("schnakenberg", (0.05, 1.0, 100.0, 0.1305, 0.7695), "periodic", 8, 8, 1 / 5000),
+    ]):
+        pb = WL.Problem(nx=nx, ny=ny, lx=1.0, ly=1.0, bc=bc, op="laplacian", kind=kind, p=p, dt=dt,
+                        tau_u=0.9, tau_p=0.9, tol=1e-11, tol_kind="f_rel")
+        r = WL.rng(110 + k)
+        if kind == "gray_scott":
+            u0 = np.stack([1 - 0.5 * r.random((ny, nx)), 0.25 * r.random((ny, nx))])
+        else:
+            u0 = 0.9 + 0.1 * r.random(pb.shape)
+        out.append((pb, u0, 3))
+    return out
+
+
+def test_two_species_requests_in_the_batch():
+    """Gray-Scott and Schnakenberg requests beside scalar ones: each against the oracle
+    (<= 1e-9 rel. L2), and one bit-identical alone and in the mix."""
+    reqs = _requests2() + _requests()[:2]
+    ids, results, outs, stats = _run(reqs)
+    assert len(results) == len(reqs)
+    for rid, (pb, u0, n) in zip(ids, reqs):
+        r = results[rid]
+        assert r["status"] == 0 and r["steps"] == n, r
+        U_ref, _ = O.solve(pb, u0, n)
+        err = np.linalg.norm(outs[rid] - U_ref) / np.linalg.norm(U_ref)
+        assert err <= 1e-9, (pb.kind, pb.bc, pb.ny, pb.nx, err)
+    _, res_alone, out_alone, _ = _run([reqs[2]])
+    assert np.array_equal(next(iter(out_alone.values())), outs[ids[2]])
+    assert next(iter(res_alone.values()))["iterations"] == results[ids[2]]["iterations"]
