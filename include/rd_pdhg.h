@@ -345,8 +345,11 @@ typedef struct {
 } rd_batch_stats;
 
 /* Create a batch: arena of hbm_budget_bytes (allocated here, once), at most max_slots requests
- * resident at a time, solver options (graph_k, max_iter, dc_inner_rtol, dc_max_outer, omega;
- * NULL = defaults), work issued on cuda_stream.  Starts the library's scheduling thread. */
+ * resident at a time, solver options (graph_k, max_iter, dc_inner_rtol, dc_max_outer, omega,
+ * small_solve, autotune; NULL = defaults), work issued on cuda_stream.  With autotune = 1 the
+ * band rows and column width of the batched sweeps are measured here for every square grid size
+ * the arena holds (16 .. 1024, a few milliseconds) and admitted requests take the fastest for
+ * their size.  Starts the library's scheduling thread. */
 RD_API rd_status rd_batch_create(rd_batch **out, size_t hbm_budget_bytes, int max_slots,
                                  const rd_opts *opts, void *cuda_stream);
 

@@ -341,7 +341,7 @@ size_t slot_bytes(const rd_request& r, size_t* npts_out) {
   b += Arena::up(npts * 4) * 6;                       // d, P0, P1, WY, r32, u32
   b += Arena::up((size_t)(nx + ny) * 2 * 8) * 1;      // twiddles + rotations (FP32 complex)
   b += Arena::up((size_t)(nx + ny) * 4);              // mu tables
-  b += Arena::up((size_t)2 * (ny / kBatchBandRows + 1) * 8);  // partials
+  b += Arena::up((size_t)2 * (ny / 2 + 1) * 8);  // partials (two-row bands at the finest tile)
   return b;
 }
 
@@ -388,6 +388,8 @@ struct rd_batch {
   bool graph_dirty = true;
   int smem_sweep = 0;
   int smem_sweep2 = 0;  // the band kernels of the two-species kinds
+  // measured tiles per grid size (index log2 of the longer side; 0 = not measured)
+  int tune_band[16] = {}, tune_col[16] = {};
   // queues
   std::mutex mu;
   std::condition_variable cv;
@@ -770,7 +772,7 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   float* u32 = (float*)take(npts * 4);
   float* tabs = (float*)take((size_t)(nx + ny) * 2 * 8);
   float* mus = (float*)take((size_t)(nx + ny) * 4);
-  double* parts = (double*)take((size_t)2 * (ny / kBatchBandRows + 1) * 8);
+  double* parts = (double*)take((size_t)2 * (ny / 2 + 1) * 8);
   const double hx = r.grid.length[0] / nx, hy = r.grid.length[1] / ny;
   // descriptors
   Desc d{};
@@ -784,9 +786,11 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   d.kind = r.reaction.kind;
   d.precond = 1;
   d.mode = MODE_PDHG;
-  d.band_rows = std::min(kBatchBandRows, ny);
+  // tiles: the measured best for this grid size (opts.autotune), else 4-row bands, 4 columns
+  const int lg = ilog2i(std::max(nx, ny));
+  d.band_rows = std::min(b->tune_band[lg] ? b->tune_band[lg] : kBatchBandRows, ny);
   d.nbands = (ny + d.band_rows - 1) / d.band_rows;
-  d.col_width = std::min(kBatchColWidth, nx);
+  d.col_width = std::min(b->tune_col[lg] ? b->tune_col[lg] : kBatchColWidth, nx);
   d.ncolblk = nx / d.col_width;
   d.hx2 = 1.0 / (hx * hx);
   d.hy2 = 1.0 / (hy * hy);
@@ -916,6 +920,116 @@ void retire(rd_batch* b, int s, const Slot& ctl) {
   if (!copy_error.empty()) b->worker_error = copy_error;
   b->done.push_back(res);
   b->cv.notify_all();
+}
+
+// opts.autotune: for each square grid size the arena can hold, admit one scratch Allen-Cahn slot
+// whose inner solve never stops, time graph-free launches of its three sweep kernels over 8
+// iterations (best of three) for band rows {2, 4} x column widths {2, 4}, and keep the fastest
+// per size; admission then takes the measured tiles.  Every candidate fits the launches' shared
+// memory (sized for 4-row bands and 4 columns).
+rd_status tune_batch_tiles(rd_batch* b) {
+  cudaStream_t st = b->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return bfail(RD_ERR_CUDA, "tile tuning: events");
+  const int g = group_of(KK_AC);
+  rd_status res = RD_OK;
+  for (int lg = 4; lg <= ilog2i(kBatchMaxSide) && res == RD_OK; ++lg) {
+    const int n = 1 << lg;
+    Request q;
+    q.req.grid.ndim = 2;
+    q.req.grid.n[0] = q.req.grid.n[1] = n;
+    q.req.grid.length[0] = q.req.grid.length[1] = 1.0;
+    q.req.bc = RD_BC_PERIODIC;
+    q.req.op = RD_OP_LAPLACIAN;
+    q.req.reaction.kind = RD_RX_ALLEN_CAHN;
+    q.req.reaction.ncomp = 1;
+    q.req.reaction.a = 0.05;
+    q.req.reaction.b = 20.0;
+    q.req.dt = 2e-3;
+    q.req.tau = q.req.sigma = 1.0;
+    q.req.tol = 1e-11;
+    q.req.tol_kind = RD_TOL_F_REL;
+    q.req.nsteps = 1;
+    q.u0.assign((size_t)n * n, 0.0);
+    rd_status err = RD_OK;
+    const int small_opt = b->opts.small_solve;
+    b->opts.small_solve = 0;  // time the sweeps, not the one-launch solve
+    const bool ok = admit(b, q, &err);
+    b->opts.small_solve = small_opt;
+    if (!ok) break;  // the arena holds no larger grid
+    int s = -1;
+    for (int k = 0; k < b->max_slots; ++k)
+      if (b->slots[k].used) s = k;
+    SlotHost& sh = b->slots[s];
+    const size_t npts = sh.npts;
+    // base state and right-hand side nonzero, d = P = 0, an inner solve that never stops
+    cudaMemsetAsync(const_cast<void*>(sh.d32.rhs), 0x3f, npts * 4, st);
+    cudaMemsetAsync(const_cast<void*>(sh.d32.base), 0x3f, npts * 4, st);
+    cudaMemsetAsync(sh.d32.X, 0, npts * 4, st);
+    cudaMemsetAsync(sh.d32.P[0], 0, npts * 4, st);
+    cudaMemsetAsync(sh.d32.P[1], 0, npts * 4, st);
+    float best = 1e30f;
+    int bb = kBatchBandRows, bc = kBatchColWidth;
+    for (int band : {2, 4})
+      for (int cw : {2, 4}) {
+        if (band > n || cw > n) continue;
+        Desc d32 = sh.d32, d64 = sh.d64;
+        d32.band_rows = d64.band_rows = band;
+        d32.nbands = d64.nbands = (n + band - 1) / band;
+        d32.col_width = d64.col_width = cw;
+        d32.ncolblk = d64.ncolblk = n / cw;
+        std::vector<int2> bands, cols;
+        for (int k = 0; k < d32.nbands; ++k) bands.push_back(make_int2(s, k));
+        for (int k = 0; k < d32.ncolblk; ++k) cols.push_back(make_int2(s, k));
+        Slot ctl{};
+        ctl.phase = PH_INNER;
+        ctl.inner.status = ST_ACTIVE;
+        ctl.inner.max_iter = 1 << 30;
+        ctl.inner.thresh = 0.0;
+        ctl.inner.stall_mul = 1 << 20;
+        cudaMemcpyAsync(b->d_d32 + s, &d32, sizeof(Desc), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(b->d_d64 + s, &d64, sizeof(Desc), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(b->d_slots + s, &ctl, sizeof(Slot), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(b->d_band_items[g], bands.data(), bands.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(b->d_col_items[g], cols.data(), cols.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+        float t_best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, st);
+          for (int it = 0; it < 8; ++it) {
+            k_res_b<float, KK_AC><<<(int)bands.size(), kBatchThreads, b->smem_sweep, st>>>(b->d_d32, b->d_slots, b->d_band_items[g]);
+            k_col_b<float><<<(int)cols.size(), kBatchThreads, b->smem_sweep, st>>>(b->d_d32, b->d_slots, b->d_col_items[g]);
+            k_upd_b<float, KK_AC><<<(int)bands.size(), kBatchThreads, b->smem_sweep, st>>>(b->d_d32, b->d_slots, b->d_band_items[g]);
+          }
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            res = bfail(RD_ERR_CUDA, std::string("tile tuning: ") + cudaGetErrorString(cudaGetLastError()));
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          t_best = std::min(t_best, ms);
+        }
+        if (res != RD_OK) break;
+        if (t_best < best) {
+          best = t_best;
+          bb = band;
+          bc = cw;
+        }
+      }
+    b->tune_band[lg] = bb;
+    b->tune_col[lg] = bc;
+    // release the scratch slot
+    b->arena.release(sh.mem, sh.mem_bytes);
+    Slot idle{};
+    cudaMemcpyAsync(b->d_slots + s, &idle, sizeof(Slot), cudaMemcpyHostToDevice, st);
+    sh = SlotHost{};
+    b->stats.admitted -= 1;
+  }
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return res;
 }
 
 void worker_loop(rd_batch* b) {
@@ -1059,6 +1173,10 @@ rd_status rd_batch_create(rd_batch** out, size_t hbm_budget_bytes, int max_slots
     cudaFuncSetAttribute(k_col_b<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(bfail(RD_ERR_CUDA, cudaGetErrorString(e)));
+  if (b->opts.autotune) {
+    const rd_status ts = tune_batch_tiles(b);
+    if (ts != RD_OK) return cleanup(ts);
+  }
   b->worker = std::thread(worker_loop, b);
   *out = b;
   return RD_OK;

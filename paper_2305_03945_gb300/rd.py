@@ -327,13 +327,14 @@ class Batch:
     come back through ``poll``, final states in the host arrays returned by ``submit``."""
 
     def __init__(self, hbm_budget_bytes, max_slots, graph_k=8, max_iter=10000, dc_inner_rtol=None,
-                 dc_max_outer=None, stream=None, small_solve=1):
+                 dc_max_outer=None, stream=None, small_solve=1, autotune=1):
         import torch
         lib = load()
         o = rd_opts()
         lib.rd_opts_default(ctypes.byref(o))
         o.graph_k, o.max_iter = graph_k, max_iter
         o.small_solve = small_solve
+        o.autotune = autotune
         if dc_max_outer is not None:
             o.dc_max_outer = dc_max_outer
         if dc_inner_rtol is not None:

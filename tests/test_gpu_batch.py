@@ -266,3 +266,25 @@ def test_two_species_requests_in_the_batch():
     _, res_alone, out_alone, _ = _run([reqs[2]])
     assert np.array_equal(next(iter(out_alone.values())), outs[ids[2]])
     assert next(iter(res_alone.values()))["iterations"] == results[ids[2]]["iterations"]
+
+
+def test_autotuned_batch_tiles_give_the_same_results():
+    """Tiles measured at batch creation (autotune) only change the launch shape: every result
+    still agrees with the oracle, and with the fixed-tile batch to the step tolerance."""
+    from paper_2305_03945_gb300 import rd
+    reqs = _requests()
+    outs = {}
+    for tune in (0, 1):
+        results = {}
+        with rd.Batch(1 << 30, 16, autotune=tune) as b:
+            ids = [b.submit(pb, u0, n) for pb, u0, n in reqs]
+            t0 = time.time()
+            while len(results) < len(ids) and time.time() - t0 < 120:
+                for r in b.poll(timeout=1.0):
+                    results[r["id"]] = r
+        assert all(r["status"] == 0 for r in results.values())
+        outs[tune] = [o for _, o in ids]
+    for (pb, u0, n), a, t in zip(reqs, outs[0], outs[1]):
+        U_ref, _ = O.solve(pb, u0, n)
+        assert np.linalg.norm(t - U_ref) <= 1e-9 * np.linalg.norm(U_ref)
+        assert np.linalg.norm(t - a) <= 1e-9 * np.linalg.norm(U_ref)
