@@ -31,8 +31,8 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
-WORKLOADS = ("allen_cahn_neumann_1024", "cahn_hilliard_split_512", "gray_scott_2048", "allen_cahn_periodic_64",
-             "fch_128")
+WORKLOADS = ("gray_scott_2048", "allen_cahn_neumann_1024", "cahn_hilliard_split_512", "allen_cahn_periodic_64",
+             "allen_cahn_periodic_128x3", "fch_128")
 
 
 def workload(name):
@@ -47,6 +47,8 @@ def workload(name):
         return WL.config_allen_cahn_periodic()
     if name == "fch_128":
         return WL.config_fch(128)
+    if name == "allen_cahn_periodic_128x3":
+        return WL.config_allen_cahn_periodic_3d()
     raise SystemExit("unknown workload " + name)
 
 
@@ -133,7 +135,13 @@ def kernel_bytes(pb, precision):
     the spectrum once; k_upd reads Y, P, the unknown (and the base state) and writes the
     unknown and P."""
     es = 4 if precision == "fp32_dc" else 8
-    npts = pb.ncomp * pb.nx * pb.ny
+    npts = pb.ncomp * pb.nx * pb.ny * getattr(pb, "nz", 1)
+    if getattr(pb, "nz", 1) > 1:
+        # 3-D: the residual reads the unknown, base state and rhs and writes W; the five transform
+        # passes read and write the array (the last also reads and writes P); the update reads
+        # P~, the unknown and the base state and writes the unknown
+        base3 = 1 if precision == "fp32_dc" else 0
+        return {"k3_res": (3 + base3) * es * npts, "k3_lines": 12 * es * npts, "k3_upd": (3 + base3) * es * npts}
     if pb.kind == "fch":
         # sixth-order equation (FP64 stencil chains): residual mu, A mu, F = 2 + 3 + 4 touches;
         # preconditioner-only transforms 2 + 2 + 2; update dual, Lap P~, A Lap P~, U = 4 + 2 + 3 + 6
@@ -141,8 +149,20 @@ def kernel_bytes(pb, precision):
     base = 1 if (precision == "fp32_dc" and pb.kind != "none") else 0
     # k_updres (fused update): k_upd's touches plus the right-hand side read and the transformed
     # residual written (the unknown is read and written once for both)
+    # k_small*: the one-launch inner solve reads d, u, r, P and writes d once per launch
     return {"k_res": (3 + base) * es * npts, "k_col": 2 * es * npts, "k_upd": (5 + base) * es * npts,
-            "k_updres": (7 + base) * es * npts}
+            "k_updres": (7 + base) * es * npts, "k_small": 5 * es * npts, "k_small_cluster": 5 * es * npts}
+
+
+def kernel_names(pb, st):
+    """Names of the kernels behind rd_stats.kernel_ms[0..2] for this problem and handle."""
+    if st.get("small_solve"):
+        return ("k_small_cluster" if st["small_solve"] == 2 else "k_small",)
+    if pb.kind == "fch":
+        return ("fch_residual", "precond", "fch_update")
+    if getattr(pb, "nz", 1) > 1:
+        return ("k3_res", "k3_lines", "k3_upd")
+    return ("k_res", "k_col", "k_updres" if st.get("fused_update") else "k_upd")
 
 
 # the files that define each profiled kernel: a traffic figure stays valid while they are unchanged
@@ -214,7 +234,7 @@ def run_reference(args, rank, world):
         return 0
     w = workload(args.workload)
     pb = w.problem
-    npts = pb.ncomp * pb.nx * pb.ny
+    npts = pb.ncomp * pb.nx * pb.ny * pb.nz
     iters = args.ref_iters if args.ref_iters > 0 else cpu_sample_iters(pb, w.u0, 0, 4.0)
     for _ in range(args.warmup):
         oracle_iterations(pb, w.u0, iters, 0)
@@ -334,7 +354,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = workload(args.workload)
     pb = w.problem
-    npts = pb.ncomp * pb.nx * pb.ny
+    npts = pb.ncomp * pb.nx * pb.ny * pb.nz
     dist = world > 1
 
     def barrier():
@@ -388,9 +408,7 @@ def run_ours(args, rank, world, local_rank):
     # per-kernel roofline from the live CUDA-event samples
     peak, peak_kind = load_peaks()
     kb = kernel_bytes(pb, args.precision)
-    names = ("k_res", "k_col", "k_updres" if st.get("fused_update") else "k_upd")
-    if pb.kind == "fch":
-        names = ("fch_residual", "precond", "fch_update")
+    names = kernel_names(pb, st)
     per = {}
     for i, nm in enumerate(names):
         n = st["kernel_samples"][i]
@@ -454,7 +472,7 @@ def run_ours(args, rank, world, local_rank):
         st64 = sv64.stats()
         kb64 = kernel_bytes(pb, "fp64")
         per64 = {}
-        for i, nm in enumerate(("k_res", "k_col", "k_updres" if st64.get("fused_update") else "k_upd")):
+        for i, nm in enumerate(kernel_names(pb, st64)):
             n = st64["kernel_samples"][i]
             if n:
                 a = st64["kernel_ms"][i] / n
@@ -512,7 +530,9 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "fp32_dc" else "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "grid": "%dx%dx%d" % (pb.ncomp, pb.ny, pb.nx), "bc": pb.bc,
+        "config": {"workload": args.workload,
+                   "grid": ("%dx%dx%dx%d" % (pb.ncomp, pb.nz, pb.ny, pb.nx)) if pb.nz > 1 else ("%dx%dx%d" % (pb.ncomp, pb.ny, pb.nx)),
+                   "bc": pb.bc,
                    "kind": pb.kind, "dt": pb.dt, "tol": "%s %g" % (pb.tol_kind, pb.tol),
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (256 MiB write)",
@@ -525,7 +545,7 @@ def run_ours(args, rank, world, local_rank):
                    "graph_k": args.graph_k,
                    "fft_buffers": args.fft_buffers, "solve_loop": args.solve_loop,
                    "dc_inner_rtol": args.dc_inner_rtol, "dc_stall_window": args.dc_stall_window,
-                   "fused_update": st.get("fused_update", 0),
+                   "fused_update": st.get("fused_update", 0), "small_solve": st.get("small_solve", 0),
                    "fft_unrolled": args.fft_unrolled},
         "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "parity_full_size": parity, "fp64_plain": fp64,
         "adaptive": adaptive, "serving": serving,
@@ -570,7 +590,7 @@ def adaptive_leg(pb, w, args, dev, stream, its_per_step):
             "t_reached": t_reached, "attempts": len(log), "accepted": len(acc), "rejected": len(log) - len(acc),
             "dt_min": min(dts) if dts else None, "dt_max": max(dts) if dts else None,
             "step_size_changes": sum(1 for a, b in zip(log, log[1:]) if a["dt"] != b["dt"]),
-            "wall_s": wall, "value": pb.ncomp * pb.nx * pb.ny * its / wall / 1e9, "unit": "Gpoint-iter/s",
+            "wall_s": wall, "value": pb.ncomp * pb.nx * pb.ny * pb.nz * its / wall / 1e9, "unit": "Gpoint-iter/s",
             "set_dt_ms": set_dt_ms}
 
 

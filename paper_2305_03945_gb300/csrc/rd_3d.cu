@@ -184,7 +184,7 @@ template cudaError_t allow3<double>(int);
 
 bool plan3(int nx, int ny, int nz, int nc, int elem_bytes, bool neumann, int smem_limit, Desc& d, const char** why) {
   const size_t npts = (size_t)nx * ny * nz;
-  d.blk3 = (int)std::max<size_t>(1, std::min<size_t>(2 * 152, (npts + 2047) / 2048));
+  d.blk3 = (int)std::max<size_t>(1, std::min<size_t>(1024, (npts + 2047) / 2048));
   const int n_ax[3] = {nx, ny, nz};
   const int lanes = elem_bytes == 4 ? 16 : 8;
   // lines available to a tile: x passes take consecutive rows, y and z passes adjacent x columns

@@ -133,6 +133,7 @@ __device__ __forceinline__ void res3_body(const Desc& d, State* __restrict__ st,
   const T* __restrict__ R = static_cast<const T*>(d.rhs);
   T* __restrict__ W = static_cast<T*>(d.WY);
   double acc = 0.0;
+#pragma unroll 4
   for (size_t q = (size_t)b * blockDim.x + threadIdx.x; q < N; q += (size_t)d.blk3 * blockDim.x) {
     int l, i, j;
     point3(d, q, l, i, j);

@@ -245,7 +245,7 @@ namespace {
 constexpr int kBatchThreads = 256;      // FP32 sweep blocks
 constexpr int kBatchMaxSide = 1024;     // batch grids: sides 4 .. 1024, powers of two
 constexpr int kBatchMaxSide3 = 512;     // 3-D batch grids: sides 4 .. 512
-constexpr int kBatchMaxBlk3 = 2 * 152;  // blocks per 3-D slot (plan3's cap)
+constexpr int kBatchMaxBlk3 = 1024;     // blocks per 3-D slot (plan3's cap)
 constexpr int kBatchBandRows = 4;
 constexpr int kBatchColWidth = 4;
 constexpr int kBatchGroups = 7;         // equation kinds served
