@@ -168,9 +168,11 @@ def kernel_names(pb, st):
 # the files that define each profiled kernel: a traffic figure stays valid while they are unchanged
 SWEEP_SOURCES = ("rd_sweep.cuh", "rd_device.cuh", "rd_internal.h", "rd_launch.h", "rd_sweep_col.cu",
                  "rd_sweep_f32_lap.cu", "rd_sweep_f32_bih.cu", "rd_sweep_f64_lap.cu", "rd_sweep_f64_bih.cu")
+SOURCES_3D = ("rd_3d.cuh", "rd_3d.cu", "rd_sweep.cuh", "rd_device.cuh", "rd_internal.h", "rd_launch3.h")
 KERNEL_SOURCES = {"k_res": SWEEP_SOURCES, "k_col": SWEEP_SOURCES, "k_upd": SWEEP_SOURCES,
                   "k_updres": SWEEP_SOURCES + ("rd_fused_lap.cu", "rd_fused_bih.cu"),
-                  "k_resid64": SWEEP_SOURCES + ("rd_kernels.cu",)}
+                  "k_resid64": SWEEP_SOURCES + ("rd_kernels.cu",),
+                  "k3_res": SOURCES_3D, "k3_lines": SOURCES_3D, "k3_upd": SOURCES_3D}
 
 
 def kernel_source_hash(kernel):
