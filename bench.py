@@ -6,7 +6,8 @@ Du = 2e-5, Dv = 1e-5, F = 0.04, k = 0.06, dt = 1, u = 1, v = 0 with ten seeded s
 and 1% noise, each implicit step solved to ||F||_2 <= 1e-11 ||U^k||_2 with FP32 PDHG sweeps
 inside FP64 defect correction (the largest configuration, and the one whose working set exceeds
 L2).  ``--workload`` selects the others (Allen-Cahn Neumann 1024^2, Cahn-Hilliard split 512^2,
-Allen-Cahn periodic 64^2, the sixth-order example 128^2).  One benchmark step = one implicit
+Allen-Cahn periodic 64^2 and 128^3, the sixth-order example 128^2, and the roofline sweep:
+Allen-Cahn periodic 8192^2 with 200 PDHG iterations per step and no stopping rule).  One benchmark step = one implicit
 time step (every PDHG iteration of it, the FP64 residual passes and the defect-correction
 updates) continuing from the previous step's state.
 
@@ -32,7 +33,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
 WORKLOADS = ("gray_scott_2048", "allen_cahn_neumann_1024", "cahn_hilliard_split_512", "allen_cahn_periodic_64",
-             "allen_cahn_periodic_128x3", "fch_128")
+             "allen_cahn_periodic_128x3", "allen_cahn_periodic_8192", "fch_128")
 
 
 def workload(name):
@@ -49,6 +50,8 @@ def workload(name):
         return WL.config_fch(128)
     if name == "allen_cahn_periodic_128x3":
         return WL.config_allen_cahn_periodic_3d()
+    if name == "allen_cahn_periodic_8192":
+        return WL.config_allen_cahn_periodic_8192()
     raise SystemExit("unknown workload " + name)
 
 
@@ -128,7 +131,7 @@ class ClockSampler:
 # --------------------------------------------------------------------------------------------
 # algorithmic bytes per launch of the three PDHG kernels
 # --------------------------------------------------------------------------------------------
-def kernel_bytes(pb, precision):
+def kernel_bytes(pb, precision, line_kernels=False):
     """Array touches per grid point of each kernel at the algorithmic minimum, times the point
     count: k_res reads the unknown, the FP32 base state (defect correction, nonlinear kinds)
     and the right-hand side and writes the row-transformed residual; k_col reads and writes
@@ -136,12 +139,14 @@ def kernel_bytes(pb, precision):
     unknown and P."""
     es = 4 if precision == "fp32_dc" else 8
     npts = pb.ncomp * pb.nx * pb.ny * getattr(pb, "nz", 1)
-    if getattr(pb, "nz", 1) > 1:
+    if getattr(pb, "nz", 1) > 1 or line_kernels:
         # 3-D: the residual reads the unknown, base state and rhs and writes W; the five transform
         # passes read and write the array (the last also reads and writes P); the update reads
-        # P~, the unknown and the base state and writes the unknown
+        # P~, the unknown and the base state and writes the unknown.  2-D grids on the same
+        # kernels have three transform passes (x, y with the scaling, x with the dual update).
         base3 = 1 if precision == "fp32_dc" else 0
-        return {"k3_res": (3 + base3) * es * npts, "k3_lines": 12 * es * npts, "k3_upd": (3 + base3) * es * npts}
+        passes = 12 if getattr(pb, "nz", 1) > 1 else 8
+        return {"k3_res": (3 + base3) * es * npts, "k3_lines": passes * es * npts, "k3_upd": (3 + base3) * es * npts}
     if pb.kind == "fch":
         # sixth-order equation (FP64 stencil chains): residual mu, A mu, F = 2 + 3 + 4 touches;
         # preconditioner-only transforms 2 + 2 + 2; update dual, Lap P~, A Lap P~, U = 4 + 2 + 3 + 6
@@ -160,7 +165,7 @@ def kernel_names(pb, st):
         return ("k_small_cluster" if st["small_solve"] == 2 else "k_small",)
     if pb.kind == "fch":
         return ("fch_residual", "precond", "fch_update")
-    if getattr(pb, "nz", 1) > 1:
+    if getattr(pb, "nz", 1) > 1 or st.get("line_kernels"):
         return ("k3_res", "k3_lines", "k3_upd")
     return ("k_res", "k_col", "k_updres" if st.get("fused_update") else "k_upd")
 
@@ -366,9 +371,13 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # fixed-iteration workloads (threshold 0) end every step as not converged after max_iter
+    fixed = pb.tol == 0.0
+    allow = (rd.RD_OK, rd.RD_ERR_NOT_CONVERGED) if fixed else (rd.RD_OK,)
+
     def timed_steps(solver, u, nsteps, warm):
         for _ in range(warm):
-            solver.step(u, u)
+            solver.step(u, u, allow=allow)
         solver.reset_stats()
         barrier()
         torch.cuda.synchronize()
@@ -378,7 +387,7 @@ def run_ours(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            info = solver.step(u, u)
+            info = solver.step(u, u, allow=allow)
             e1.record(stream)
             e1.synchronize()
             tot_ms += e0.elapsed_time(e1)
@@ -394,6 +403,9 @@ def run_ours(args, rank, world, local_rank):
                 fft_buffers=args.fft_buffers, solve_loop=args.solve_loop, fft_unrolled=args.fft_unrolled,
                 autotune=args.autotune, dc_inner_rtol=args.dc_inner_rtol, dc_stall_window=args.dc_stall_window,
                 fused_update=args.fused_update)
+    if fixed and args.precision == "fp32_dc":
+        # one outer round whose inner solve runs its max_iter updates: no inner stop, no stall
+        tune.update(dc_max_outer=1, dc_stall_window=1 << 30, dc_inner_rtol=1e-300)
     sv = rd.Solver(pb, precision=args.precision, profile=1, **tune)
     with ClockSampler(local_rank) as clk:
         tot_ms, its, infos = timed_steps(sv, u, args.steps, args.warmup)
@@ -409,7 +421,7 @@ def run_ours(args, rank, world, local_rank):
 
     # per-kernel roofline from the live CUDA-event samples
     peak, peak_kind = load_peaks()
-    kb = kernel_bytes(pb, args.precision)
+    kb = kernel_bytes(pb, args.precision, st.get("line_kernels", 0))
     names = kernel_names(pb, st)
     per = {}
     for i, nm in enumerate(names):
@@ -444,7 +456,7 @@ def run_ours(args, rank, world, local_rank):
         uh_np = uh.numpy()
         sv_e = rd.Solver(pb, precision=args.precision, **tune)
         for _ in range(args.warmup):
-            sv_e.solve_host(uh_np, 1)
+            sv_e.solve_host(uh_np, 1, allow=allow)
         barrier()
         torch.cuda.synchronize()
         t_e, its_e = 0.0, 0
@@ -452,7 +464,7 @@ def run_ours(args, rank, world, local_rank):
             flush.fill_(k & 0xFF)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            infos_e, _ = sv_e.solve_host(uh_np, 1)
+            infos_e, _ = sv_e.solve_host(uh_np, 1, allow=allow)
             t_e += time.perf_counter() - t0
             its_e += infos_e[0]["iterations"]
         sv_e.close()
@@ -472,7 +484,7 @@ def run_ours(args, rank, world, local_rank):
         sv64 = rd.Solver(pb, precision="fp64", profile=1)
         ms64, its64, _ = timed_steps(sv64, u64, args.fp64_steps, 1)
         st64 = sv64.stats()
-        kb64 = kernel_bytes(pb, "fp64")
+        kb64 = kernel_bytes(pb, "fp64", st64.get("line_kernels", 0))
         per64 = {}
         for i, nm in enumerate(kernel_names(pb, st64)):
             n = st64["kernel_samples"][i]
@@ -499,7 +511,7 @@ def run_ours(args, rank, world, local_rank):
                          "(C++ FP64 oracle, %d threads, %.1f s)" % (its_a, used, dt_a),
                "cpu": cpu_model(), "nproc": os.cpu_count(),
                "single_thread": {"value": npts * its_1 / dt_1 / 1e9, "iterations": its_1, "seconds": dt_1}}
-        ns = args.parity_steps
+        ns = 0 if fixed else args.parity_steps  # fixed-iteration steps: parity in the GPU tests
         if ns > 0:
             from oracle import cpp_oracle as C
             C.set_threads(0)
@@ -518,7 +530,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- adaptive time step size (Section 2.2) on the same workload ----
     adaptive = None
-    if rank == 0 and not args.no_adaptive:
+    if rank == 0 and not args.no_adaptive and not fixed:
         adaptive = adaptive_leg(pb, w, args, dev, stream, its / args.steps)
 
     serving = None
@@ -535,7 +547,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload,
                    "grid": ("%dx%dx%dx%d" % (pb.ncomp, pb.nz, pb.ny, pb.nx)) if pb.nz > 1 else ("%dx%dx%d" % (pb.ncomp, pb.ny, pb.nx)),
                    "bc": pb.bc,
-                   "kind": pb.kind, "dt": pb.dt, "tol": "%s %g" % (pb.tol_kind, pb.tol),
+                   "kind": pb.kind, "dt": pb.dt,
+                   "tol": ("none: %d PDHG iterations per step" % pb.max_iter) if fixed else "%s %g" % (pb.tol_kind, pb.tol),
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "iterations_per_step": its / args.steps,

@@ -95,9 +95,11 @@ typedef enum {
 /* Grid.  2-D: sides nx, ny.  3-D (ndim = 3, not in the paper, which is 2-D: its scheme with a
  * third axis -- seven-point Laplacian, Lap^2 as its square, transforms along x, y and z; scalar
  * kinds RD_RX_NONE, Allen-Cahn and both Cahn-Hilliard forms; arrays [ncomp][nz][ny][nx]).
- * Every side is a power of two, at least 2 and at most 2048 for RD_PREC_FP32_DC, 4096 for
- * RD_PREC_FP64 on 2-D grids (one row or column is transformed by one thread block), at most
- * 2048 on 3-D grids; longer sides return RD_ERR_UNSUPPORTED. */
+ * Every side is a power of two, at least 2; at most 2048 on 3-D grids and 8192 on 2-D grids.
+ * 2-D grids with a side above 2048 (RD_PREC_FP32_DC) or 4096 (RD_PREC_FP64) run on the
+ * line-transform kernels of 3-D grids (pointwise residual and update, one transform pass per
+ * axis, the spectral scaling on the y pass) and take the scalar kinds only; longer sides, and
+ * two-species or sixth-order equations on such grids, return RD_ERR_UNSUPPORTED. */
 typedef struct {
     int ndim;            /* 2 or 3                                                             */
     int n[3];            /* n[0] = nx (contiguous), n[1] = ny, n[2] = nz (3-D)                 */
@@ -211,6 +213,8 @@ typedef struct {
     int plan_upd_rows;           /* rows per CTA of the update sweep (k_upd) chosen at create    */
     int fused_update;            /* 1 when the fused update + residual kernel (k_updres) runs      */
     int small_solve;             /* 1 when each inner solve runs in one block (rd_opts.small_solve) */
+    int line_kernels;            /* 1 when the iteration runs on the line-transform kernels (3-D
+                                    grids; 2-D grids with a side beyond the band / column sweeps) */
 } rd_stats;
 
 typedef struct rd_pdhg rd_pdhg;

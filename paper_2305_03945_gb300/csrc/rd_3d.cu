@@ -23,6 +23,15 @@ __global__ void __launch_bounds__(256) k3_lines(const __grid_constant__ Desc d, 
   lines3_body<T, AX, MODE>(d, st, nullptr, blockIdx.x, smem_raw);
 }
 
+// The same passes for lines of 2^LOGN = 4096 and 8192 points (2-D grids beyond the band /
+// column sweeps): blocks of 2^LOGN / 8 threads (one radix-8 job each per FFT pass: with two jobs
+// per thread and 128 registers the passes spilled), the pass sequence fixed at compile time.
+template <class T, int AX, int MODE, int LOGN>
+__global__ void __launch_bounds__(LOGN > 12 ? 1024 : 512) k3_lines_long(const __grid_constant__ Desc d, State* __restrict__ st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  lines3_body<T, AX, MODE, LOGN>(d, st, nullptr, blockIdx.x, smem_raw);
+}
+
 // rhs of the step from U^k (the explicit part of the convex split), ||U^k||^2 and a fresh solve
 // state; d.blk3 blocks of 256 threads.
 __global__ void __launch_bounds__(256) k3_begin(const Desc* __restrict__ d64, State* __restrict__ st,
@@ -97,7 +106,24 @@ inline cudaError_t record(cudaStream_t s, cudaEvent_t* ev, int i, unsigned flags
 template <class T, int AX, int MODE>
 cudaError_t launch_lines(const Desc& d, State* st, cudaStream_t s) {
   const int n = AX == 0 ? d.nx : (AX == 1 ? d.ny : d.nz);
-  k3_lines<T, AX, MODE><<<d.blk3, d.thr3[AX], lines3_smem_bytes<T>(n, d.lw3[AX], d.bc == BC_NEUMANN), s>>>(d, st);
+  const int smem = lines3_smem_bytes<T>(n, d.lw3[AX], d.bc == BC_NEUMANN);
+  // the passes of a 2-D grid (x: forward, inverse with the dual update, inverse; y: the scaled
+  // pass) on lines of 4096 and 8192 points, which plan3 gives n / 8 threads
+  constexpr bool two_d_pass = (AX == 0 && (MODE == L3_FWD || MODE == L3_INVP || MODE == L3_INVX)) ||
+                              (AX == 1 && MODE == L3_FSI);
+  if constexpr (two_d_pass) {
+    if (d.thr3[AX] > 256) {
+      if (n == 8192) {
+        k3_lines_long<T, AX, MODE, 13><<<d.blk3, d.thr3[AX], smem, s>>>(d, st);
+      } else if constexpr (sizeof(T) == 4) {
+        k3_lines_long<T, AX, MODE, 12><<<d.blk3, d.thr3[AX], smem, s>>>(d, st);
+      } else {
+        return cudaErrorNotSupported;  // FP64 lines up to 4096 points run on the band / column sweeps
+      }
+      return cudaGetLastError();
+    }
+  }
+  k3_lines<T, AX, MODE><<<d.blk3, d.thr3[AX], smem, s>>>(d, st);
   return cudaGetLastError();
 }
 
@@ -118,9 +144,13 @@ cudaError_t launch_iter3_k(const Desc& d, State* st, cudaStream_t s, cudaEvent_t
   if (e == cudaSuccess) e = record(s, ev, 1, flags);
   if (d.precond != 0) {
     if (e == cudaSuccess) e = launch_lines<T, 0, L3_FWD>(d, st, s);
-    if (e == cudaSuccess) e = launch_lines<T, 1, L3_FWD>(d, st, s);
-    if (e == cudaSuccess) e = launch_lines<T, 2, L3_FSI>(d, st, s);
-    if (e == cudaSuccess) e = launch_lines<T, 1, L3_INV>(d, st, s);
+    if (d.nz > 1) {
+      if (e == cudaSuccess) e = launch_lines<T, 1, L3_FWD>(d, st, s);
+      if (e == cudaSuccess) e = launch_lines<T, 2, L3_FSI>(d, st, s);
+      if (e == cudaSuccess) e = launch_lines<T, 1, L3_INV>(d, st, s);
+    } else if (e == cudaSuccess) {
+      e = launch_lines<T, 1, L3_FSI>(d, st, s);  // 2-D grid: the scaling on the y pass
+    }
     if (e == cudaSuccess) e = launch_lines<T, 0, L3_INVP>(d, st, s);
   }
   if (e == cudaSuccess) e = record(s, ev, 2, flags);
@@ -158,11 +188,24 @@ cudaError_t launch_iteration3(const Desc& d, State* st, cudaStream_t s, cudaEven
 template <class T>
 cudaError_t launch_precond3(const Desc& d, State* st, cudaStream_t s) {
   cudaError_t e = launch_lines<T, 0, L3_FWD>(d, st, s);
-  if (e == cudaSuccess) e = launch_lines<T, 1, L3_FWD>(d, st, s);
-  if (e == cudaSuccess) e = launch_lines<T, 2, L3_FSI>(d, st, s);
-  if (e == cudaSuccess) e = launch_lines<T, 1, L3_INV>(d, st, s);
+  if (d.nz > 1) {
+    if (e == cudaSuccess) e = launch_lines<T, 1, L3_FWD>(d, st, s);
+    if (e == cudaSuccess) e = launch_lines<T, 2, L3_FSI>(d, st, s);
+    if (e == cudaSuccess) e = launch_lines<T, 1, L3_INV>(d, st, s);
+  } else if (e == cudaSuccess) {
+    e = launch_lines<T, 1, L3_FSI>(d, st, s);
+  }
   if (e == cudaSuccess) e = launch_lines<T, 0, L3_INVX>(d, st, s);
   return e;
+}
+
+template <class T, int LOGN>
+cudaError_t allow_long(int optin) {
+  cudaError_t e;
+  if ((e = allow3_k(k3_lines_long<T, 0, L3_FWD, LOGN>, optin)) != cudaSuccess) return e;
+  if ((e = allow3_k(k3_lines_long<T, 1, L3_FSI, LOGN>, optin)) != cudaSuccess) return e;
+  if ((e = allow3_k(k3_lines_long<T, 0, L3_INVP, LOGN>, optin)) != cudaSuccess) return e;
+  return allow3_k(k3_lines_long<T, 0, L3_INVX, LOGN>, optin);
 }
 
 template <class T>
@@ -171,9 +214,13 @@ cudaError_t allow3(int optin) {
   if ((e = allow3_k(k3_lines<T, 0, L3_FWD>, optin)) != cudaSuccess) return e;
   if ((e = allow3_k(k3_lines<T, 1, L3_FWD>, optin)) != cudaSuccess) return e;
   if ((e = allow3_k(k3_lines<T, 2, L3_FSI>, optin)) != cudaSuccess) return e;
+  if ((e = allow3_k(k3_lines<T, 1, L3_FSI>, optin)) != cudaSuccess) return e;
   if ((e = allow3_k(k3_lines<T, 1, L3_INV>, optin)) != cudaSuccess) return e;
   if ((e = allow3_k(k3_lines<T, 0, L3_INVP>, optin)) != cudaSuccess) return e;
-  return allow3_k(k3_lines<T, 0, L3_INVX>, optin);
+  if ((e = allow3_k(k3_lines<T, 0, L3_INVX>, optin)) != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4)
+    if ((e = allow_long<T, 12>(optin)) != cudaSuccess) return e;
+  return allow_long<T, 13>(optin);
 }
 
 template cudaError_t launch_iteration3<float>(const Desc&, State*, cudaStream_t, cudaEvent_t*);
@@ -193,8 +240,21 @@ bool plan3(int nx, int ny, int nz, int nc, int elem_bytes, bool neumann, int sme
     const int n = n_ax[a];
     const int line_thr = n >= 8 ? n / 8 : 1;
     if (line_thr > 256) {
-      *why = "3-D grid side longer than a 256-thread block transforms (2048 points)";
-      return false;
+      // 2-D grids only (nz = 1): x and y lines of up to 8192 points, one pair line per tile,
+      // on blocks of n / 8 threads
+      if (nz > 1 || n > 8192) {
+        *why = nz > 1 ? "3-D grid side longer than a 256-thread block transforms (2048 points)"
+                      : "grid side longer than 8192 points";
+        return false;
+      }
+      const int smem = elem_bytes == 4 ? lines3_smem_bytes<float>(n, 2, neumann) : lines3_smem_bytes<double>(n, 2, neumann);
+      if (smem > smem_limit) {
+        *why = "transform line does not fit in shared memory";
+        return false;
+      }
+      d.lw3[a] = 2;
+      d.thr3[a] = line_thr;
+      continue;
     }
     int lw = std::min(lanes, avail[a]);
     if (lw < 2) lw = 2;

@@ -22,13 +22,16 @@
 
 namespace rd {
 
-// one component of a 3-D grid array in global memory, boundary-mapped on every axis
+// one component of a 3-D grid array in global memory, boundary-mapped on every axis; a 2-D grid
+// run on these kernels has nz = 1, and every z offset maps to its one plane (the descriptor's
+// hz2 = 0 removes the z terms of the stencils)
 template <class T>
 struct G3 {
   const T* __restrict__ p;
   int nx, ny, nz, bc;
   __device__ __forceinline__ T operator()(int l, int i, int j) const {
-    return p[((size_t)bcmap(l, nz, bc) * ny + bcmap(i, ny, bc)) * nx + bcmap(j, nx, bc)];
+    const int lz = nz > 1 ? bcmap(l, nz, bc) : 0;
+    return p[((size_t)lz * ny + bcmap(i, ny, bc)) * nx + bcmap(j, nx, bc)];
   }
 };
 
@@ -182,13 +185,14 @@ enum Lines3Mode {
 // Lines of axis AX grouped in tiles of lw lines, two lines per complex line in shared memory:
 // x: lw consecutive rows; y (z): lw adjacent x columns of one (component, z) plane (one
 // (component, y) row of planes).  Returns the tile's first element; *sl = element stride along
-// the line.  For y and z the lw lines of a tile are contiguous in memory.
+// the line; *orow = the tile's index along the third axis (z for y lines, y for z lines).  For y
+// and z the lw lines of a tile are contiguous in memory.
 template <int AX>
-__device__ __forceinline__ size_t tile3(const Desc& d, long t, int lw, size_t* sl, int* yrow) {
+__device__ __forceinline__ size_t tile3(const Desc& d, long t, int lw, size_t* sl, int* orow) {
   const size_t plane = (size_t)d.nx * d.ny;
   if (AX == 0) {
     *sl = 1;
-    *yrow = 0;
+    *orow = 0;
     return (size_t)t * lw * d.nx;
   }
   const long ntx = d.nx / lw;
@@ -196,16 +200,21 @@ __device__ __forceinline__ size_t tile3(const Desc& d, long t, int lw, size_t* s
   const size_t x0 = (size_t)(t - g * ntx) * lw;
   if (AX == 1) {
     *sl = d.nx;
-    *yrow = 0;
+    *orow = (int)(g & (long)(d.nz - 1));
     return (size_t)g * plane + x0;
   }
   const long c = g / d.ny, y = g - c * d.ny;
   *sl = plane;
-  *yrow = (int)y;
+  *orow = (int)y;
   return (size_t)c * plane * d.nz + (size_t)y * d.nx + x0;
 }
 
-template <class T, int AX, int MODE>
+// One transform pass over the tiles of axis AX.  The spectral scaling (L3_FSI) runs on the last
+// axis of the grid: z on 3-D grids, y on 2-D grids (nz = 1), which the launchers route to these
+// kernels when a line is too long for the band / column sweeps.  LOGN > 0: lines of 2^LOGN
+// points (4096 or 8192), one radix-8 job per thread and pass (2^LOGN / 8 threads), with the
+// pass sequence and line stride fixed at compile time.
+template <class T, int AX, int MODE, int LOGN = 0>
 __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ st, Slot* slot, int b,
                                             unsigned char* smem_raw) {
   const bool pc = d.mode == MODE_PRECOND_ONLY;
@@ -229,8 +238,8 @@ __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ s
   constexpr bool INV = MODE == L3_INV || MODE == L3_INVP || MODE == L3_INVX;
   for (long t = b; t < ntiles; t += d.blk3) {
     size_t sl;
-    int yrow;
-    const size_t base = tile3<AX>(d, t, lw, &sl, &yrow);
+    int orow;
+    const size_t base = tile3<AX>(d, t, lw, &sl, &orow);
     __syncthreads();  // the tables are loaded / the previous tile's buffer is free
     // 1. load: spatial values (forward modes; Neumann in Makhoul order), or coefficients k in
     //    natural order (inverse modes; Neumann: the conjugated DCT-III preparation)
@@ -289,7 +298,9 @@ __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ s
       }
     }
     __syncthreads();
-    cx<T>* cur = block_fft_loop<T, -1>(buf, buf, nl, logn, ls, tw, tid, nt);
+    cx<T>* cur;
+    if constexpr (LOGN > 0) cur = block_fft_long<T, -1, 1, LOGN>(buf, nl, tw, tid, nt);
+    else cur = block_fft_loop<T, -1>(buf, buf, nl, logn, ls, tw, tid, nt);
     if constexpr (MODE == L3_FSI) {
       // forward epilogue and the spectral scaling 1 / (g_hat nx ny nz), in place; then the
       // second (inverse) transform as in the 2-D column pass
@@ -303,8 +314,11 @@ __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ s
         if constexpr (sizeof(T) == 4) return inn * __frcp_rn(g * g);
         else return inn / (g * g);
       };
+      // eigenvalues: mu_line of the line's own axis at frequency k, plus those of the other
+      // axes at the tile's position (x: the pair's two columns; the third axis: orow)
+      const T* mul = AX == 2 ? muz : muy;
       const int x0 = (int)(base % d.nx);
-      const T my = muy[yrow];
+      const T my = AX == 2 ? muy[orow] : muz[orow];
       for (int g = tid; g < (nl << lh); g += nt) {
         const int p = g >> lh, k = g & (hn - 1);
         cx<T>* L = cur + p * ls;
@@ -316,7 +330,7 @@ __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ s
           fwd_post(L, n, d.bc, dc, hn, okp, tt);
         }
         const T ma = mux[x0 + 2 * p] + my, mb = mux[x0 + 2 * p + 1] + my;
-        const T m1 = muz[k], m2 = muz[k2];
+        const T m1 = mul[k], m2 = mul[k2];
         L[pidx(k)] = cx<T>{ok.x * sym(ma + m1), ok.y * sym(mb + m1)};
         L[pidx(k2)] = cx<T>{okp.x * sym(ma + m2), okp.y * sym(mb + m2)};
       }
@@ -343,7 +357,8 @@ __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ s
         }
         __syncthreads();
       }
-      cur = block_fft_loop<T, -1>(cur, cur, nl, logn, ls, tw, tid, nt);
+      if constexpr (LOGN > 0) cur = block_fft_long<T, -1, 1, LOGN>(cur, nl, tw, tid, nt);
+      else cur = block_fft_loop<T, -1>(cur, cur, nl, logn, ls, tw, tid, nt);
     }
     if constexpr (MODE == L3_FWD) {
       // forward epilogue straight to global memory: coefficient k of both lines

@@ -519,7 +519,7 @@ rd_status capture_graphs(rd_pdhg* h) {
   const LaunchCfg& lc = h->dc ? h->cfg32 : h->cfg64;
   h->kernels_per_iter = h->small ? 1
                     : h->fch ? (lc.transform ? 10 : 7)
-                    : h->nd3 ? (lc.transform ? 7 : 2)
+                    : h->nd3 ? (lc.transform ? (h->nz > 1 ? 7 : 5) : 2)
                              : (h->dc && h->h_desc[1].fused ? 2 : (lc.transform ? 3 : 2));
   if (h->opts.profile)
     for (int i = 0; i < 4; ++i)
@@ -815,8 +815,16 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
                       double tau, double sigma, const rd_precond* pc, const rd_opts* o, void* stream) {
   h->nx = grid->n[0];
   h->ny = grid->n[1];
-  h->nd3 = grid->ndim == 3;
-  h->nz = h->nd3 ? grid->n[2] : 1;
+  if (o) h->opts = *o; else rd_opts_default(&h->opts);
+  h->dc = h->opts.precision == RD_PREC_FP32_DC;
+  // 2-D grids with a side longer than the band / column sweeps transform (2048 points in FP32,
+  // 4096 in FP64) run on the line-transform kernels of 3-D grids with nz = 1
+  const bool long2d = grid->ndim == 2 && std::max(h->nx, h->ny) > (h->dc ? 2048 : 4096);
+  if (long2d && rx->kind != RD_RX_NONE && rx->kind != RD_RX_ALLEN_CAHN && rx->kind != RD_RX_CH_IMPLICIT &&
+      rx->kind != RD_RX_CH_SPLIT)
+    return fail(RD_ERR_UNSUPPORTED, "2-D sides beyond 2048 (FP32) / 4096 (FP64) points are built for the scalar kinds");
+  h->nd3 = grid->ndim == 3 || long2d;
+  h->nz = grid->ndim == 3 ? grid->n[2] : 1;
   h->nc = rx->ncomp;
   h->npts = (size_t)h->nc * h->nx * h->ny * h->nz;
   h->bc = bc;
@@ -829,9 +837,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   h->sigma = sigma;
   h->hx = grid->length[0] / h->nx;
   h->hy = grid->length[1] / h->ny;
-  h->hz = h->nd3 ? grid->length[2] / h->nz : 1.0;
-  if (o) h->opts = *o; else rd_opts_default(&h->opts);
-  h->dc = h->opts.precision == RD_PREC_FP32_DC;
+  h->hz = grid->ndim == 3 ? grid->length[2] / h->nz : 1.0;
   h->stream = static_cast<cudaStream_t>(stream);
   RD_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   RD_CUDA(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
@@ -861,7 +867,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   base.omega = h->opts.omega;
   base.nz = h->nz;
   base.lognz = ilog2(h->nz);
-  base.hz2 = h->nd3 ? 1.0 / (h->hz * h->hz) : 0.0;
+  base.hz2 = grid->ndim == 3 ? 1.0 / (h->hz * h->hz) : 0.0;  // 0: no z terms in the stencils
 
   std::string why;
   Desc d64 = base, d32 = base;
@@ -1073,6 +1079,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   }
   h->stats.fused_update = h->h_desc[1].fused;
   h->stats.small_solve = h->small;
+  h->stats.line_kernels = h->nd3;
   h->stats.plan_band_rows = h->h_desc[h->dc ? 1 : 0].band_rows;
   h->stats.plan_upd_rows = h->h_desc[h->dc ? 1 : 0].upd_rows;
   h->stats.plan_col_width = h->h_desc[h->dc ? 1 : 0].col_width;
@@ -1501,10 +1508,11 @@ rd_status rd_pdhg_get_stats(const rd_pdhg* h, rd_stats* out) {
 rd_status rd_pdhg_reset_stats(rd_pdhg* h) {
   if (!h) return fail(RD_ERR_INVALID_ARG, "NULL handle");
   const int pb = h->stats.plan_band_rows, pc = h->stats.plan_col_width, pu = h->stats.plan_upd_rows;
-  const int fu = h->stats.fused_update, sm = h->stats.small_solve;
+  const int fu = h->stats.fused_update, sm = h->stats.small_solve, lk = h->stats.line_kernels;
   h->stats = rd_stats{};
   h->stats.fused_update = fu;
   h->stats.small_solve = sm;
+  h->stats.line_kernels = lk;
   h->stats.plan_band_rows = pb;
   h->stats.plan_col_width = pc;
   h->stats.plan_upd_rows = pu;

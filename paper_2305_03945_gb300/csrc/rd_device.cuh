@@ -140,12 +140,14 @@ __device__ __forceinline__ void job_twiddles(const cx<T>* __restrict__ tw, int s
 // One Stockham pass of radix R (Govindaraju et al., SC 2008 formulation): job j of a line reads
 // entries j + r N/R of src, twiddles them by w^{r (j mod Ns) N/(Ns R)}, applies the radix-R DFT
 // and writes entries (j div Ns) Ns R + (j mod Ns) + r Ns of dst.  With src == dst all reads
-// happen before a barrier and all writes after it.  Sizes enter as base-2 logarithms.
-template <class T, int R, int DIR>
+// happen before a barrier and all writes after it.  Sizes enter as base-2 logarithms.  Each
+// thread holds J * RM / R jobs (J radix-RM jobs' worth of values), so that J > 1 lets a block
+// transform lines of up to J * RM points per thread.
+template <class T, int R, int DIR, int J = 1>
 __device__ __forceinline__ void stockham_pass(const cx<T>* src, cx<T>* dst, int nlines, int logN, int ls, int logNs,
                                               const cx<T>* __restrict__ tw, int tid) {
   constexpr int RM = FftRadix<T>::value;
-  constexpr int S = RM / R;
+  constexpr int S = J * RM / R;
   constexpr int LR = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4));
   const int lj = logN - LR;  // log2 jobs per line
   const int jpl = 1 << lj;
@@ -294,7 +296,9 @@ __device__ __forceinline__ cx<T>* block_fft_c(cx<T>* buf, cx<T>* scr, int nlines
 // fft_line_threads<T>(N).  With `unrolled`, lengths 64 .. 2048 run passes specialised and
 // unrolled at compile time for that length; otherwise one looped pass body serves every pass
 // (fewer distinct instructions, more index arithmetic; measured slower on GB300).
-template <class T, int DIR>
+// block_fft_loop with J > 1 holds J radix-8 jobs per thread and pass, for lines longer than
+// 8 x nthreads points (it needs nthreads * 8 * J >= N).
+template <class T, int DIR, int J = 1>
 __device__ cx<T>* block_fft_loop(cx<T>* buf, cx<T>* scr, int nlines, int logN, int ls, const cx<T>* __restrict__ tw,
                                  int tid, int nthreads);
 
@@ -314,12 +318,12 @@ __device__ cx<T>* block_fft(cx<T>* buf, cx<T>* scr, int nlines, int logN, int ls
 }
 
 // The looped form of block_fft: one pass body for every pass of every length.
-template <class T, int DIR>
+template <class T, int DIR, int J>
 __device__ cx<T>* block_fft_loop(cx<T>* buf, cx<T>* scr, int nlines, int logN, int ls, const cx<T>* __restrict__ tw,
                                  int tid, int nthreads) {
   constexpr int RM = FftRadix<T>::value;
   constexpr int LRM = RM == 8 ? 3 : 4;
-  int chunk = (nthreads * RM) >> logN;
+  int chunk = (nthreads * RM * J) >> logN;
   if (chunk < 1) chunk = 1;
   cx<T>* res = buf;
   for (int l0 = 0; l0 < nlines; l0 += chunk) {
@@ -329,10 +333,10 @@ __device__ cx<T>* block_fft_loop(cx<T>* buf, cx<T>* scr, int nlines, int logN, i
     int logNs = 0, rem = logN;
     while (rem > 0) {
       const int bb = rem >= LRM ? LRM : rem;
-      if (bb == 4) stockham_pass<T, (RM >= 16 ? 16 : RM), DIR>(a, b, nl, logN, ls, logNs, tw, tid);
-      else if (bb == 3) stockham_pass<T, 8, DIR>(a, b, nl, logN, ls, logNs, tw, tid);
-      else if (bb == 2) stockham_pass<T, 4, DIR>(a, b, nl, logN, ls, logNs, tw, tid);
-      else stockham_pass<T, 2, DIR>(a, b, nl, logN, ls, logNs, tw, tid);
+      if (bb == 4) stockham_pass<T, (RM >= 16 ? 16 : RM), DIR, J>(a, b, nl, logN, ls, logNs, tw, tid);
+      else if (bb == 3) stockham_pass<T, 8, DIR, J>(a, b, nl, logN, ls, logNs, tw, tid);
+      else if (bb == 2) stockham_pass<T, 4, DIR, J>(a, b, nl, logN, ls, logNs, tw, tid);
+      else stockham_pass<T, 2, DIR, J>(a, b, nl, logN, ls, logNs, tw, tid);
       cx<T>* t = a;
       a = b;
       b = t;
@@ -342,6 +346,35 @@ __device__ cx<T>* block_fft_loop(cx<T>* buf, cx<T>* scr, int nlines, int logN, i
     res = a - l0 * ls;
   }
   return res;
+}
+
+// Transform of lines of a length 2^LOGN known at compile time (lines of 4096 and 8192 points),
+// with J radix-8 jobs per thread and pass: the pass sequence unrolled at compile time, in place,
+// as block_fft_loop with scr == buf.
+template <class T, int DIR, int J, int LOGN, int LOGNS>
+__device__ __forceinline__ void fft_passes_j(cx<T>* a, int nlines, int ls, const cx<T>* __restrict__ tw, int tid) {
+  constexpr int REM = LOGN - LOGNS;
+  if constexpr (REM > 0) {
+    constexpr int B = REM >= 3 ? 3 : REM;
+    stockham_pass<T, 1 << B, DIR, J>(a, a, nlines, LOGN, ls, LOGNS, tw, tid);
+    fft_passes_j<T, DIR, J, LOGN, LOGNS + B>(a, nlines, ls, tw, tid);
+  }
+}
+
+// (the line stride is padded_len(2^LOGN), a compile-time constant: with it the index arithmetic
+// of the passes folds into immediates)
+template <class T, int DIR, int J, int LOGN>
+__device__ __forceinline__ cx<T>* block_fft_long(cx<T>* buf, int nlines, const cx<T>* __restrict__ tw, int tid,
+                                                 int nthreads) {
+  constexpr int RM = FftRadix<T>::value;
+  constexpr int LS = ((1 << LOGN) + (1 << (LOGN - 4)) + 2) & ~1;
+  int chunk = (nthreads * RM * J) >> LOGN;
+  if (chunk < 1) chunk = 1;
+  for (int l0 = 0; l0 < nlines; l0 += chunk) {
+    const int nl = nlines - l0 < chunk ? nlines - l0 : chunk;
+    fft_passes_j<T, DIR, J, LOGN, 0>(buf + l0 * LS, nl, LS, tw, tid);
+  }
+  return buf;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -61,7 +61,7 @@ class rd_stats(ctypes.Structure):
                 ("host_syncs", ctypes.c_longlong), ("kernel_ms", ctypes.c_double * 3),
                 ("kernel_samples", ctypes.c_longlong * 3), ("plan_band_rows", ctypes.c_int),
                 ("plan_col_width", ctypes.c_int), ("plan_upd_rows", ctypes.c_int),
-                ("fused_update", ctypes.c_int), ("small_solve", ctypes.c_int)]
+                ("fused_update", ctypes.c_int), ("small_solve", ctypes.c_int), ("line_kernels", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -250,6 +250,20 @@ def config_allen_cahn_periodic_3d(n: int = 128, nsteps: int = 20, seed: int = 60
     return Workload("allen_cahn_periodic_%dx3" % n, pb, uniform_field(seed, pb.shape, -0.05, 0.05), nsteps)
 
 
+def config_allen_cahn_periodic_8192(n: int = 8192, nsteps: int = 2, seed: int = 7000,
+                                    fixed_iters: int = 200) -> Workload:
+    """The roofline sweep: Allen-Cahn, periodic [0,2pi)^2 with n^2 points and the physics of the
+    64^2 configuration (a = eps = 0.1, b = 1/eps, dt = 0.01), u0 ~ U[-0.05, 0.05] iid, and a
+    fixed number of PDHG iterations per step (threshold 0: the stopping rule never fires, the
+    step ends after max_iter = fixed_iters updates)."""
+    eps = 0.1
+    L = 2 * np.pi
+    pb = Problem(nx=n, ny=n, lx=L, ly=L, bc="periodic", op="laplacian", kind="allen_cahn",
+                 a=eps, b=1 / eps, dt=0.01, tau_u=1.0, tau_p=1.0, tol=0.0, tol_kind="res_abs",
+                 max_iter=fixed_iters)
+    return Workload("allen_cahn_periodic_%d" % n, pb, uniform_field(seed, (1, n, n), -0.05, 0.05), nsteps)
+
+
 def config_allen_cahn_neumann(n: int = 1024, nsteps: int = 100, seed: int = 2000) -> Workload:
     """Allen-Cahn, Neumann [0,1]^2 cell-centred (h=1/n), eps=0.01 (a=eps, b=1/eps), dt=1e-4,
     u0 = tanh of smoothed noise (sigma = 8 cells), stop on ||F||_2 <= 1e-11 ||U^k||_2."""
