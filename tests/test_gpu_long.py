@@ -57,9 +57,13 @@ FP64_SHAPES = [(4, 8192), (8192, 2), (16, 8192), (8192, 32)]
 FP32_SHAPES = [(8, 4096), (4096, 16), (4, 8192), (8192, 8), (64, 8192)]
 
 
-def _pb(kind, op, bc, ny, nx, **kw):
+def _pb(kind, op, bc, ny, nx, scaled=False, **kw):
+    """scaled: side lengths in proportion to the points (h about 0.02 as on a 64^2 grid of the
+    same lengths), so that the nonlinear terms stay as stiff as on the small grids and a step
+    converges to the tolerance; otherwise [0,1.7) x [0,1.3) whatever the points."""
     ch = op == "neg_biharmonic"
-    base = dict(nx=nx, ny=ny, lx=1.7, ly=1.3, bc=bc, op=op, kind=kind,
+    lx, ly = (1.7 * nx / 64, 1.3 * ny / 64) if scaled else (1.7, 1.3)
+    base = dict(nx=nx, ny=ny, lx=lx, ly=ly, bc=bc, op=op, kind=kind,
                 dt=1e-5 if ch else 2e-3, a=4e-4 if ch else 0.05, b=1.0 if ch else 20.0,
                 tau_u=0.9, tau_p=0.9, tol=1e-12, tol_kind="f_rel", max_iter=3000)
     base.update(kw)
@@ -119,7 +123,7 @@ STEP_CASES = [
 @pytest.mark.parametrize("loop", ["graph", "host"])
 def test_long_fp64_step_matches_oracle(kind, op, bc, shape, loop):
     rd = _rd()
-    pb = _pb(kind, op, bc, *shape)
+    pb = _pb(kind, op, bc, *shape, scaled=True)
     uk = WL.rng(13).uniform(-0.8, 0.8, pb.shape)
     U_ref, info_ref = O.pdhg_step(pb, uk, history=True)
     with rd.Solver(pb, solve_loop=loop) as s:
@@ -137,7 +141,7 @@ def test_long_fp64_step_matches_oracle(kind, op, bc, shape, loop):
 @pytest.mark.parametrize("shape", FP32_SHAPES)
 def test_long_fp32_defect_correction_step_matches_oracle(bc, kind, op, shape):
     rd = _rd()
-    pb = _pb(kind, op, bc, *shape)
+    pb = _pb(kind, op, bc, *shape, scaled=True)
     uk = WL.rng(14).uniform(-0.8, 0.8, pb.shape)
     U_ref, _ = O.pdhg_step(pb, uk)
     with rd.Solver(pb, precision="fp32_dc") as s:
@@ -169,11 +173,14 @@ def test_long_two_species_and_oversized_refused():
 
 def test_roofline_sweep_grid_8192_squared_step_matches_oracle():
     """The roofline sweep's grid, Allen-Cahn periodic 8192^2 (the 64^2 configuration's physics), one
-    implicit step from its seeded state solved to ||F||_2 <= 1e-11 ||U^k||_2 in both precisions,
-    element by element against the C++ oracle on all host cores."""
+    implicit step from its seeded state in both precisions, element by element against the C++
+    oracle on all host cores.  The step diffuses the i.i.d. initial state to 1/140 of its norm, so
+    the threshold, relative to ||U^k||, is tightened to 1e-13: at 1e-11 two solutions within it
+    (the oracle's and defect correction's, which take different paths to it) may differ by
+    about 1.4e-9 of ||U^{k+1}|| (measured: 1.0e-9), above the per-step bound the test checks."""
     rd = _rd()
     w = WL.config_allen_cahn_periodic_8192()
-    pb = w.problem.replace(tol=1e-11, tol_kind="f_rel", max_iter=10000)
+    pb = w.problem.replace(tol=1e-13, tol_kind="f_rel", max_iter=10000)
     C.set_threads(0)
     U_ref, info_ref = C.pdhg_step(pb, w.u0)
     assert info_ref["status"] == C.OK
