@@ -35,6 +35,32 @@ struct G3 {
   }
 };
 
+// The same array read at y and z offsets from one point's row (l0, i0) without boundary mapping,
+// for rows whose stencil rows and planes all lie inside the grid, and with the x index mapped;
+// pz = 0 on a 2-D grid (nz = 1), where every z offset maps to the point's own plane.  The test
+// for it depends only on the row, so that a warp (32 consecutive points of one row when
+// nx >= 32) takes one path.
+template <class T>
+struct G3r {
+  const T* __restrict__ p;  // element (l0, i0, 0)
+  int l0, i0, nx, bc;
+  long pz;                  // elements per z plane (0 when nz = 1)
+  __device__ __forceinline__ T operator()(int l, int i, int j) const {
+    return p[(long)(l - l0) * pz + (long)(i - i0) * nx + bcmap(j, nx, bc)];
+  }
+};
+
+// Do the rows and planes of a radius-R stencil around row (l, i) lie inside the grid?
+template <int R>
+__device__ __forceinline__ bool inside_yz(const Desc& d, int l, int i) {
+  return i >= R && i < d.ny - R && (d.nz == 1 || (l >= R && l < d.nz - R));
+}
+// stencil radius of the residual / adjoint of equation key K (13-point biharmonic: 2)
+template <int K>
+__device__ __forceinline__ constexpr int radius3() {
+  return (K == KK_NONE_LAP || K == KK_AC) ? 1 : 2;
+}
+
 // seven-point Laplacian at (l, i, j) with centre value c
 template <class T, class F>
 __device__ __forceinline__ T lap7(const F& f, int l, int i, int j, T c, T hx2, T hy2, T hz2) {
@@ -135,14 +161,24 @@ __device__ __forceinline__ void res3_body(const Desc& d, State* __restrict__ st,
   const G3<T> B{static_cast<const T*>(d.base), d.nx, d.ny, d.nz, d.bc};
   const T* __restrict__ R = static_cast<const T*>(d.rhs);
   T* __restrict__ W = static_cast<T*>(d.WY);
+  const long pz = d.nz > 1 ? (long)d.nx * d.ny : 0;
+  constexpr int RAD = radius3<K>();
   double acc = 0.0;
 #pragma unroll 4
   for (size_t q = (size_t)b * blockDim.x + threadIdx.x; q < N; q += (size_t)d.blk3 * blockDim.x) {
     int l, i, j;
     point3(d, q, l, i, j);
-    const T w = residual3_pt<T, K, DC>(d, X, B, l, i, j, R[q]);
+    T w;
+    if (inside_yz<RAD>(d, l, i)) {
+      const size_t row = q - (size_t)j;
+      const G3r<T> Xr{static_cast<const T*>(d.X) + row, l, i, d.nx, d.bc, pz};
+      const G3r<T> Br{static_cast<const T*>(d.base) + row, l, i, d.nx, d.bc, pz};
+      w = residual3_pt<T, K, DC>(d, Xr, Br, l, i, j, R[q]);
+    } else {
+      w = residual3_pt<T, K, DC>(d, X, B, l, i, j, R[q]);
+    }
     W[q] = w;
-    acc += (double)w * (double)w;
+    acc += (double)(w * w);
   }
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) d.partials[b] = s;
@@ -161,13 +197,22 @@ __device__ __forceinline__ void upd3_body(const Desc& d, State* __restrict__ st,
   T* __restrict__ X = static_cast<T*>(d.X);
   const T* __restrict__ Bs = static_cast<const T*>(d.base);
   const T tu = T(d.tau_u);
+  const long pz = d.nz > 1 ? (long)d.nx * d.ny : 0;
+  constexpr int RAD = radius3<K>();
   for (size_t q = (size_t)b * blockDim.x + threadIdx.x; q < N; q += (size_t)d.blk3 * blockDim.x) {
     int l, i, j;
     point3(d, q, l, i, j);
     const T xq = X[q];
     T x0 = xq;
     if constexpr (DC && KT<K>::nonlinear) x0 += Bs[q];
-    X[q] = xq - tu * gradT3_pt<T, K>(d, Pt, x0, l, i, j);
+    T g;
+    if (inside_yz<RAD>(d, l, i)) {
+      const G3r<T> Pr{static_cast<const T*>(d.WY) + (q - (size_t)j), l, i, d.nx, d.bc, pz};
+      g = gradT3_pt<T, K>(d, Pr, x0, l, i, j);
+    } else {
+      g = gradT3_pt<T, K>(d, Pt, x0, l, i, j);
+    }
+    X[q] = xq - tu * g;
   }
 }
 
