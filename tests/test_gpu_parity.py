@@ -361,7 +361,8 @@ def test_host_loop_matches_graph_loop(precision, fused, kind, op, p, bc, shape):
     uk = _state(pb, 13)
     res = []
     for loop in ("graph", "host"):
-        with rd.Solver(pb, precision=precision, solve_loop=loop, fused_update=fused) as s:
+        # small_solve = 0: these grids would otherwise run each inner solve in one launch
+        with rd.Solver(pb, precision=precision, solve_loop=loop, fused_update=fused, small_solve=0) as s:
             assert s.stats()["fused_update"] == fused
             out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
             info = s.step(dev(uk), out)
@@ -451,7 +452,7 @@ def test_fused_update_matches_oracle(kind, op, p, bc, shape, upd_rows):
     pb = _problem(kind, op, p, bc, *shape)
     uk = _state(pb, 18)
     rd = _rd()
-    with rd.Solver(pb, precision="fp32_dc", fused_update=1, upd_rows=upd_rows) as s:
+    with rd.Solver(pb, precision="fp32_dc", fused_update=1, upd_rows=upd_rows, small_solve=0) as s:
         assert s.stats()["fused_update"] == 1
         out = torch.empty(pb.shape, dtype=torch.float64, device="cuda")
         info = s.step(dev(uk), out)
@@ -472,7 +473,8 @@ def test_fused_update_twenty_steps_match_unfused():
         w = WL.config_allen_cahn_periodic()
         pb = w.problem.replace(tol_kind="f_rel", tol=1e-11)
         u = dev(w.u0)
-        with rd.Solver(pb, precision="fp32_dc", fused_update=fu) as s:
+        with rd.Solver(pb, precision="fp32_dc", fused_update=fu, small_solve=0) as s:
+            assert s.stats()["fused_update"] == fu
             infos, st = s.solve(u, w.nsteps)
         assert st == 0
         outs.append(host(u))
