@@ -106,7 +106,8 @@ inline cudaError_t record(cudaStream_t s, cudaEvent_t* ev, int i, unsigned flags
 template <class T, int AX, int MODE>
 cudaError_t launch_lines(const Desc& d, State* st, cudaStream_t s) {
   const int n = AX == 0 ? d.nx : (AX == 1 ? d.ny : d.nz);
-  const int smem = lines3_smem_bytes<T>(n, d.lw3[AX], d.bc == BC_NEUMANN);
+  const bool pf = AX == 0 && MODE == L3_INVP && sizeof(T) == 4 && d.thr3[AX] > 256 && d.pf3;
+  const int smem = lines3_smem_bytes<T>(n, d.lw3[AX], d.bc == BC_NEUMANN, pf);
   // the passes of a 2-D grid (x: forward, inverse with the dual update, inverse; y: the scaled
   // pass) on lines of 4096 and 8192 points, which plan3 gives n / 8 threads
   constexpr bool two_d_pass = (AX == 0 && (MODE == L3_FWD || MODE == L3_INVP || MODE == L3_INVX)) ||
@@ -231,6 +232,7 @@ template cudaError_t allow3<double>(int);
 
 bool plan3(int nx, int ny, int nz, int nc, int elem_bytes, bool neumann, int smem_limit, Desc& d, const char** why) {
   const size_t npts = (size_t)nx * ny * nz;
+  d.pf3 = 0;
   d.blk3 = (int)std::max<size_t>(1, std::min<size_t>(1024, (npts + 2047) / 2048));
   const int n_ax[3] = {nx, ny, nz};
   const int lanes = elem_bytes == 4 ? 16 : 8;
@@ -261,6 +263,8 @@ bool plan3(int nx, int ny, int nz, int nc, int elem_bytes, bool neumann, int sme
       }
       d.lw3[a] = lwl;
       d.thr3[a] = line_thr;
+      // x lines in FP32: the inverse pass with the dual update prefetches its rows of P
+      if (a == 0 && elem_bytes == 4) d.pf3 = lines3_smem_bytes<float>(n, lwl, neumann, true) <= smem_limit;
       continue;
     }
     int lw = std::min(lanes, avail[a]);

@@ -50,6 +50,18 @@ struct G3r {
   }
 };
 
+// Asynchronous copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to
+// shared memory by the whole block, 16 bytes per copy (cp.async, completion awaited by
+// cp_async_wait_all and a block barrier).
+__device__ __forceinline__ void cp_async_block(void* smem_dst, const void* gsrc, int bytes) {
+  const unsigned s0 = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const char* g0 = static_cast<const char*>(gsrc);
+  for (int o = 16 * threadIdx.x; o < bytes; o += 16 * blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s0 + o), "l"(g0 + o) : "memory");
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Do the rows and planes of a radius-R stencil around row (l, i) lie inside the grid?
 template <int R>
 __device__ __forceinline__ bool inside_yz(const Desc& d, int l, int i) {
@@ -281,11 +293,19 @@ __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ s
   cx<T>* buf = reinterpret_cast<cx<T>*>(place_tables<T>(smem_raw, twg, dcg, n, true, !per, tw, dc));
   T* __restrict__ WY = static_cast<T*>(d.WY);
   constexpr bool INV = MODE == L3_INV || MODE == L3_INVP || MODE == L3_INVX;
+  // the long x inverse pass with the dual update: the tile's rows of P are copied into shared
+  // memory behind the line buffer while the transform runs, so that the epilogue's reads of P
+  // do not wait on global memory after it (d.pf3: the copy fits)
+  constexpr bool PFC = LOGN > 0 && AX == 0 && MODE == L3_INVP && sizeof(T) == 4;
+  const bool pf = PFC && d.pf3;
+  T* Ps = reinterpret_cast<T*>(buf + nl * ls);
   for (long t = b; t < ntiles; t += d.blk3) {
     size_t sl;
     int orow;
     const size_t base = tile3<AX>(d, t, lw, &sl, &orow);
     __syncthreads();  // the tables are loaded / the previous tile's buffer is free
+    if constexpr (PFC)
+      if (pf) cp_async_block(Ps, static_cast<const T*>(d.P[0]) + base, lw * d.nx * (int)sizeof(T));
     // 1. load: spatial values (forward modes; Neumann in Makhoul order), or coefficients k in
     //    natural order (inverse modes; Neumann: the conjugated DCT-III preparation)
     if constexpr (!INV) {
@@ -439,6 +459,12 @@ __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ s
         const T tp = T(d.tau_p), tpe = T((1.0 + d.omega) * d.tau_p);
         T* P = static_cast<T*>(d.P[0]);
         T* dst = MODE == L3_INVX ? static_cast<T*>(d.X) : WY;
+        if constexpr (PFC) {
+          if (pf) {
+            cp_async_wait_all();
+            __syncthreads();
+          }
+        }
         for (int g = tid; g < nl * n; g += nt) {
           const int p = g / n, j = g - p * n;
           const cx<T> v0 = cur[p * ls + pidx(j)];
@@ -446,7 +472,14 @@ __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ s
           const T ya = v0.x, yb = per ? v0.y : -v0.y;
           const size_t oa = base + (size_t)(2 * p) * d.nx + jj, ob = oa + d.nx;
           if constexpr (MODE == L3_INVP) {
-            const T pa = P[oa], pb = P[ob];
+            T pa, pb;
+            if (PFC && pf) {
+              pa = Ps[oa - base];
+              pb = Ps[ob - base];
+            } else {
+              pa = P[oa];
+              pb = P[ob];
+            }
             P[oa] = pa + tp * ya;
             P[ob] = pb + tp * yb;
             dst[oa] = pa + tpe * ya;
@@ -469,10 +502,12 @@ __device__ __forceinline__ void lines3_body(const Desc& d, State* __restrict__ s
 }
 
 // Shared-memory bytes of a transform pass block: the tables of the line length and the lw / 2
-// complex lines of a tile.
+// complex lines of a tile (plus, with prefetch, the tile's lw rows of P).
 template <class T>
-__host__ __device__ inline int lines3_smem_bytes(int n, int lw, bool neumann) {
-  return table_bytes<T>(n, true, neumann) + (lw >> 1) * padded_len(n) * (int)sizeof(cx<T>);
+__host__ __device__ inline int lines3_smem_bytes(int n, int lw, bool neumann, bool prefetch = false) {
+  return table_bytes<T>(n, true, neumann) + (lw >> 1) * padded_len(n) * (int)sizeof(cx<T>) +
+         (prefetch ? lw * n * (int)sizeof(T) : 0);
 }
+
 
 }  // namespace rd

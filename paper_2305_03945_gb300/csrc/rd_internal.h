@@ -87,6 +87,7 @@ struct Desc {
   int blk3;
   int lw3[3];
   int thr3[3];       // threads per block of the transform pass of each axis
+  int pf3;           // 1: the long x inverse pass prefetches its P rows into shared memory
 };
 
 struct State {
