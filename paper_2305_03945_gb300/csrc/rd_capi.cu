@@ -403,8 +403,11 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   cudaGraph_t g = nullptr;
   RD_CUDA(cudaGraphCreate(&g, 0));
   *out = g;
+  // one-launch inner solves in defect correction: the first graph holds the whole step, the outer
+  // rounds in a WHILE node (a round's inner solve is one launch, so no loop inside it)
+  const bool outer_loop = h->small && h->dc && first;
   cudaGraphConditionalHandle cond = 0;
-  if (!h->small) RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  if (!h->small || outer_loop) RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
   const Desc dd = h->dc ? h->h_desc[1] : h->h_desc[0];
   auto iteration = [&](cudaStream_t st, cudaEvent_t* ev, bool first_it) {
     if (h->small) return small_launch(h, st, ev);
@@ -430,7 +433,47 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   // fused update: the per-band halo copies of U start at U_0 = d = 0
   if (dd.fused && (e = cudaMemsetAsync(h->halo32, 0, h->halo_bytes, cs)) != cudaSuccess)
     return abort_capture(cs, "clearing the halo copies during capture", e);
-  if (h->small) {
+  // appends a WHILE node on `cond` to the capture in cs and captures body(stream) into it
+  auto while_node = [&](auto body) -> cudaError_t {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t r = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+    if (r != cudaSuccess) return r;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn = nullptr;
+    if ((r = cudaGraphAddNode(&wn, cg, deps, nullptr, ndeps, &cp)) != cudaSuccess) return r;
+    if ((r = cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+      return r;
+    if ((r = cudaStreamBeginCaptureToGraph(h->body_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return r;
+    r = body(h->body_stream);
+    cudaGraph_t body_out = nullptr;
+    const cudaError_t r2 = cudaStreamEndCapture(h->body_stream, &body_out);
+    return r != cudaSuccess ? r : r2;
+  };
+  if (outer_loop) {
+    // round 1 outside the loop (the profiling events around its inner solve cannot sit in a
+    // conditional body), then the rounds while the outer state is active: inner solve, u += d,
+    // FP64 residual and decision, loop condition
+    auto round = [&](cudaStream_t st, cudaEvent_t* ev) -> cudaError_t {
+      cudaError_t r = iteration(st, ev, true);
+      if (r == cudaSuccess) r = launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, st);
+      if (r == cudaSuccess) r = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, st);
+      if (r == cudaSuccess) r = launch_loop_cond(st0, cond, 1u, st);
+      return r;
+    };
+    if ((e = round(cs, h->opts.profile ? h->ev : nullptr)) != cudaSuccess)
+      return abort_capture(cs, "kernel launch during capture", e);
+    if ((e = while_node([&](cudaStream_t st) { return round(st, nullptr); })) != cudaSuccess)
+      return abort_capture(cs, "the outer-round loop node", e);
+  } else if (h->small) {
     // the whole inner solve is one launch: no loop node
     if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr, true)) != cudaSuccess)
       return abort_capture(cs, "kernel launch during capture", e);
@@ -470,8 +513,10 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
     return abort_capture(cs, "ending the loop body capture", e);
   }
   if (h->dc) {
-    e = launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, cs);
-    if (e == cudaSuccess) e = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, cs);
+    if (!outer_loop) {
+      e = launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, cs);
+      if (e == cudaSuccess) e = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, cs);
+    }
     if (e == cudaSuccess) e = launch_mass(d64, h->d_state + 2, h->U64, st0, nb, cs);
   } else {
     e = launch_mass(d64, h->d_state + 2, h->U64, nullptr, nb, cs);
@@ -1118,8 +1163,12 @@ rd_status graph_round(rd_pdhg* h, int which) {
   }
   h->stats.pdhg_iterations += updates;
   if (h->small) {
-    // one launch of the one-block inner solve per round graph
-    h->stats.kernel_launches += 1;
+    // one launch of the one-block inner solve per round graph; with the outer rounds on the
+    // device (the first graph of a defect-correction step) four launches per round (inner
+    // solve, u += d, FP64 residual, loop condition), counted by the outer state's trips, in
+    // place of the one round the count above assumes
+    if (h->dc && which == 0) h->stats.kernel_launches += 4LL * (long long)o.trips - 2;
+    else h->stats.kernel_launches += 1;
     if (h->opts.profile && sweeps > 0) {
       float ms = 0.f;
       RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
