@@ -185,9 +185,12 @@ typedef struct {
                              fits, and with autotune only where it measures faster; 0: never.
                              Fused and unfused inner iterates differ by FP32 rounding only.     */
     int small_solve;      /* 1 (default): FP32 defect correction on a 2-D grid small enough that
-                             every array of the inner solve fits one thread block's shared memory
-                             (about 8 K points: 64 x 64, 64 x 128, ...) runs each inner solve as ONE
-                             kernel launch, its iterations separated by block barriers; 0: never */
+                             every array of the inner solve fits on chip runs each inner solve as
+                             ONE kernel launch, its iterations separated by barriers: one block
+                             below 16 points a side (up to 4 K points), a cluster of eight blocks
+                             with distributed shared memory from 16 x 16 up to 16 K points; the
+                             outer rounds then loop on the device too (one graph launch and one
+                             host read per step); 0: never */
 } rd_opts;
 
 typedef struct {
@@ -212,7 +215,8 @@ typedef struct {
     int plan_col_width;          /* columns per CTA of the column transform chosen at create      */
     int plan_upd_rows;           /* rows per CTA of the update sweep (k_upd) chosen at create    */
     int fused_update;            /* 1 when the fused update + residual kernel (k_updres) runs      */
-    int small_solve;             /* 1 when each inner solve runs in one block (rd_opts.small_solve) */
+    int small_solve;             /* inner solves in one launch (rd_opts.small_solve): 1 one block,
+                                    2 a cluster of eight blocks, 0 the multi-kernel sweeps        */
     int line_kernels;            /* 1 when the iteration runs on the line-transform kernels (3-D
                                     grids; 2-D grids with a side beyond the band / column sweeps) */
 } rd_stats;
