@@ -200,6 +200,7 @@ struct rd_pdhg {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t body_stream = nullptr;  // captures the body of the device-side loop
+  cudaStream_t body_stream2 = nullptr; // captures a loop body nested in another (inner solves in the outer rounds)
   int dc = 0;
   // FP64 state and plain-path workspaces
   double* U64 = nullptr;
@@ -403,11 +404,15 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
   cudaGraph_t g = nullptr;
   RD_CUDA(cudaGraphCreate(&g, 0));
   *out = g;
-  // one-launch inner solves in defect correction: the first graph holds the whole step, the outer
-  // rounds in a WHILE node (a round's inner solve is one launch, so no loop inside it)
-  const bool outer_loop = h->small && h->dc && first;
-  cudaGraphConditionalHandle cond = 0;
-  if (!h->small || outer_loop) RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  // defect correction: the first graph holds the whole step, the outer rounds after the first in
+  // a WHILE node on the outer state (each round: the inner solve -- one launch, or iteration 1
+  // and a WHILE node over the rest -- then u += d, the FP64 residual and decision, the loop
+  // condition); the second graph, one host-driven round, is the fallback should the device loop
+  // reach its bound
+  const bool outer_loop = h->dc && first;
+  cudaGraphConditionalHandle cond = 0, cond_o = 0;
+  if (!h->small) RD_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  if (outer_loop) RD_CUDA(cudaGraphConditionalHandleCreate(&cond_o, g, 1, cudaGraphCondAssignDefault));
   const Desc dd = h->dc ? h->h_desc[1] : h->h_desc[0];
   auto iteration = [&](cudaStream_t st, cudaEvent_t* ev, bool first_it) {
     if (h->small) return small_launch(h, st, ev);
@@ -422,6 +427,58 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
     if (tmp && tmp != g) cudaGraphDestroy(tmp);
     return fail(RD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
+  // appends a WHILE node on handle `c` to the capture in stream `st` and captures body(bs) into
+  // its body graph; make_handle(body graph) may create handles on that graph first
+  auto while_node = [&](cudaStream_t st, cudaGraphConditionalHandle c, cudaStream_t bs, auto make_handle,
+                        auto body) -> cudaError_t {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t r = cudaStreamGetCaptureInfo(st, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+    if (r != cudaSuccess) return r;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = c;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn = nullptr;
+    if ((r = cudaGraphAddNode(&wn, cg, deps, nullptr, ndeps, &cp)) != cudaSuccess) return r;
+    if ((r = cudaStreamUpdateCaptureDependencies(st, &wn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+      return r;
+    cudaGraph_t bg = cp.conditional.phGraph_out[0];
+    if ((r = make_handle(bg)) != cudaSuccess) return r;
+    if ((r = cudaStreamBeginCaptureToGraph(bs, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return r;
+    r = body(bs);
+    cudaGraph_t body_out = nullptr;
+    const cudaError_t r2 = cudaStreamEndCapture(bs, &body_out);
+    return r != cudaSuccess ? r : r2;
+  };
+  auto no_handle = [](cudaGraph_t) { return cudaSuccess; };
+  // one inner solve on stream st: iteration 1 (with the profiling events when ev), then the
+  // WHILE node on handle c (body captured on stream bs) over graph_k iterations per trip
+  auto inner_solve = [&](cudaStream_t st, cudaEvent_t* ev, cudaGraphConditionalHandle c, cudaStream_t bs) -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    // fused update: the per-band halo copies of U start at U_0 = d = 0
+    if (dd.fused) r = cudaMemsetAsync(h->halo32, 0, h->halo_bytes, st);
+    if (r == cudaSuccess) r = iteration(st, ev, true);
+    if (h->small || r != cudaSuccess) return r;
+    if ((r = launch_loop_cond(sti, c, 1u, st)) != cudaSuccess) return r;
+    return while_node(st, c, bs, no_handle, [&](cudaStream_t b) {
+      cudaError_t q = cudaSuccess;
+      for (int k = 0; k < K && q == cudaSuccess; ++k) q = iteration(b, nullptr, false);
+      if (q == cudaSuccess) q = launch_loop_cond(sti, c, (unsigned)K, b);
+      return q;
+    });
+  };
+  // one outer round after the FP64 residual that armed it
+  auto round = [&](cudaStream_t st, cudaEvent_t* ev, cudaGraphConditionalHandle c, cudaStream_t bs) -> cudaError_t {
+    cudaError_t r = inner_solve(st, ev, c, bs);
+    if (r == cudaSuccess) r = launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, st);
+    if (r == cudaSuccess) r = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, st);
+    return r;
+  };
   RD_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   if (first) {
@@ -430,94 +487,34 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
     if (e == cudaSuccess && h->dc) e = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, cs);
     if (e != cudaSuccess) return abort_capture(cs, "step set-up during capture", e);
   }
-  // fused update: the per-band halo copies of U start at U_0 = d = 0
-  if (dd.fused && (e = cudaMemsetAsync(h->halo32, 0, h->halo_bytes, cs)) != cudaSuccess)
-    return abort_capture(cs, "clearing the halo copies during capture", e);
-  // appends a WHILE node on `cond` to the capture in cs and captures body(stream) into it
-  auto while_node = [&](auto body) -> cudaError_t {
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t cg = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    cudaError_t r = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
-    if (r != cudaSuccess) return r;
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t wn = nullptr;
-    if ((r = cudaGraphAddNode(&wn, cg, deps, nullptr, ndeps, &cp)) != cudaSuccess) return r;
-    if ((r = cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
-      return r;
-    if ((r = cudaStreamBeginCaptureToGraph(h->body_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-      return r;
-    r = body(h->body_stream);
-    cudaGraph_t body_out = nullptr;
-    const cudaError_t r2 = cudaStreamEndCapture(h->body_stream, &body_out);
-    return r != cudaSuccess ? r : r2;
-  };
-  if (outer_loop) {
-    // round 1 outside the loop (the profiling events around its inner solve cannot sit in a
-    // conditional body), then the rounds while the outer state is active: inner solve, u += d,
-    // FP64 residual and decision, loop condition
-    auto round = [&](cudaStream_t st, cudaEvent_t* ev) -> cudaError_t {
-      cudaError_t r = iteration(st, ev, true);
-      if (r == cudaSuccess) r = launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, st);
-      if (r == cudaSuccess) r = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, st);
-      if (r == cudaSuccess) r = launch_loop_cond(st0, cond, 1u, st);
-      return r;
-    };
-    if ((e = round(cs, h->opts.profile ? h->ev : nullptr)) != cudaSuccess)
-      return abort_capture(cs, "kernel launch during capture", e);
-    if ((e = while_node([&](cudaStream_t st) { return round(st, nullptr); })) != cudaSuccess)
-      return abort_capture(cs, "the outer-round loop node", e);
-  } else if (h->small) {
-    // the whole inner solve is one launch: no loop node
-    if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr, true)) != cudaSuccess)
-      return abort_capture(cs, "kernel launch during capture", e);
+  cudaEvent_t* ev1 = h->opts.profile ? h->ev : nullptr;
+  if (!h->dc) {
+    // FP64: the PDHG loop of the step
+    if ((e = inner_solve(cs, ev1, cond, h->body_stream)) != cudaSuccess)
+      return abort_capture(cs, "the PDHG loop", e);
+  } else if (outer_loop) {
+    // round 1 outside the outer loop (the profiling events cannot sit in a conditional body)
+    e = round(cs, ev1, cond, h->body_stream);
+    if (e == cudaSuccess) e = launch_loop_cond(st0, cond_o, 1u, cs);
+    if (e != cudaSuccess) return abort_capture(cs, "the first outer round", e);
+    cudaGraphConditionalHandle cond_i = 0;
+    e = while_node(
+        cs, cond_o, h->body_stream,
+        [&](cudaGraph_t bg) {
+          return h->small ? cudaSuccess : cudaGraphConditionalHandleCreate(&cond_i, bg, 1, cudaGraphCondAssignDefault);
+        },
+        [&](cudaStream_t b) {
+          cudaError_t q = round(b, nullptr, cond_i, h->body_stream2);
+          if (q == cudaSuccess) q = launch_loop_cond(st0, cond_o, 1u, b);
+          return q;
+        });
+    if (e != cudaSuccess) return abort_capture(cs, "the outer-round loop", e);
   } else {
-  if ((e = iteration(cs, h->opts.profile ? h->ev : nullptr, true)) != cudaSuccess ||
-      (e = launch_loop_cond(sti, cond, 1u, cs)) != cudaSuccess)
-    return abort_capture(cs, "kernel launch during capture", e);
-  // the WHILE node, appended to the capture after the first iteration
-  cudaStreamCaptureStatus cst;
-  cudaGraph_t cg = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t ndeps = 0;
-  if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps)) != cudaSuccess)
-    return abort_capture(cs, "cudaStreamGetCaptureInfo", e);
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = cond;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t wn = nullptr;
-  if ((e = cudaGraphAddNode(&wn, cg, deps, nullptr, ndeps, &cp)) != cudaSuccess)
-    return abort_capture(cs, "adding the loop node", e);
-  if ((e = cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
-    return abort_capture(cs, "cudaStreamUpdateCaptureDependencies", e);
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  if ((e = cudaStreamBeginCaptureToGraph(h->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
-      cudaSuccess)
-    return abort_capture(cs, "capturing the loop body", e);
-  for (int k = 0; k < K && e == cudaSuccess; ++k) e = iteration(h->body_stream, nullptr, false);
-  if (e == cudaSuccess) e = launch_loop_cond(sti, cond, (unsigned)K, h->body_stream);
-  if (e != cudaSuccess) {
-    abort_capture(h->body_stream, "loop body", e);
-    return abort_capture(cs, "kernel launch during capture", e);
-  }
-  cudaGraph_t body_out = nullptr;
-  if ((e = cudaStreamEndCapture(h->body_stream, &body_out)) != cudaSuccess)
-    return abort_capture(cs, "ending the loop body capture", e);
+    if ((e = round(cs, ev1, cond, h->body_stream)) != cudaSuccess)
+      return abort_capture(cs, "the outer round", e);
   }
   if (h->dc) {
-    if (!outer_loop) {
-      e = launch_axpy_dc(h->U64, h->D32, h->npts, st0, st1, cs);
-      if (e == cudaSuccess) e = resid64_any(h, st0, st1, h->U64, nullptr, h->r32, h->u32, h->D32, h->P32[0], 1, nb, cs);
-    }
-    if (e == cudaSuccess) e = launch_mass(d64, h->d_state + 2, h->U64, st0, nb, cs);
+    e = launch_mass(d64, h->d_state + 2, h->U64, st0, nb, cs);
   } else {
     e = launch_mass(d64, h->d_state + 2, h->U64, nullptr, nb, cs);
   }
@@ -886,6 +883,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   h->stream = static_cast<cudaStream_t>(stream);
   RD_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   RD_CUDA(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
+  RD_CUDA(cudaStreamCreateWithFlags(&h->body_stream2, cudaStreamNonBlocking));
 
   const int H = op == RD_OP_NEG_BIHARMONIC ? 2 : 1;  // the sixth-order kind plans only the preconditioner
   h->fch = rx->kind == RD_RX_FCH;
@@ -1178,9 +1176,17 @@ rd_status graph_round(rd_pdhg* h, int which) {
     return RD_OK;
   }
   // every k_res launch (active or not) is followed by k_col and k_upd in the graph, and
-  // k_loop_cond runs after the first and then after every graph_k of them
+  // k_loop_cond runs after the first and then after every graph_k of them; with the outer rounds
+  // on the device (the first graph of a defect-correction step) each round adds its own first
+  // iteration's loop condition and an outer loop condition, and the count above assumed one
+  // round of u += d and FP64 residual
   h->stats.kernel_launches += (long long)sweeps * h->kernels_per_iter;
-  h->stats.kernel_launches += sweeps > 0 ? 1 + (sweeps - 1) / h->opts.graph_k : 1;
+  if (h->dc && which == 0) {
+    const long long R = o.trips;
+    h->stats.kernel_launches += 4 * R - 2 + (sweeps - R) / h->opts.graph_k + (h->h_desc[1].fused ? R : 0);
+  } else {
+    h->stats.kernel_launches += sweeps > 0 ? 1 + (sweeps - 1) / h->opts.graph_k : 1;
+  }
   if (h->opts.profile && sweeps > 0) {
     float ms = 0.f;
     RD_CUDA(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
@@ -1578,6 +1584,7 @@ void rd_pdhg_destroy(rd_pdhg* h) {
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->body_stream) cudaStreamDestroy(h->body_stream);
+  if (h->body_stream2) cudaStreamDestroy(h->body_stream2);
   delete h;
 }
 

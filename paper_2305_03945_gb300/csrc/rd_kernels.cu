@@ -159,7 +159,9 @@ __global__ void k_loop_cond(State* __restrict__ st, cudaGraphConditionalHandle c
   volatile State* vs = st;
   const unsigned t = vs->trips + sweeps;
   vs->trips = t;
-  if (vs->status != ST_ACTIVE || t > (unsigned)vs->max_iter + kLoopSlack) cudaGraphSetConditional(cond, 0);
+  // set on every call (not only cleared): a loop nested in another loop's body starts each trip of
+  // the outer loop with the condition this call leaves
+  cudaGraphSetConditional(cond, (vs->status != ST_ACTIVE || t > (unsigned)vs->max_iter + kLoopSlack) ? 0u : 1u);
 }
 
 // u += d after an inner solve of defect correction, when `outer` is active and the inner solve
