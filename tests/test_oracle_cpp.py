@@ -148,3 +148,20 @@ def test_thread_count_does_not_change_results():
         outs.append(C.pdhg_step(w.problem, w.u0))
     C.set_threads(1)
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+def test_fixed_iteration_step_of_the_roofline_sweep():
+    """The roofline sweep's step form (threshold 0, max_iter = m, Section 2.1's loop with a
+    stopping rule that never holds): both oracles take exactly m updates, report not converged
+    and return the same U_m; U_m moves toward the step's solution as m grows."""
+    w = WL.config_allen_cahn_periodic_8192(n=32, fixed_iters=7)
+    pb = w.problem
+    U_n, info_n = O.pdhg_step(pb, w.u0)
+    U_c, info_c = C.pdhg_step(pb, w.u0)
+    assert info_n["status"] == O.NOT_CONVERGED and info_n["iterations"] == 7
+    assert info_c["status"] == C.NOT_CONVERGED and info_c["iterations"] == 7
+    assert np.max(np.abs(U_n - U_c)) <= 1e-12 * np.max(np.abs(U_n))
+    U_ref, info_ref = O.pdhg_step(pb.replace(tol=1e-12, tol_kind="f_rel", max_iter=10000), w.u0)
+    assert info_ref["status"] == O.OK
+    U_3, _ = O.pdhg_step(pb.replace(max_iter=3), w.u0)
+    assert np.linalg.norm(U_n - U_ref) < np.linalg.norm(U_3 - U_ref)
