@@ -351,14 +351,16 @@ cudaError_t fch_iteration(rd_pdhg* h, cudaStream_t s, cudaEvent_t* ev) {
 }
 
 // Capture one step graph.  Layout (FP64 plain, first = true):
-//   k_begin, P_0 = 0, iteration 1, WHILE { graph_k iterations }, k_mass
-// and for defect correction (first adds k_begin and the first FP64 residual in front):
-//   [k_begin, k_resid64], iteration 1, WHILE { graph_k iterations }, k_axpy_dc, k_resid64, k_mass
-// Iteration 1 sits outside the loop so that the profiling events (which a conditional body
-// cannot hold) bracket its three kernels.  The loop's condition starts at 1 on every launch;
-// k_loop_cond, run after iteration 1 and at the end of every trip, clears it once the solve has
-// ended (or after max_iter + slack k_res launches).  k_axpy_dc, the second k_resid64 and
-// k_mass act only while (resp. once no longer) the outer loop is active.
+//   k_begin, P_0 = 0, iteration 1, k_loop_cond, WHILE { graph_k iterations, k_loop_cond }, k_mass
+// and for defect correction, with ROUND = the inner solve (iteration 1, k_loop_cond and the
+// WHILE node above; or one small-solve launch), k_axpy_dc, k_resid64:
+//   first = true : k_begin, k_resid64, ROUND, k_loop_cond(outer), WHILE { ROUND, k_loop_cond(outer) }, k_mass
+//   first = false: ROUND, k_mass   (one host-driven round, the fallback beyond the loop's bound)
+// Iteration 1 and round 1 sit outside the loops so that the profiling events (which a conditional
+// body cannot hold) bracket the first iteration's kernels.  k_loop_cond, run after iteration 1
+// (round 1) and at the end of every trip, sets its loop's condition: 1 while the solve (the
+// outer state) is active, 0 once it has ended or after max_iter + slack launches.  k_axpy_dc,
+// k_resid64 and k_mass act only while (resp. once no longer) the outer state is active.
 // Step-level launches of either grid kind: the step set-up and the FP64 residual.
 cudaError_t begin_any(rd_pdhg* h, State* st, const double* uk, double tol, int tol_kind, int nb, cudaStream_t s) {
   if (h->nd3) return launch_begin3(h->h_desc[0], h->d_desc + 0, st, uk, h->rhs64, tol, tol_kind, s);

@@ -149,12 +149,12 @@ __global__ void __launch_bounds__(256)
 // the launches that find the solve already finished inside the last loop trip (<= 256 per trip).
 constexpr unsigned kLoopSlack = 1024;
 
-// Decision of the device-side PDHG loop (a WHILE node of the step's CUDA graph), taken by one
-// thread after the first iteration and at the end of every loop trip: adds the `sweeps` k_res
-// launches since the last check to st->trips, and clears the loop condition when the solve is
-// no longer active or, as a hard bound that holds whatever the stopping logic does, when the
-// launches exceed max_iter + kLoopSlack.  Kept out of the sweep kernels, which thereby use no
-// device-side graph API.
+// Decision of a device-side loop (a WHILE node of the step's CUDA graph: the PDHG loop, or the
+// outer rounds of defect correction), taken by one thread after the loop's first pass and at the
+// end of every trip: adds `sweeps` (k_res launches, or 1 per round) to st->trips, and sets the
+// loop condition to 0 when the solve is no longer active or, as a hard bound that holds
+// whatever the stopping logic does, when the count exceeds max_iter + kLoopSlack, else to 1.
+// Kept out of the sweep kernels, which thereby use no device-side graph API.
 __global__ void k_loop_cond(State* __restrict__ st, cudaGraphConditionalHandle cond, unsigned sweeps) {
   volatile State* vs = st;
   const unsigned t = vs->trips + sweeps;
