@@ -116,11 +116,21 @@ typedef struct {
 /* Preconditioner G of the dual proximal step (Section 2.1, "Choosing the matrix G"). */
 typedef enum {
     RD_PC_NONE = 0,      /* G = I: the plain linearised PDHG (eqs. illustrate pdhg dynamic 1-3) */
-    RD_PC_LINEAR = 1     /* G = A_lin^2, A_lin the constant-coefficient linear part of F:
+    RD_PC_LINEAR = 1,    /* G = A_lin^2, A_lin the constant-coefficient linear part of F:
                             (I - D dt Lap)^2 per species, or (I + a dt Lap^2)^2 (default)       */
+    RD_PC_STABILIZED = 2 /* G = A_s^2, A_s the Jacobian of F with its nonlinear factor replaced by
+                            the constant s (Section 3.3's construction of G, for any scalar
+                            reaction): Allen-Cahn (1 + b dt s) I - a dt Lap; Cahn-Hilliard
+                            I + a dt Lap^2 - b s dt Lap (s in place of W''(U), or of 3 U^2 for the
+                            convex split: 2, resp. 3, at u = +-1, where G equals the square of the
+                            exact Jacobian); sixth order with (s b - a) in place of (2b - a).
+                            Scalar reactions only (else RD_ERR_UNSUPPORTED).  Near u = +-1 it keeps
+                            PDHG convergent where RD_PC_LINEAR's iteration diverges (stiff
+                            reaction terms b dt).                                             */
 } rd_precond_kind;
 
-typedef struct { int kind; double s; } rd_precond;   /* s: reserved, must be 0 */
+typedef struct { int kind; double s; } rd_precond;   /* s: the RD_PC_STABILIZED constant (>= 0);
+                                                         0 for the other kinds */
 
 typedef enum {
     RD_TOL_RES_ABS = 0,  /* stop when sum_c ||F_c(U_n)||_2 / dt <= tol  (||Res||_2 <= delta)   */

@@ -26,7 +26,7 @@ _STATUS = {0: OK, 1: NOT_CONVERGED, 2: DIVERGED}
 _BC = {"periodic": 0, "neumann": 1}
 _OP = {"laplacian": 0, "neg_biharmonic": 1, "functionalized": 2}
 _KIND = {"none": 0, "allen_cahn": 1, "ch_implicit": 2, "ch_split": 3, "gray_scott": 4, "schnakenberg": 5, "fch": 6}
-_PC = {"none": 0, "linear": 1}
+_PC = {"none": 0, "linear": 1, "stabilized": 2}
 _TOL = {"res_abs": 0, "f_rel": 1}
 
 
@@ -37,7 +37,7 @@ class rdo_problem(ctypes.Structure):
                 ("p", ctypes.c_double * 6), ("tau_u", ctypes.c_double), ("tau_p", ctypes.c_double),
                 ("omega", ctypes.c_double), ("precond", ctypes.c_int), ("tol", ctypes.c_double),
                 ("tol_kind", ctypes.c_int), ("max_iter", ctypes.c_int), ("nz", ctypes.c_int),
-                ("lz", ctypes.c_double)]
+                ("lz", ctypes.c_double), ("shift", ctypes.c_double)]
 
 
 def up_to_date() -> bool:
@@ -101,6 +101,7 @@ def _problem(pb) -> rdo_problem:
     s.tau_u, s.tau_p, s.omega = pb.tau_u, pb.tau_p, pb.omega
     s.precond, s.tol, s.tol_kind, s.max_iter = _PC[pb.precond], pb.tol, _TOL[pb.tol_kind], pb.max_iter
     s.nz, s.lz = pb.nz, pb.lz
+    s.shift = pb.shift
     return s
 
 

@@ -206,11 +206,24 @@ def ghat(pb):
       functionalized    A_lin = I - dt Lap (a Lap - (2b - a) I) a Lap, W'' replaced by its value
                         2b at u = +-1 (Section 3.3)  ->  g = (1 + dt a mu^2 (a mu + 2b - a))^2
     precond 'none' gives G = I (plain linearised PDHG, eqs. illustrate pdhg dynamic 1-3).
+    precond 'stabilized' squares the Jacobian of F with its nonlinear factor replaced by the
+    constant s = pb.shift (Section 3.3's idea, for any scalar reaction): Allen-Cahn
+    A = (1 + b dt s) I - a dt Lap; Cahn-Hilliard A = I + a dt Lap^2 - b s dt Lap (s in place of
+    W''(U), or of 3 U^2 for the convex split); sixth-order A as above with (s b - a).
     """
     if pb.precond == "none":
         return np.ones(pb.shape)
     mu = symbol_mu(pb)
     dt = pb.dt
+    if pb.precond == "stabilized":
+        if pb.kind not in ("allen_cahn", "ch_implicit", "ch_split", "fch"):
+            raise ValueError("the stabilized preconditioner needs a scalar reaction")
+        s = pb.shift
+        if pb.op == "laplacian":
+            return ((1 + pb.b * dt * s + pb.a * dt * mu) ** 2)[None]
+        if pb.op == "functionalized":
+            return ((1 + dt * pb.a * mu ** 2 * (pb.a * mu + s * pb.b - pb.a)) ** 2)[None]
+        return ((1 + pb.b * s * dt * mu + pb.a * dt * mu ** 2) ** 2)[None]
     if pb.kind in ("gray_scott", "schnakenberg"):
         d1, d2 = pb.p[0], pb.p[1]
         return np.stack([(1 + d1 * dt * mu) ** 2, (1 + d2 * dt * mu) ** 2])

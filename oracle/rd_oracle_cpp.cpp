@@ -39,7 +39,7 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 enum { BC_PERIODIC = 0, BC_NEUMANN = 1 };
 enum { OP_LAPLACIAN = 0, OP_NEG_BIHARMONIC = 1, OP_FUNCTIONALIZED = 2 };
 enum { K_NONE = 0, K_AC = 1, K_CH_IMPLICIT = 2, K_CH_SPLIT = 3, K_GRAY_SCOTT = 4, K_SCHNAKENBERG = 5, K_FCH = 6 };
-enum { PC_NONE = 0, PC_LINEAR = 1 };
+enum { PC_NONE = 0, PC_LINEAR = 1, PC_STABILIZED = 2 };
 enum { TOL_RES_ABS = 0, TOL_F_REL = 1 };
 enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_DIVERGED = 2 };
 constexpr double kDivergeFactor = 1e8;
@@ -56,12 +56,14 @@ typedef struct {
   double dt, a, b;     // h_t and the diffusion / reaction scales
   double p[6];         // Gray-Scott (Du, Dv, F, k); Schnakenberg (D1, D2, kappa, a, b)
   double tau_u, tau_p, omega;
-  int precond;         // PC_NONE (G = I) or PC_LINEAR (G = A_lin^2)
+  int precond;         // PC_NONE (G = I), PC_LINEAR (G = A_lin^2) or PC_STABILIZED (A_lin with
+                       // the nonlinear factor replaced by the constant `shift`, squared)
   double tol;
   int tol_kind;
   int max_iter;
   int nz;              // points along z of a 3-D grid (1: a 2-D grid)
   double lz;           // side length along z; h_z = lz / nz
+  double shift;        // PC_STABILIZED: the constant in place of the nonlinear factor
 } rdo_problem;
 
 }  // extern "C"
@@ -365,10 +367,13 @@ vec ghat(const rdo_problem& pb) {
     for (size_t q = 0; q < n; ++q) {
       const double m = mu[q];
       double r;
+      const bool stab = pb.precond == PC_STABILIZED;
+      const double s = pb.shift;
       if (nc == 2) r = 1.0 + pb.p[c] * dt * m;                                          // (I - D dt Lap)
-      else if (pb.op == OP_LAPLACIAN) r = 1.0 + pb.a * dt * m;                          // (I - a dt Lap)
-      else if (pb.op == OP_FUNCTIONALIZED) r = 1.0 + dt * pb.a * m * m * (pb.a * m + 2.0 * pb.b - pb.a);
-      else r = 1.0 + pb.a * dt * m * m;                                                 // (I + a dt Lap^2)
+      else if (pb.op == OP_LAPLACIAN) r = 1.0 + (stab ? pb.b * dt * s : 0.0) + pb.a * dt * m;  // ((1 + b dt s) I - a dt Lap)
+      else if (pb.op == OP_FUNCTIONALIZED)
+        r = 1.0 + dt * pb.a * m * m * (pb.a * m + (stab ? s : 2.0) * pb.b - pb.a);
+      else r = 1.0 + (stab ? pb.b * s * dt * m : 0.0) + pb.a * dt * m * m;             // (I + a dt Lap^2 - b s dt Lap)
       g[c * n + q] = r * r;
     }
   return g;

@@ -194,6 +194,7 @@ struct rd_pdhg {
   double hz = 0;
   size_t npts = 0;  // nc * nx * ny * nz
   int bc = 0, op = 0, kind = 0, precond = 1;
+  double pc_shift = 0;  // RD_PC_STABILIZED: the constant in place of the nonlinear factor
   double dt = 0, tau = 0, sigma = 0, hx = 0, hy = 0;
   rd_reaction rx{};
   rd_opts opts{};
@@ -313,25 +314,35 @@ void host_mu_z(const rd_pdhg* h, std::vector<double>& mz) {
   }
 }
 
+// RD_PC_STABILIZED (scalar reactions): the Jacobian of F with its nonlinear factor replaced by
+// the constant s (Section 3.3's construction of G), squared:
+//   Allen-Cahn      (1 + b dt s) + a dt mu      = c0 (1 + (a dt / c0) mu): gc1 = a dt / c0 and
+//                   the constant c0^2 folded into the normalisation inv_nn
+//   Cahn-Hilliard   1 + b s dt mu + a dt mu^2   (s in place of W''(U), or of 3 U^2 for the split)
+//   sixth order     1 + dt a (s b - a) mu^2 + dt a^2 mu^3 (RD_PC_LINEAR: s = 2)
 void symbol_coefficients(const rd_pdhg* h, Desc& d) {
+  const bool stab = h->precond == RD_PC_STABILIZED;
+  const double s = h->pc_shift;
+  double c0 = 1.0;
   for (int c = 0; c < 2; ++c) {
     double D = h->rx.a;
     if (h->kind == RD_RX_GRAY_SCOTT || h->kind == RD_RX_SCHNAKENBERG) D = h->rx.p[c < h->nc ? c : 0];
     d.gc3[c] = 0.0;
     if (h->op == RD_OP_LAPLACIAN) {
-      d.gc1[c] = D * h->dt;
+      if (stab) c0 = 1.0 + h->rx.b * h->dt * s;
+      d.gc1[c] = D * h->dt / c0;
       d.gc2[c] = 0.0;
     } else if (h->op == RD_OP_FUNCTIONALIZED) {
       // G = (I - dt Lap (a Lap - (2b - a) I) a Lap)^2: 1 + dt a (2b - a) mu^2 + dt a^2 mu^3
       d.gc1[c] = 0.0;
-      d.gc2[c] = h->dt * h->rx.a * (2.0 * h->rx.b - h->rx.a);
+      d.gc2[c] = h->dt * h->rx.a * ((stab ? s : 2.0) * h->rx.b - h->rx.a);
       d.gc3[c] = h->dt * h->rx.a * h->rx.a;
     } else {
-      d.gc1[c] = 0.0;
+      d.gc1[c] = stab ? h->rx.b * s * h->dt : 0.0;
       d.gc2[c] = h->rx.a * h->dt;
     }
   }
-  d.inv_nn = 1.0 / ((double)h->nx * (double)h->ny * (double)h->nz);
+  d.inv_nn = 1.0 / ((double)h->nx * (double)h->ny * (double)h->nz * c0 * c0);
 }
 
 rd_status status_of(int st) {
@@ -643,8 +654,16 @@ rd_status validate(const rd_grid* grid, rd_bc bc, rd_operator op, const rd_react
   if ((rx->kind == RD_RX_CH_IMPLICIT || rx->kind == RD_RX_CH_SPLIT) && op != RD_OP_NEG_BIHARMONIC)
     return fail(RD_ERR_INVALID_ARG, "Cahn-Hilliard needs RD_OP_NEG_BIHARMONIC");
   if (two && (!(rx->p[0] >= 0) || !(rx->p[1] >= 0))) return fail(RD_ERR_INVALID_ARG, "diffusivities must be >= 0");
-  if (pc && pc->kind != RD_PC_NONE && pc->kind != RD_PC_LINEAR) return fail(RD_ERR_UNSUPPORTED, "preconditioner kind not built");
-  if (pc && pc->s != 0.0) return fail(RD_ERR_UNSUPPORTED, "preconditioner shift s must be 0");
+  if (pc && pc->kind != RD_PC_NONE && pc->kind != RD_PC_LINEAR && pc->kind != RD_PC_STABILIZED)
+    return fail(RD_ERR_INVALID_ARG, "bad preconditioner kind");
+  if (pc && pc->kind == RD_PC_STABILIZED) {
+    if (rx->kind != RD_RX_ALLEN_CAHN && rx->kind != RD_RX_CH_IMPLICIT && rx->kind != RD_RX_CH_SPLIT &&
+        rx->kind != RD_RX_FCH)
+      return fail(RD_ERR_UNSUPPORTED, "the stabilized preconditioner is built for the scalar reactions");
+    if (!(pc->s >= 0) || !std::isfinite(pc->s)) return fail(RD_ERR_INVALID_ARG, "stabilized shift s must be >= 0");
+  } else if (pc && pc->s != 0.0) {
+    return fail(RD_ERR_INVALID_ARG, "the shift s belongs to RD_PC_STABILIZED and must be 0 otherwise");
+  }
   if (o) {
     if (!(o->tol >= 0)) return fail(RD_ERR_INVALID_ARG, "tol must be >= 0");
     if (o->tol_kind != RD_TOL_RES_ABS && o->tol_kind != RD_TOL_F_REL) return fail(RD_ERR_INVALID_ARG, "bad tol_kind");
@@ -875,6 +894,7 @@ rd_status create_impl(rd_pdhg* h, const rd_grid* grid, rd_bc bc, rd_operator op,
   h->op = op;
   h->kind = rx->kind;
   h->precond = pc ? pc->kind : RD_PC_LINEAR;
+  h->pc_shift = pc && pc->kind == RD_PC_STABILIZED ? pc->s : 0.0;
   h->rx = *rx;
   h->dt = dt;
   h->tau = tau;

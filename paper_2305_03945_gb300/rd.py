@@ -20,7 +20,7 @@ BC = {"periodic": 0, "neumann": 1}
 OP = {"laplacian": 0, "neg_biharmonic": 1, "functionalized": 2}
 KIND = {"none": 0, "allen_cahn": 1, "ch_implicit": 2, "ch_split": 3, "gray_scott": 4, "schnakenberg": 5,
         "fch": 6}
-PRECOND = {"none": 0, "linear": 1}
+PRECOND = {"none": 0, "linear": 1, "stabilized": 2}
 TOL = {"res_abs": 0, "f_rel": 1}
 PREC = {"fp64": 0, "fp32_dc": 1}
 
@@ -201,7 +201,7 @@ def make_structs(pb, precision="fp64", graph_k=2, band_rows=0, col_width=0, dc_i
     rx.a, rx.b = pb.a, pb.b
     for k, v in enumerate(pb.p):
         rx.p[k] = v
-    pc = rd_precond(PRECOND[pb.precond], 0.0)
+    pc = rd_precond(PRECOND[pb.precond], getattr(pb, "shift", 0.0) if pb.precond == "stabilized" else 0.0)
     o = rd_opts()
     load().rd_opts_default(ctypes.byref(o))
     o.tol = pb.tol

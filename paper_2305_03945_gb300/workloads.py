@@ -47,7 +47,12 @@ class Problem:
     dt              physical time step h_t
     tau_u, tau_p    PDHG primal / dual step sizes
     omega           extrapolation coefficient (1 in all of the paper's experiments)
-    precond         'linear' (G = A_lin^2, Section 2.1 "Choosing the matrix G") or 'none'
+    precond         'linear' (G = A_lin^2, Section 2.1 "Choosing the matrix G"), 'none', or
+                    'stabilized' (A_lin with the nonlinear factor replaced by the constant `shift`,
+                    the idea of Section 3.3)
+    shift           the constant of the 'stabilized' preconditioner: in place of W''(U) for
+                    Allen-Cahn, implicit Cahn-Hilliard and the sixth-order equation, of 3 U^2
+                    for the convex split (2, resp. 3, at u = +-1)
     tol, tol_kind   'res_abs': stop when sum_c ||F_c(U)||_2 / dt <= tol   (Section 2.1 stopping rule)
                     'f_rel'  : stop when sum_c ||F_c(U)||_2 <= tol * ||U^k||_2
     max_iter        cap on PDHG iterations per time step
@@ -71,6 +76,7 @@ class Problem:
     tau_p: float = 0.8
     omega: float = 1.0
     precond: str = "linear"
+    shift: float = 0.0
     tol: float = 1e-10
     tol_kind: str = "res_abs"
     max_iter: int = 10000
