@@ -88,3 +88,20 @@ def test_stabilized_keeps_the_iteration_convergent_near_the_equilibria(kind, op,
     assert info["status"] == O.OK
     r, thr = O.measure(WL.Problem(precond="stabilized", **base), O.residual(WL.Problem(**base), U, u0), u0)
     assert r <= thr
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("kind,op,s", CASES)
+def test_stabilized_with_s_0_is_the_linear_G(bc, kind, op, s):
+    """With the nonlinear factor set to 0 the Jacobian is the linear part's: G = A_lin^2."""
+    pb = _pb(kind, op, bc, 16, 0.0)
+    lin = pb.replace(precond="linear", shift=0.0)
+    for M in (O, C):
+        g0, gl = M.ghat(pb), M.ghat(lin)
+        assert np.max(np.abs(g0 - gl)) <= 1e-14 * np.max(gl)
+    uk = WL.rng(6).uniform(-0.9, 0.9, pb.shape)
+    p0 = pb.replace(tau_u=0.9, tau_p=0.9, tol=1e-12, tol_kind="f_rel", max_iter=3000)
+    U0, i0 = O.pdhg_step(p0, uk)
+    Ul, il = O.pdhg_step(p0.replace(precond="linear"), uk)
+    assert i0["iterations"] == il["iterations"]
+    assert np.max(np.abs(U0 - Ul)) <= 1e-14 * np.max(np.abs(Ul))
