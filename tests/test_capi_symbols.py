@@ -59,3 +59,30 @@ def test_status_strings_and_argument_checks_without_gpu():
                            ctypes.byref(pc), ctypes.byref(o), None)
     assert s == rd.RD_ERR_INVALID_ARG
     assert lib.rd_pdhg_step(None, None, None, None) == rd.RD_ERR_INVALID_ARG
+    rx.ncomp = 1
+
+
+def test_preconditioner_arguments_checked_without_gpu():
+    """RD_PC_STABILIZED: s >= 0 and finite; the shift belongs to that kind alone; two-species
+    systems refuse it (no scalar nonlinear factor); unknown kinds are invalid."""
+    from paper_2305_03945_gb300 import build, rd, workloads as WL
+    build.build()
+    lib = rd.load()
+    h = ctypes.c_void_p()
+
+    def create(pb, kind, shift):
+        g, rx, pc, o = rd.make_structs(pb)
+        pc.kind, pc.s = kind, shift
+        return lib.rd_pdhg_create(ctypes.byref(h), ctypes.byref(g), rd.BC[pb.bc], rd.OP[pb.op], ctypes.byref(rx),
+                                  pb.dt, pb.tau_u, pb.tau_p, ctypes.byref(pc), ctypes.byref(o), None)
+
+    ac = WL.config_allen_cahn_periodic(16, 1).problem
+    for shift in (-1.0, float("nan"), float("inf")):
+        assert create(ac, rd.PRECOND["stabilized"], shift) == rd.RD_ERR_INVALID_ARG and not h.value
+        assert b"shift" in lib.rd_last_error()
+    assert create(ac, rd.PRECOND["linear"], 2.0) == rd.RD_ERR_INVALID_ARG
+    assert create(ac, rd.PRECOND["none"], 2.0) == rd.RD_ERR_INVALID_ARG
+    assert create(ac, 3, 0.0) == rd.RD_ERR_INVALID_ARG and b"preconditioner kind" in lib.rd_last_error()
+    gs = WL.Problem(nx=16, ny=16, lx=1.0, ly=1.0, bc="periodic", op="laplacian", kind="gray_scott",
+                    p=(2e-3, 1e-3, 0.04, 0.06), dt=1.0)
+    assert create(gs, rd.PRECOND["stabilized"], 2.0) == rd.RD_ERR_UNSUPPORTED and not h.value
