@@ -105,3 +105,16 @@ def test_stabilized_with_s_0_is_the_linear_G(bc, kind, op, s):
     Ul, il = O.pdhg_step(p0.replace(precond="linear"), uk)
     assert i0["iterations"] == il["iterations"]
     assert np.max(np.abs(U0 - Ul)) <= 1e-14 * np.max(np.abs(Ul))
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("kind,op,s", CASES)
+@pytest.mark.parametrize("value", [1.0, -1.0])
+def test_stabilized_G_on_3d_grids_is_the_squared_jacobian_at_the_equilibria(bc, kind, op, s, value):
+    """The same construction with a third axis (the Kronecker-sum Laplacian of the dense module)."""
+    pb = _pb(kind, op, bc, 4, s, nz=4, ny=4, nx=8, lx=1.0, ly=0.8, lz=1.3)
+    J = D.jacobian(pb, np.full(pb.nx * pb.ny * pb.nz, value))
+    x = WL.rng(4).standard_normal(pb.shape)
+    GX = (J @ (J @ x.ravel())).reshape(pb.shape)
+    assert np.max(np.abs(O.apply_ginv(pb, GX) - x)) <= 1e-12
+    assert np.max(np.abs(C.apply_ginv(pb, GX) - x)) <= 1e-12
