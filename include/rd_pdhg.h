@@ -308,8 +308,9 @@ RD_API rd_status rd_pdhg_solve_adaptive(rd_pdhg *h, double *u, const rd_adapt *a
  * (eq. F(U) rd equation / F(U) CH / Section 3.4.1). */
 RD_API rd_status rd_pdhg_residual(rd_pdhg *h, const double *u, const double *u_k, double *w);
 
-/* Y <- G^{-1} W (device, FP64): the preconditioner solve of eq. G-prox dynamic 1, by 2-D
- * FFT-type (periodic) or DCT-II (Neumann) transforms.  y may alias w. */
+/* Y <- G^{-1} W (device, FP64): the preconditioner solve of eq. G-prox dynamic 1 with the
+ * handle's G (rd_precond_kind: A_lin^2, A_s^2, or I), by FFT-type (periodic) or DCT-II (Neumann)
+ * transforms along every axis.  y may alias w. */
 RD_API rd_status rd_pdhg_apply_precond(rd_pdhg *h, const double *w, double *y);
 
 /* Copy the handle's counters to *out (host). */
@@ -323,8 +324,8 @@ RD_API void rd_pdhg_destroy(rd_pdhg *h);
  * same method).  Every request is an independent run of nsteps implicit steps of one equation
  * (RD_RX_NONE, Allen-Cahn, Cahn-Hilliard, Gray-Scott or Schnakenberg; 2-D grids with sides powers
  * of two in [4, 1024], or -- scalar kinds -- 3-D grids with sides in [4, 512]; either boundary
- * condition) solved with FP32 PDHG sweeps inside FP64 defect correction to the request's
- * tolerance.  Small 2-D requests (up to 16 K points) run each inner solve in one launch
+ * condition) solved with FP32 PDHG sweeps (G = A_lin^2, RD_PC_LINEAR) inside FP64 defect
+ * correction to the request's tolerance.  Small 2-D requests (up to 16 K points) run each inner solve in one launch
  * (rd_opts.small_solve).  The batch owns one device arena of hbm_budget_bytes; a request is
  * admitted when a slot is free and its workspace (about 48 bytes per grid point) fits the
  * arena, its state then stays resident on the GPU across all its steps, and all admitted
@@ -392,8 +393,8 @@ RD_API void rd_batch_destroy(rd_batch *b);
  * exists for callers that cannot allocate device memory when they need the operator -- code
  * running inside a fixed memory budget it does not own, latency-critical loops that must not
  * pay the device-wide synchronisation of cudaMalloc / cudaFree, or callers holding no solver
- * handle.  It computes the same G = A_lin^2 solve as rd_pdhg_apply_precond for the equation
- * described by (grid, bc, op, reaction, dt), with its scratch (transform buffer, twiddle and
+ * handle.  It computes the same G = A_lin^2 solve as rd_pdhg_apply_precond of an RD_PC_LINEAR
+ * handle for the 2-D equation described by (grid, bc, op, reaction, dt), with its scratch (transform buffer, twiddle and
  * eigenvalue tables) in one static device array of 2.5 MiB that every device loading the
  * library holds until process exit.
  *   w, y: device arrays of ncomp*ny*nx doubles (caller-owned; y may alias w).
