@@ -390,7 +390,9 @@ struct rd_batch {
   int smem_sweep2 = 0;  // the band kernels of the two-species kinds
   // measured tiles per grid size (index log2 of the longer side; 0 = not measured)
   int tune_band[16] = {}, tune_col[16] = {};
-  // queues
+  // queues.  mu guards the queues, outputs, stats, worker_error, stop and the arena's free list
+  // (allocated and released by the worker, read by rd_batch_get_stats); never held across a
+  // CUDA call that waits on the device.
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Request> queue;
@@ -735,7 +737,11 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   if (s < 0) return false;
   size_t npts = 0;
   const size_t bytes = slot_bytes(q.req, &npts);
-  char* mem = b->arena.alloc(bytes);
+  char* mem = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    mem = b->arena.alloc(bytes);
+  }
   if (!mem) return false;
   SlotHost& sh = b->slots[s];
   sh.used = true;
@@ -751,6 +757,7 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   sh.nd3 = false;
   if (q.req.grid.ndim == 3) {
     admit3(b, q, s, mem, npts, err);
+    std::lock_guard<std::mutex> lk(b->mu);
     b->stats.admitted += 1;
     return true;
   }
@@ -872,6 +879,7 @@ bool admit(rd_batch* b, Request& q, rd_status* err) {
   // the host vectors above are pageable: wait for the copies before they go out of scope
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) *err = bfail(RD_ERR_CUDA, std::string("admission: ") + cudaGetErrorString(e));
+  std::lock_guard<std::mutex> lk(b->mu);
   b->stats.admitted += 1;
   return true;
 }
@@ -911,12 +919,14 @@ void retire(rd_batch* b, int s, const Slot& ctl) {
   res.t_submit = sh.t_submit;
   res.t_admit = sh.t_admit;
   res.t_done = now_s();
-  b->arena.release(sh.mem, sh.mem_bytes);
+  char* mem = sh.mem;
+  const size_t mem_bytes = sh.mem_bytes;
   Slot idle{};
   cudaMemcpyAsync(b->d_slots + s, &idle, sizeof(Slot), cudaMemcpyHostToDevice, b->stream);
   sh = SlotHost{};
-  b->stats.completed += 1;
   std::lock_guard<std::mutex> lk(b->mu);
+  b->arena.release(mem, mem_bytes);
+  b->stats.completed += 1;
   if (!copy_error.empty()) b->worker_error = copy_error;
   b->done.push_back(res);
   b->cv.notify_all();
@@ -1020,11 +1030,14 @@ rd_status tune_batch_tiles(rd_batch* b) {
     b->tune_band[lg] = bb;
     b->tune_col[lg] = bc;
     // release the scratch slot
-    b->arena.release(sh.mem, sh.mem_bytes);
+    {
+      std::lock_guard<std::mutex> lk(b->mu);
+      b->arena.release(sh.mem, sh.mem_bytes);
+      b->stats.admitted -= 1;
+    }
     Slot idle{};
     cudaMemcpyAsync(b->d_slots + s, &idle, sizeof(Slot), cudaMemcpyHostToDevice, st);
     sh = SlotHost{};
-    b->stats.admitted -= 1;
   }
   cudaStreamSynchronize(st);
   cudaEventDestroy(e0);
@@ -1083,7 +1096,10 @@ void worker_loop(rd_batch* b) {
       b->cv.notify_all();
       return;
     }
-    b->stats.graph_launches += 1;
+    {
+      std::lock_guard<std::mutex> lk(b->mu);
+      b->stats.graph_launches += 1;
+    }
     bool retired = false;
     for (int s = 0; s < b->max_slots; ++s) {
       if (!b->slots[s].used) continue;
