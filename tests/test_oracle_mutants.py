@@ -1,0 +1,254 @@
+"""Sensitivity of the oracle's pins, CPU only.
+
+Each case plants one plausible mistake in the numpy oracle and checks that a committed pin
+fails.  The mistakes include a dropped term, a wrong sign, index, coefficient or boundary rule,
+a transposed operand, a preconditioner not squared, an extrapolation left out, and a norm or
+threshold in the wrong units.  The mistake is a one-line textual change of the oracle's own
+source (`oracle/rd_oracle.py`), loaded as a separate module whose functions replace the
+oracle's for the duration of the case.  Each edited line must occur exactly once, so a later
+change to the oracle that removes it makes the case fail loudly instead of testing nothing.
+The pins are the functions of the other `tests/test_oracle_*.py` files, called unchanged: every
+one passes on the unmodified oracle, and at least one of a case's pins must fail on the mutant.
+"""
+import inspect
+import types
+
+import numpy as np
+import pytest
+
+import test_oracle_3d as T3
+import test_oracle_iteration as IT
+import test_oracle_operators as OPS
+import test_oracle_reactions as RX
+import test_oracle_stabilized as ST
+from oracle import rd_oracle
+
+SRC = inspect.getsource(rd_oracle)
+GS = (2e-3, 1e-3, 0.04, 0.06)
+SCH = (0.05, 1.0, 100.0, 0.1305, 0.7695)
+O = rd_oracle
+
+# the pins, by name: zero-argument calls of committed test functions
+PINS = {
+    "neumann_block_matrix": lambda: OPS.test_stencil_equals_paper_block_matrix("neumann", 4),
+    "periodic_block_matrix": lambda: OPS.test_stencil_equals_paper_block_matrix("periodic", 5),
+    "eigenmodes_rect_periodic": lambda: OPS.test_stencil_eigenmodes("periodic", (8, 32), (3, 2)),
+    "eigenmodes_rect_neumann": lambda: OPS.test_stencil_eigenmodes("neumann", (8, 32), (3, 2)),
+    "ginv_dense_ac_periodic": lambda: OPS.test_ginv_matches_dense_solve("periodic", "allen_cahn", "laplacian", ()),
+    "ginv_dense_none_neumann": lambda: OPS.test_ginv_matches_dense_solve("neumann", "none", "laplacian", ()),
+    "ginv_dense_ch_periodic": lambda: OPS.test_ginv_matches_dense_solve("periodic", "ch_implicit", "neg_biharmonic", ()),
+    "ginv_dense_gs_neumann": lambda: OPS.test_ginv_matches_dense_solve("neumann", "gray_scott", "laplacian", GS),
+    "ginv_dense_fch_periodic": lambda: OPS.test_ginv_matches_dense_solve("periodic", "fch", "functionalized", ()),
+    "dense_F_fch": lambda: OPS.test_residual_matches_dense_form("periodic", "fch", "functionalized", ()),
+    "adjoint_ac": lambda: OPS.test_adjoint_jacobian_by_complex_step("periodic", "allen_cahn", "laplacian", ()),
+    "adjoint_ch": lambda: OPS.test_adjoint_jacobian_by_complex_step("neumann", "ch_implicit", "neg_biharmonic", ()),
+    "adjoint_gs": lambda: OPS.test_adjoint_jacobian_by_complex_step("periodic", "gray_scott", "laplacian", GS),
+    "adjoint_sch": lambda: OPS.test_adjoint_jacobian_by_complex_step("neumann", "schnakenberg", "laplacian", SCH),
+    "adjoint_fch": lambda: OPS.test_adjoint_jacobian_by_complex_step("periodic", "fch", "functionalized", ()),
+    "ac_uniform_ode": lambda: RX.test_allen_cahn_uniform_step_is_the_ode_step(0.3, O),
+    "ac_mode_on_one": lambda: RX.test_allen_cahn_mode_on_a_steady_state("periodic", 2, 3, 1.0, O),
+    "ch_split_mode_0": lambda: RX.test_cahn_hilliard_split_mode("periodic", 1, 2, 0.0, O),
+    "ch_split_mode_045": lambda: RX.test_cahn_hilliard_split_mode("neumann", 3, 2, 0.45, O),
+    "ch_implicit_mode": lambda: RX.test_cahn_hilliard_implicit_mode("periodic", 1, 2, 0.45, O),
+    "gs_uniform_ode": lambda: RX.test_gray_scott_uniform_step_is_the_ode_step("periodic", 1.0, O),
+    "gs_mode_per_species": lambda: RX.test_gray_scott_mode_on_the_trivial_state_decays_per_species("periodic", 3, 1, O),
+    "sch_uniform_ode": lambda: RX.test_schnakenberg_uniform_step_is_the_ode_step(1 / 1000, O),
+    "recurrence_unit": lambda: IT.test_single_mode_history_matches_recurrence("periodic", "laplacian", (1.0, 1.0), 1.0, "linear"),
+    "recurrence_unequal": lambda: IT.test_single_mode_history_matches_recurrence("neumann", "laplacian", (0.5, 1.6), 1.0, "linear"),
+    "recurrence_omega": lambda: IT.test_single_mode_history_matches_recurrence("periodic", "neg_biharmonic", (0.9, 0.9), 0.5, "linear"),
+    "nilpotent": lambda: IT.test_unit_steps_are_nilpotent("neumann"),
+    "stop_rule_f_rel": lambda: IT.test_stopping_rule_checked_with_dense_residual("f_rel", 1e-11),
+    "stop_rule_res_abs": lambda: IT.test_stopping_rule_checked_with_dense_residual("res_abs", 1e-8),
+    "newton_ac": lambda: IT.test_nonlinear_step_matches_dense_newton("allen_cahn", "laplacian", (), "neumann"),
+    "stab_jacobian_ac": lambda: ST.test_stabilized_G_is_the_squared_jacobian_at_the_equilibria("periodic", "allen_cahn", "laplacian", 2.0, 1.0),
+    "stab_jacobian_ch": lambda: ST.test_stabilized_G_is_the_squared_jacobian_at_the_equilibria("neumann", "ch_implicit", "neg_biharmonic", 2.0, -1.0),
+    "lap3_kron": lambda: T3.test_seven_point_laplacian_is_the_kron_sum("periodic", (3, 4, 5), O),
+    "ginv3_dense_neumann": lambda: T3.test_3d_ginv_matches_dense_solve("neumann", "allen_cahn", "laplacian", (), O),
+}
+
+# (name, [(old line fragment, new fragment), ...], pins of which at least one must fail)
+MUTANTS = [
+    ("Neumann ghost mirrored about the boundary node",
+     [("idx = np.where(idx < 0, -1 - idx, idx)", "idx = np.where(idx < 0, -idx, idx)"),
+      ("idx = np.where(idx >= n, 2 * n - 1 - idx, idx)", "idx = np.where(idx >= n, 2 * n - 2 - idx, idx)")],
+     ["neumann_block_matrix"]),
+    ("periodic shift in the wrong direction on one side",
+     [("return np.roll(u, -step, axis=axis)", "return np.roll(u, -abs(step), axis=axis)")],
+     ["periodic_block_matrix", "eigenmodes_rect_periodic"]),
+    ("h_y taken equal to h_x",
+     [("return pb.lx / pb.nx, pb.ly / pb.ny", "return pb.lx / pb.nx, pb.lx / pb.nx")],
+     ["eigenmodes_rect_periodic", "eigenmodes_rect_neumann"]),
+    ("y second difference divided by h_x^2",
+     [("+ (_shift(u, -2, 1, pb.bc) + _shift(u, -2, -1, pb.bc) - 2 * u) / hy ** 2",
+       "+ (_shift(u, -2, 1, pb.bc) + _shift(u, -2, -1, pb.bc) - 2 * u) / hx ** 2")],
+     ["eigenmodes_rect_periodic"]),
+    ("z second difference divided by h_y^2",
+     [("- 2 * u) / spacing_z(pb) ** 2", "- 2 * u) / hy ** 2")],
+     ["lap3_kron"]),
+    ("Neumann eigenvalues at the periodic frequencies",
+     [('d = 1.0 if pb.bc == "periodic" else 2.0', "d = 1.0")],
+     ["ginv_dense_none_neumann"]),
+    ("eigenvalue factor 2 for 4",
+     [("mu = (4 / hx ** 2 *", "mu = (2 / hx ** 2 *")],
+     ["ginv_dense_ac_periodic"]),
+    ("3-D Neumann z eigenvalues at the periodic frequency",
+     [("np.sin(np.pi * kz / (d * pb.nz)) ** 2", "np.sin(np.pi * kz / pb.nz) ** 2")],
+     ["ginv3_dense_neumann"]),
+    ("Allen-Cahn reaction with the wrong sign",
+     [("f = -b * (U ** 3 - U)", "f = b * (U ** 3 - U)")],
+     ["ac_uniform_ode", "ac_mode_on_one"]),
+    ("Allen-Cahn W' = u^3 + u",
+     [("f = -b * (U ** 3 - U)", "f = -b * (U ** 3 + U)")],
+     ["ac_uniform_ode", "ac_mode_on_one"]),
+    ("Cahn-Hilliard fourth-order term with the other sign reading",
+     [("return U + dt * a * L(L(U)) - Uk - dt * b * L(U ** 3 - U)",
+       "return U - dt * a * L(L(U)) - Uk - dt * b * L(U ** 3 - U)")],
+     ["ch_implicit_mode"]),
+    ("Cahn-Hilliard implicit W' = u^3",
+     [("return U + dt * a * L(L(U)) - Uk - dt * b * L(U ** 3 - U)",
+       "return U + dt * a * L(L(U)) - Uk - dt * b * L(U ** 3)")],
+     ["ch_implicit_mode"]),
+    ("convex split: explicit term with the wrong sign",
+     [("- dt * b * L(U ** 3) + dt * b * L(Uk)", "- dt * b * L(U ** 3) - dt * b * L(Uk)")],
+     ["ch_split_mode_0"]),
+    ("convex split: U^3 taken explicitly",
+     [("- dt * b * L(U ** 3) + dt * b * L(Uk)", "- dt * b * L(Uk ** 3) + dt * b * L(Uk)")],
+     ["ch_split_mode_045"]),
+    ("Gray-Scott: u v^2 enters the u equation with a plus sign",
+     [("Fu = u - Uk[0] - dt * (Du * L(u) - u * v * v + Ff * (1 - u))",
+       "Fu = u - Uk[0] - dt * (Du * L(u) + u * v * v + Ff * (1 - u))")],
+     ["gs_uniform_ode"]),
+    ("Gray-Scott: feed term dropped",
+     [("- u * v * v + Ff * (1 - u))", "- u * v * v)")],
+     ["gs_uniform_ode", "gs_mode_per_species"]),
+    ("Gray-Scott: D_v diffuses u",
+     [("Du * L(u)", "Dv * L(u)")],
+     ["gs_mode_per_species"]),
+    ("Gray-Scott: kill rate dropped from v",
+     [("+ u * v * v - (Ff + k) * v)", "+ u * v * v - Ff * v)")],
+     ["gs_uniform_ode", "gs_mode_per_species"]),
+    ("Schnakenberg: linear decay with the wrong sign",
+     [("kap * (a_s - u + u * u * v)", "kap * (a_s + u + u * u * v)")],
+     ["sch_uniform_ode"]),
+    ("sixth order: the printed W'' = 3u^2",
+     [("return pb.a * lap(x, pb) - pb.b * (3 * U ** 2 - 1) * x + pb.a * x",
+       "return pb.a * lap(x, pb) - pb.b * (3 * U ** 2) * x + pb.a * x")],
+     ["dense_F_fch"]),
+    ("adjoint: Allen-Cahn reaction derivative dropped",
+     [("return Pt - dt * a * L(Pt) - dt * fprime * Pt", "return Pt - dt * a * L(Pt)")],
+     ["adjoint_ac"]),
+    ("adjoint: Cahn-Hilliard diag(W'') and Lap in the forward order",
+     [("return Pt + dt * a * L(L(Pt)) - dt * b * (3 * U ** 2 - 1) * L(Pt)",
+       "return Pt + dt * a * L(L(Pt)) - dt * b * L((3 * U ** 2 - 1) * Pt)")],
+     ["adjoint_ch"]),
+    ("adjoint: Gray-Scott coupling blocks not transposed",
+     [("+ dt * (v * v + Ff) * P - dt * v * v * Q", "+ dt * (v * v + Ff) * P + 2 * dt * u * v * Q"),
+      ("gv = Q - dt * Dv * L(Q) + 2 * dt * u * v * P", "gv = Q - dt * Dv * L(Q) - dt * v * v * P")],
+     ["adjoint_gs"]),
+    ("adjoint: Schnakenberg coupling sign",
+     [("kap * (-P + 2 * u * v * (P - Q))", "kap * (-P + 2 * u * v * (P + Q))")],
+     ["adjoint_sch"]),
+    ("adjoint: sixth-order W''' term dropped",
+     [("return Pt - dt * s + dt * b * _fch_mu(pb, U) * (6 * U) * q", "return Pt - dt * s")],
+     ["adjoint_fch"]),
+    ("preconditioner A_lin instead of A_lin^2",
+     [("return ((1 + pb.a * dt * mu) ** 2)[None]", "return (1 + pb.a * dt * mu)[None]")],
+     ["ginv_dense_ac_periodic"]),
+    ("biharmonic symbol mu instead of mu^2",
+     [("return ((1 + pb.a * dt * mu ** 2) ** 2)[None]", "return ((1 + pb.a * dt * mu) ** 2)[None]")],
+     ["ginv_dense_ch_periodic"]),
+    ("two species: D_1 for both symbols",
+     [("(1 + d2 * dt * mu) ** 2", "(1 + d1 * dt * mu) ** 2")],
+     ["ginv_dense_gs_neumann"]),
+    ("sixth-order symbol (2b + a) for (2b - a)",
+     [("(pb.a * mu + 2 * pb.b - pb.a)) ** 2)[None]", "(pb.a * mu + 2 * pb.b + pb.a)) ** 2)[None]")],
+     ["ginv_dense_fch_periodic"]),
+    ("stabilised Allen-Cahn symbol with the wrong sign of s",
+     [("(1 + pb.b * dt * s + pb.a * dt * mu)", "(1 - pb.b * dt * s + pb.a * dt * mu)")],
+     ["stab_jacobian_ac"]),
+    ("stabilised Cahn-Hilliard symbol with the wrong sign of s",
+     [("(1 + pb.b * s * dt * mu + pb.a * dt * mu ** 2)", "(1 - pb.b * s * dt * mu + pb.a * dt * mu ** 2)")],
+     ["stab_jacobian_ch"]),
+    ("periodic solve multiplies by the symbol",
+     [("np.fft.fftn(W, axes=ax) / g", "np.fft.fftn(W, axes=ax) * g")],
+     ["ginv_dense_ac_periodic"]),
+    ("Neumann forward DCT-II not orthonormal",
+     [('Wh = sfft.dctn(W, type=2, axes=ax, norm="ortho")', "Wh = sfft.dctn(W, type=2, axes=ax)")],
+     ["ginv_dense_none_neumann"]),
+    ("stopping norm weighted by the cell area",
+     [("s = sum(np.sqrt(np.sum(W[c] * W[c])) for c in range(W.shape[0]))",
+       "s = sum(np.sqrt(np.sum(W[c] * W[c]) * pb.lx * pb.ly / (pb.nx * pb.ny)) for c in range(W.shape[0]))")],
+     ["stop_rule_f_rel"]),
+    ("||Res|| without the 1/h_t",
+     [("return s / pb.dt, pb.tol", "return s, pb.tol")],
+     ["stop_rule_res_abs"]),
+    ("iteration started from U = 0 instead of U^k",
+     [("U = Uk.copy() if U0 is None", "U = np.zeros_like(Uk) if U0 is None")],
+     ["recurrence_unit", "recurrence_unequal"]),
+    ("extrapolation left out (P~ = P_{n+1})",
+     [("Pt = P + (1 + pb.omega) * pb.tau_p * Y", "Pt = P + pb.tau_p * Y")],
+     ["recurrence_unit", "nilpotent"]),
+    ("extrapolation weight omega taken as 1",
+     [("Pt = P + (1 + pb.omega) * pb.tau_p * Y", "Pt = P + 2 * pb.tau_p * Y")],
+     ["recurrence_omega"]),
+    ("dual step with tau_u",
+     [("P = P + pb.tau_p * Y ", "P = P + pb.tau_u * Y ")],
+     ["recurrence_unequal"]),
+    ("primal update with P_{n+1} instead of P~",
+     [("U = U - pb.tau_u * grad_F_T(pb, U, Pt)", "U = U - pb.tau_u * grad_F_T(pb, U, P)")],
+     ["recurrence_unit", "nilpotent"]),
+    ("primal update with the wrong sign",
+     [("U = U - pb.tau_u * grad_F_T(pb, U, Pt)", "U = U + pb.tau_u * grad_F_T(pb, U, Pt)")],
+     ["recurrence_unit", "newton_ac"]),
+]
+
+
+def _mutant_module(edits):
+    src = SRC
+    for old, new in edits:
+        assert src.count(old) == 1, "the line the mutant edits is not unique in the oracle: %r" % old
+        src = src.replace(old, new)
+    m = types.ModuleType("rd_oracle_mutant")
+    exec(compile(src, "rd_oracle_mutant", "exec"), m.__dict__)
+    return m
+
+
+def _plant(monkeypatch, edits):
+    m = _mutant_module(edits)
+    for name, obj in vars(m).items():
+        if isinstance(obj, types.FunctionType) and isinstance(getattr(rd_oracle, name, None), types.FunctionType):
+            monkeypatch.setattr(rd_oracle, name, obj)
+
+
+def _fails(pin):
+    try:
+        with np.errstate(all="ignore"):
+            pin()
+    except AssertionError:
+        return True
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(PINS))
+def test_pins_pass_on_the_oracle(name):
+    PINS[name]()
+
+
+@pytest.mark.parametrize("name,edits,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(monkeypatch, name, edits, pins):
+    _plant(monkeypatch, edits)
+    assert any(_fails(PINS[p]) for p in pins), "no pin caught: " + name
+
+
+def test_every_pin_is_used():
+    used = {p for _, _, pins in MUTANTS for p in pins}
+    assert used == set(PINS), set(PINS) - used
+
+
+def test_a_neutral_edit_fails_no_pin(monkeypatch):
+    """Control: an edit that keeps the arithmetic (the loaded copy of the oracle itself) fails
+    none of the pins, so the cases above fail for their mistakes and not for the loading."""
+    _plant(monkeypatch, [("return pb.lx / pb.nx, pb.ly / pb.ny", "return (pb.lx / pb.nx), (pb.ly / pb.ny)")])
+    assert rd_oracle.spacing.__module__ == "rd_oracle_mutant" or rd_oracle.spacing.__globals__["__name__"] == "rd_oracle_mutant"
+    failed = [name for name, pin in PINS.items() if _fails(pin)]
+    assert failed == []
