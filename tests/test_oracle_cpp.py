@@ -97,6 +97,23 @@ def test_cpp_oracle_equals_numpy_oracle(bc, kind, op, p, shape):
 
 
 @pytest.mark.parametrize("bc", ["periodic", "neumann"])
+@pytest.mark.parametrize("kind,op,p", KINDS)
+def test_cpp_oracle_equals_numpy_oracle_with_the_res_abs_rule(bc, kind, op, p):
+    """The paper's stopping rule ||Res|| = ||F|| / h_t <= delta (Section 2.1), with delta set to
+    stop near ||F|| = 1e-11: the same statuses, iteration counts, measures and results."""
+    pb = _pb(kind, op, p, bc, 16, 16)
+    pb = pb.replace(tol_kind="res_abs", tol=1e-11 / pb.dt)
+    r = WL.rng(77)
+    Uk = _state(pb, r)
+    Ua, ia = O.pdhg_step(pb, Uk, history=True)
+    Ub, ib = C.pdhg_step(pb, Uk, history=True)
+    assert ia["status"] == O.OK
+    assert (ia["status"], ia["iterations"]) == (ib["status"], ib["iterations"])
+    assert np.max(np.abs(ia["history"] - ib["history"])) <= 1e-11 * ia["history"][0]
+    assert _rel(Ub, Ua) <= 1e-12
+
+
+@pytest.mark.parametrize("bc", ["periodic", "neumann"])
 def test_unit_steps_are_nilpotent(bc):
     """Appendix A: reaction off, G = A^2, tau_u = tau_p = omega = 1 -- the per-mode iteration
     matrix is nilpotent, so the second iterate is the exact implicit step."""

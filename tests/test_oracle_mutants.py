@@ -9,19 +9,23 @@ oracle's for the duration of the case.  Each edited line must occur exactly once
 change to the oracle that removes it makes the case fail loudly instead of testing nothing.
 The pins are the functions of the other `tests/test_oracle_*.py` files, called unchanged: every
 one passes on the unmodified oracle, and at least one of a case's pins must fail on the mutant.
+The same is done for the C++ oracle (`oracle/rd_oracle_cpp.cpp`): each mutant source is compiled
+with g++ into a temporary library that the ctypes binding loads in place of the built one.
 """
 import inspect
+import subprocess
 import types
 
 import numpy as np
 import pytest
 
 import test_oracle_3d as T3
+import test_oracle_cpp as CPP
 import test_oracle_iteration as IT
 import test_oracle_operators as OPS
 import test_oracle_reactions as RX
 import test_oracle_stabilized as ST
-from oracle import rd_oracle
+from oracle import cpp_oracle, rd_oracle
 
 SRC = inspect.getsource(rd_oracle)
 GS = (2e-3, 1e-3, 0.04, 0.06)
@@ -251,4 +255,122 @@ def test_a_neutral_edit_fails_no_pin(monkeypatch):
     _plant(monkeypatch, [("return pb.lx / pb.nx, pb.ly / pb.ny", "return (pb.lx / pb.nx), (pb.ly / pb.ny)")])
     assert rd_oracle.spacing.__module__ == "rd_oracle_mutant" or rd_oracle.spacing.__globals__["__name__"] == "rd_oracle_mutant"
     failed = [name for name, pin in PINS.items() if _fails(pin)]
+    assert failed == []
+
+
+# ------------------------------------------------------------------------------------------
+# the C++ oracle
+# ------------------------------------------------------------------------------------------
+
+CPP_SRC = open(cpp_oracle.SRC).read()
+C = cpp_oracle
+
+CPP_PINS = {
+    "fft_is_the_dft": lambda: CPP.test_fft_is_the_dft(32),
+    "dct_pair": lambda: CPP.test_dct_pair_is_the_orthonormal_dct2(32),
+    "vs_numpy_ac_periodic": lambda: CPP.test_cpp_oracle_equals_numpy_oracle("periodic", "allen_cahn", "laplacian", (), (16, 16)),
+    "vs_numpy_ac_neumann": lambda: CPP.test_cpp_oracle_equals_numpy_oracle("neumann", "allen_cahn", "laplacian", (), (16, 16)),
+    "vs_numpy_split": lambda: CPP.test_cpp_oracle_equals_numpy_oracle("periodic", "ch_split", "neg_biharmonic", (), (16, 16)),
+    "vs_numpy_gs": lambda: CPP.test_cpp_oracle_equals_numpy_oracle("periodic", "gray_scott", "laplacian", GS, (16, 16)),
+    "vs_numpy_fch": lambda: CPP.test_cpp_oracle_equals_numpy_oracle("periodic", "fch", "functionalized", (), (16, 16)),
+    "nilpotent": lambda: CPP.test_unit_steps_are_nilpotent("periodic"),
+    "vs_numpy_res_abs": lambda: CPP.test_cpp_oracle_equals_numpy_oracle_with_the_res_abs_rule("periodic", "allen_cahn", "laplacian", ()),
+    "ac_uniform_ode": lambda: RX.test_allen_cahn_uniform_step_is_the_ode_step(0.3, C),
+    "ch_split_mode_0": lambda: RX.test_cahn_hilliard_split_mode("periodic", 1, 2, 0.0, C),
+    "gs_uniform_ode": lambda: RX.test_gray_scott_uniform_step_is_the_ode_step("periodic", 1.0, C),
+    "sch_uniform_ode": lambda: RX.test_schnakenberg_uniform_step_is_the_ode_step(1 / 1000, C),
+    "lap3_kron": lambda: T3.test_seven_point_laplacian_is_the_kron_sum("neumann", (3, 4, 5), C),
+    "ginv3_dense_gs": lambda: T3.test_3d_ginv_matches_dense_solve("periodic", "gray_scott", "laplacian", GS, C),
+}
+
+CPP_MUTANTS = [
+    ("Neumann ghost one point inside", [("return j < 0 ? 0 : n - 1;", "return j < 0 ? 1 : n - 2;")],
+     ["vs_numpy_ac_neumann", "lap3_kron"]),
+    ("h_y from the x side length",
+     [("hy2 = 1.0 / ((pb.ly / ny) * (pb.ly / ny))", "hy2 = 1.0 / ((pb.lx / ny) * (pb.lx / ny))")],
+     ["vs_numpy_ac_periodic", "lap3_kron"]),
+    ("z second difference weighted by h_y", [("- 2.0 * c) * hz2;", "- 2.0 * c) * hy2;")], ["lap3_kron"]),
+    ("Allen-Cahn reaction with the wrong sign",
+     [("const double f = -b * (U[q] * U[q] * U[q] - U[q]);", "const double f = b * (U[q] * U[q] * U[q] - U[q]);")],
+     ["ac_uniform_ode"]),
+    ("convex split: explicit term with the wrong sign",
+     [("if (!impl) W[q] += dt * b * Lk[q];", "if (!impl) W[q] -= dt * b * Lk[q];")], ["ch_split_mode_0"]),
+    ("Gray-Scott: u v^2 with a plus sign in u",
+     [("- dt * (Du * Lu[q] - uvv + F * (1.0 - u[q]));", "- dt * (Du * Lu[q] + uvv + F * (1.0 - u[q]));")],
+     ["gs_uniform_ode"]),
+    ("Gray-Scott: kill rate dropped", [("+ uvv - (F + k) * v[q]);", "+ uvv - F * v[q]);")], ["gs_uniform_ode"]),
+    ("Schnakenberg: linear decay with the wrong sign", [("kap * (as - u[q] + u2v)", "kap * (as + u[q] + u2v)")],
+     ["sch_uniform_ode"]),
+    ("sixth order: the printed W'' = 3u^2",
+     [("o[q] = pb.a * L[q] - pb.b * (3.0 * U[q] * U[q] - 1.0) * x[q] + pb.a * x[q];",
+       "o[q] = pb.a * L[q] - pb.b * (3.0 * U[q] * U[q]) * x[q] + pb.a * x[q];")],
+     ["vs_numpy_fch"]),
+    ("adjoint: Allen-Cahn reaction derivative dropped",
+     [("g[q] = Pt[q] - dt * a * L[q] - dt * fp * Pt[q];", "g[q] = Pt[q] - dt * a * L[q];")],
+     ["vs_numpy_ac_periodic"]),
+    ("adjoint: Gray-Scott coupling blocks not transposed",
+     [("- dt * v[q] * v[q] * Q[q];", "+ 2.0 * dt * u[q] * v[q] * Q[q];")], ["vs_numpy_gs"]),
+    ("FFT: the inverse with the forward sign", [("const double ang = sgn * 2.0 * kPi * k / len;",
+                                                 "const double ang = -2.0 * kPi * k / len;")], ["fft_is_the_dft"]),
+    ("FFT: bit reversal left out", [("if (i < j) std::swap(x[i], x[j]);", "")], ["fft_is_the_dft"]),
+    ("DCT-II: k = 0 scaled like the others",
+     [("X[k] = C * (k == 0 ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n));", "X[k] = C * std::sqrt(2.0 / n);")],
+     ["dct_pair"]),
+    ("DCT-III: Z_0 not doubled",
+     [("const double s = k == 0 ? 2.0 * std::sqrt(1.0 / n) : std::sqrt(2.0 / n);",
+       "const double s = k == 0 ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);")], ["dct_pair"]),
+    ("Neumann eigenvalues at the periodic frequencies",
+     [("d = pb.bc == BC_PERIODIC ? 1.0 : 2.0;", "d = 1.0;")], ["vs_numpy_ac_neumann"]),
+    ("preconditioner A_lin instead of A_lin^2", [("g[c * n + q] = r * r;", "g[c * n + q] = r;")],
+     ["nilpotent", "vs_numpy_ac_periodic"]),
+    ("two species: D_1 for both symbols", [("r = 1.0 + pb.p[c] * dt * m;", "r = 1.0 + pb.p[0] * dt * m;")],
+     ["ginv3_dense_gs", "vs_numpy_gs"]),
+    ("periodic inverse transform not normalised",
+     [("Y[q] = z[q].real() / (double)n;", "Y[q] = z[q].real();")], ["nilpotent"]),
+    ("extrapolation left out",
+     [("Pt[q] = P[q] + (1.0 + pb.omega) * pb.tau_p * Y[q];", "Pt[q] = P[q] + pb.tau_p * Y[q];")],
+     ["nilpotent"]),
+    ("||Res|| without the 1/h_t", [("*r = s / pb.dt;", "*r = s;")], ["vs_numpy_res_abs"]),
+    ("adjoint: convex split with W'' = 3u^2 - 1",
+     [("const double sh = pb.kind == K_CH_IMPLICIT ? 1.0 : 0.0;", "const double sh = 1.0;")], ["vs_numpy_split"]),
+]
+
+
+def _plant_cpp(monkeypatch, tmp_path, edits):
+    src = CPP_SRC
+    for old, new in edits:
+        assert src.count(old) == 1, "the line the mutant edits is not unique in the C++ oracle: %r" % old
+        src = src.replace(old, new)
+    cpp, so = tmp_path / "rd_oracle_mutant.cpp", tmp_path / "librd_oracle_mutant.so"
+    cpp.write_text(src)
+    r = subprocess.run(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-o", str(so), str(cpp)],
+                       stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    assert r.returncode == 0, r.stdout.decode(errors="replace")
+    monkeypatch.setattr(cpp_oracle, "LIB", str(so))
+    monkeypatch.setattr(cpp_oracle, "up_to_date", lambda: True)
+    monkeypatch.setattr(cpp_oracle, "_lib", None)
+    cpp_oracle.set_threads(1)
+
+
+@pytest.mark.parametrize("name", sorted(CPP_PINS))
+def test_cpp_pins_pass_on_the_oracle(name):
+    cpp_oracle.set_threads(1)
+    CPP_PINS[name]()
+
+
+@pytest.mark.parametrize("name,edits,pins", CPP_MUTANTS, ids=[m[0] for m in CPP_MUTANTS])
+def test_planted_mistake_in_the_cpp_oracle_fails_a_pin(monkeypatch, tmp_path, name, edits, pins):
+    _plant_cpp(monkeypatch, tmp_path, edits)
+    assert any(_fails(CPP_PINS[p]) for p in pins), "no pin caught: " + name
+
+
+def test_every_cpp_pin_is_used():
+    used = {p for _, _, pins in CPP_MUTANTS for p in pins}
+    assert used == set(CPP_PINS), set(CPP_PINS) - used
+
+
+def test_a_neutral_edit_of_the_cpp_oracle_fails_no_pin(monkeypatch, tmp_path):
+    _plant_cpp(monkeypatch, tmp_path, [("return j < 0 ? 0 : n - 1;", "return (j < 0) ? 0 : (n - 1);")])
+    assert cpp_oracle.load()._name.endswith("librd_oracle_mutant.so")
+    failed = [name for name, pin in CPP_PINS.items() if _fails(pin)]
     assert failed == []
