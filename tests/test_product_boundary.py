@@ -36,3 +36,16 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(rd, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         rd.load(str(tmp_path / "librd_pdhg.so"))
+
+
+def test_oracle_sources_reference_no_product_code():
+    """The oracle shares nothing with the CUDA path: no import of the package, no path into its
+    sources, no use of the product library."""
+    product_ref = re.compile(r"^\s*(from|import)\s+paper_2305_03945_gb300|^\s*#\s*include\s*[<\"][^>\"]*"
+                             r"(csrc|rd_pdhg|rd_internal|rd_device|rd_sweep)|librd_pdhg", re.M)
+    d = os.path.join(ROOT, "oracle")
+    files = [os.path.join(d, f) for f in os.listdir(d) if f.endswith(SOURCES)]
+    assert len(files) >= 6
+    hits = ["%s: %s" % (os.path.basename(p), m.group(0)) for p in files
+            for m in product_ref.finditer(open(p, encoding="utf-8").read())]
+    assert hits == []
