@@ -92,6 +92,10 @@ def set_threads(n: int) -> int:
 
 
 def _problem(pb) -> rdo_problem:
+    # the radix-2 FFT and the DCT through it take power-of-two lengths only
+    for n in (pb.nx, pb.ny) + ((pb.nz,) if pb.nz > 1 else ()):
+        if n < 1 or n & (n - 1):
+            raise ValueError("the C++ oracle needs power-of-two grid sides, got %d" % n)
     s = rdo_problem()
     s.nx, s.ny, s.lx, s.ly = pb.nx, pb.ny, pb.lx, pb.ly
     s.bc, s.op, s.kind = _BC[pb.bc], _OP[pb.op], _KIND[pb.kind]

@@ -182,3 +182,9 @@ def test_fixed_iteration_step_of_the_roofline_sweep():
     assert info_ref["status"] == O.OK
     U_3, _ = O.pdhg_step(pb.replace(max_iter=3), w.u0)
     assert np.linalg.norm(U_n - U_ref) < np.linalg.norm(U_3 - U_ref)
+
+
+def test_non_power_of_two_sides_refused():
+    pb = _pb("allen_cahn", "laplacian", (), "periodic", 16, 16).replace(nx=12)
+    with pytest.raises(ValueError, match="power-of-two"):
+        C.pdhg_step(pb, np.zeros(pb.shape))

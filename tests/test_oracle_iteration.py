@@ -253,6 +253,24 @@ def test_paper_allen_cahn_circle_iterations_below_200():
     assert max(its) < g["max_iterations"] and min(its) > 100
 
 
+def test_paper_allen_cahn_two_disks_at_most_200_iterations():
+    """Section 3.1.1, second example: the symmetric difference of two overlapping disks on
+    [0, 0.5]^2 (nodes at j h), tau = 0.5: no more than 200 iterations per step (the numpy oracle:
+    100 points a side is not a power of two)."""
+    g = GOLDEN["allen_cahn_two_disks"]
+    n = g["n"]
+    pb = WL.Problem(nx=n, ny=n, lx=g["side"], ly=g["side"], bc="periodic", op="laplacian",
+                    kind="allen_cahn", a=g["eps"], b=1 / g["eps"], dt=g["dt"], tau_u=g["tau"],
+                    tau_p=g["tau"], tol=g["delta"], tol_kind="res_abs")
+    x = np.arange(n) * g["side"] / n
+    X, Y = np.meshgrid(x, x)
+    inside = [(X - cx) ** 2 + (Y - cy) ** 2 < g["radius"] ** 2 for cx, cy in g["centres"]]
+    u0 = np.where(inside[0] ^ inside[1], 1.0, -1.0)[None]
+    _, infos = O.solve(pb, u0, 3)
+    assert all(i["status"] == O.OK for i in infos)
+    assert max(i["iterations"] for i in infos) <= g["max_iterations"]
+
+
 def test_paper_schnakenberg_about_30_iterations():
     """Section 3.4.1: about 30 PDHG iterations per time step (band 20..40)."""
     w = WL.config_schnakenberg(GOLDEN["schnakenberg"]["n"], 3)
