@@ -91,11 +91,16 @@ def set_threads(n: int) -> int:
     return load().rdo_set_threads(int(n))
 
 
-def _problem(pb) -> rdo_problem:
-    # the radix-2 FFT and the DCT through it take power-of-two lengths only
+def _transform_sides(pb):
+    """The radix-2 FFT and the DCT through it take power-of-two lengths only."""
+    if pb.precond == "none":
+        return
     for n in (pb.nx, pb.ny) + ((pb.nz,) if pb.nz > 1 else ()):
         if n < 1 or n & (n - 1):
-            raise ValueError("the C++ oracle needs power-of-two grid sides, got %d" % n)
+            raise ValueError("the C++ oracle's transforms need power-of-two grid sides, got %d" % n)
+
+
+def _problem(pb) -> rdo_problem:
     s = rdo_problem()
     s.nx, s.ny, s.lx, s.ly = pb.nx, pb.ny, pb.lx, pb.ly
     s.bc, s.op, s.kind = _BC[pb.bc], _OP[pb.op], _KIND[pb.kind]
@@ -141,6 +146,7 @@ def ghat(pb):
 
 
 def apply_ginv(pb, W):
+    _transform_sides(pb)
     W = _arr(W, pb)
     Y = np.empty(pb.shape)
     load().rdo_apply_ginv(ctypes.byref(_problem(pb)), _ptr(W), _ptr(Y))
@@ -149,6 +155,7 @@ def apply_ginv(pb, W):
 
 def pdhg_step(pb, Uk, history=False):
     """As rd_oracle.pdhg_step: (U, {iterations, status, residual[, history]})."""
+    _transform_sides(pb)
     Uk = _arr(Uk, pb)
     U = np.empty(pb.shape)
     it, st, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
