@@ -147,11 +147,13 @@ typedef enum {
 
 typedef enum {
     RD_LOOP_GRAPH = 0,    /* the PDHG iterations run in a WHILE node of the step's CUDA graph
-                             (graph_k iterations per trip) that the kernels end themselves: one
-                             graph launch per FP64 step or per defect-correction outer round  */
-    RD_LOOP_HOST = 1      /* plain CUDA graphs of graph_k iterations, launched until the host
-                             reads a finished state: the same kernels as ordinary graph kernel
-                             nodes (profilers cannot attribute kernels inside conditional nodes) */
+                             (graph_k iterations per trip) that the kernels end themselves, and
+                             the defect-correction outer rounds in a second WHILE node around
+                             it: one graph launch per step                                    */
+    RD_LOOP_HOST = 1      /* plain CUDA graphs of graph_k iterations (one outer round of defect
+                             correction at a time), launched until the host reads a finished
+                             state: the same kernels as ordinary graph kernel nodes (profilers
+                             cannot attribute kernels inside conditional nodes)                */
 } rd_solve_loop;
 
 typedef struct {
@@ -243,9 +245,10 @@ RD_API void rd_opts_default(rd_opts *o);
  *   cuda_stream: a cudaStream_t (NULL = legacy default stream); all work is issued on it.
  * Allocates every workspace (about 7 arrays of the grid size plus twiddle tables) and captures
  * the step graphs: the PDHG iteration loop runs on the device as a WHILE node of a CUDA graph
- * (graph_k iterations per trip) that the kernels end themselves, so that an FP64 step is one
- * graph launch and a defect-correction step one launch per outer round.  Needs a GPU and driver
- * with CUDA-graph conditional nodes.  On error *out is NULL. */
+ * (graph_k iterations per trip) that the kernels end themselves, and the outer rounds of
+ * defect correction as a WHILE node around it, so that a step of either precision is one graph
+ * launch and one host read.  Needs a GPU and driver with CUDA-graph conditional nodes.  On
+ * error *out is NULL. */
 RD_API rd_status rd_pdhg_create(rd_pdhg **out, const rd_grid *grid, rd_bc bc, rd_operator op,
                          const rd_reaction *reaction, double dt, double tau, double sigma,
                          const rd_precond *precond, const rd_opts *opts, void *cuda_stream);
@@ -265,7 +268,7 @@ RD_API rd_status rd_pdhg_solve_host(rd_pdhg *h, double *u_host, int nsteps, rd_s
 
 /* Change the physical time step h_t of a live handle (dt finite, > 0).  Every quantity that
  * depends on h_t (the residual and adjoint coefficients, the preconditioner symbol
- * (1 + c1 mu + c2 mu^2)^2) is re-derived and the step graphs are captured again, so a change
+ * (1 + c1 mu + c2 mu^2 + c3 mu^3)^2) is re-derived and the step graphs are captured again, so a change
  * costs about one graph capture; the tile plan and the workspaces are kept.  Synchronises the
  * handle's stream.  RD_ERR_INVALID_ARG leaves the handle unchanged. */
 RD_API rd_status rd_pdhg_set_dt(rd_pdhg *h, double dt);
@@ -325,13 +328,13 @@ RD_API void rd_pdhg_destroy(rd_pdhg *h);
  * (RD_RX_NONE, Allen-Cahn, Cahn-Hilliard, Gray-Scott or Schnakenberg; 2-D grids with sides powers
  * of two in [4, 1024], or -- scalar kinds -- 3-D grids with sides in [4, 512]; either boundary
  * condition) solved with FP32 PDHG sweeps (G = A_lin^2, RD_PC_LINEAR) inside FP64 defect
- * correction to the request's tolerance.  Small 2-D requests (up to 16 K points) run each inner solve in one launch
- * (rd_opts.small_solve).  The batch owns one device arena of hbm_budget_bytes; a request is
- * admitted when a slot is free and its workspace (about 48 bytes per grid point) fits the
- * arena, its state then stays resident on the GPU across all its steps, and all admitted
- * requests advance together in shared launches (one per equation kind and sweep kernel, over
- * every admitted grid size) of a CUDA graph that a library thread relaunches until the slot
- * finishes.  Requests submitted while others run are admitted as slots and memory free up.
+ * correction to the request's tolerance.  Small 2-D requests (up to 16 K points) run each
+ * inner solve in one launch (rd_opts.small_solve).  The batch owns one device arena of
+ * hbm_budget_bytes; a request is admitted when a slot is free and its workspace (about 48
+ * bytes per grid point) fits the arena, its state then stays resident on the GPU across all its
+ * steps, and all admitted requests advance together in shared launches (one per equation kind
+ * and sweep kernel, over every admitted grid size) of a CUDA graph that a library thread
+ * relaunches until the slot finishes.  Requests submitted while others run are admitted as slots and memory free up.
  * --------------------------------------------------------------------------------------- */
 typedef struct rd_batch rd_batch;
 
@@ -394,9 +397,9 @@ RD_API void rd_batch_destroy(rd_batch *b);
  * running inside a fixed memory budget it does not own, latency-critical loops that must not
  * pay the device-wide synchronisation of cudaMalloc / cudaFree, or callers holding no solver
  * handle.  It computes the same G = A_lin^2 solve as rd_pdhg_apply_precond of an RD_PC_LINEAR
- * handle for the 2-D equation described by (grid, bc, op, reaction, dt), with its scratch (transform buffer, twiddle and
- * eigenvalue tables) in one static device array of 2.5 MiB that every device loading the
- * library holds until process exit.
+ * handle for the 2-D equation described by (grid, bc, op, reaction, dt), with its scratch
+ * (transform buffer, twiddle and eigenvalue tables) in one static device array of 2.5 MiB that
+ * every device loading the library holds until process exit.
  *   w, y: device arrays of ncomp*ny*nx doubles (caller-owned; y may alias w).
  *   cuda_stream: cudaStream_t to issue the work on (NULL = legacy default); returns after the
  *   stream is synchronised.
