@@ -1334,8 +1334,9 @@ rd_status step_host(rd_pdhg* h, rd_step_info* info) {
 }
 
 // One implicit step on the handle's FP64 iterate U64 (holding U^k).  FP64: one graph launch
-// runs the whole step.  Defect correction: one graph launch per outer round; the host only
-// reads the outer state between rounds.
+// runs the whole step.  Defect correction: the first graph runs the outer rounds in a device
+// loop too; should that loop reach its bound with the step still active, the second graph
+// takes one host-driven round at a time (the host reading the outer state between them).
 rd_status step_impl(rd_pdhg* h, rd_step_info* info) {
   if (h->opts.solve_loop == RD_LOOP_HOST) return step_host(h, info);
   rd_step_info inf{};
