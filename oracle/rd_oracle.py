@@ -11,9 +11,11 @@ Everything is written for readability against the paper (arxiv 2305.03945):
                           Cahn-Hilliard, Section 3.4.1 for the two-species Schnakenberg system
   adjoint Jacobian        the U-update of the G-prox dynamic (eqs. G-prox RD pdhg dynamic 3,
                           G-prox RD pdhg dynamic CH 3, Section 3.4.1 U/V updates)
-  preconditioner          G = A_lin^2 (Section 2.1 "Choosing the matrix G"), inverted in the
-                          Fourier basis (periodic) or DCT-II basis (Neumann), Section 2.1
-                          "Application of FFT" and Remark 1
+  preconditioner          G = A_lin^2 (Section 2.1 "Choosing the matrix G"), or the
+                          stabilised square of F's Jacobian with its nonlinear factor set to a
+                          constant (Section 3.3's construction), inverted in the Fourier basis
+                          (periodic) or DCT-II basis (Neumann), Section 2.1 "Application of
+                          FFT" and Remark 1
   iteration               G-prox PDHG (eqs. G-prox linearized pdhg dynamic 1-3) inside
                           Algorithm 1, initial guess U_0 = U^k, P_0 = 0, extrapolation omega,
                           stopping rule ||Res(U_n)||_2 <= delta (Section 2.1 "Stopping criterion")
