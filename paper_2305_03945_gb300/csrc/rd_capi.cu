@@ -367,10 +367,11 @@ cudaError_t fch_iteration(rd_pdhg* h, cudaStream_t s, cudaEvent_t* ev) {
 // WHILE node above; or one small-solve launch), k_axpy_dc, k_resid64:
 //   first = true : k_begin, k_resid64, ROUND, k_loop_cond(outer), WHILE { ROUND, k_loop_cond(outer) }, k_mass
 //   first = false: ROUND, k_mass   (one host-driven round, the fallback beyond the loop's bound)
-// Iteration 1 and outer round 1 sit outside the loops so that the profiling events (which a conditional
-// body cannot hold) bracket the first iteration's kernels.  k_loop_cond, run after iteration 1
-// (outer round 1) and at the end of every trip, sets its loop's condition: 1 while the solve (the
-// outer state) is active, 0 once it has ended or after max_iter + slack launches.  k_axpy_dc,
+// Iteration 1 and the first outer round sit outside the loops so that the profiling events
+// (which a conditional body cannot hold) bracket the first iteration's kernels.  k_loop_cond,
+// run after iteration 1 (the first outer round) and at the end of every trip, sets its loop's
+// condition: 1 while the solve (the outer state) is active, 0 once it has ended or after
+// max_iter + slack launches.  k_axpy_dc,
 // k_resid64 and k_mass act only while (resp. once no longer) the outer state is active.
 // Step-level launches of either grid kind: the step set-up and the FP64 residual.
 cudaError_t begin_any(rd_pdhg* h, State* st, const double* uk, double tol, int tol_kind, int nb, cudaStream_t s) {
@@ -506,7 +507,7 @@ rd_status capture_step_graph(rd_pdhg* h, bool first, cudaGraph_t* out, cudaGraph
     if ((e = inner_solve(cs, ev1, cond, h->body_stream)) != cudaSuccess)
       return abort_capture(cs, "the PDHG loop", e);
   } else if (outer_loop) {
-    // outer round 1 outside the outer loop (the profiling events cannot sit in a conditional body)
+    // the first outer round outside the outer loop (the profiling events cannot sit in a conditional body)
     e = round(cs, ev1, cond, h->body_stream);
     if (e == cudaSuccess) e = launch_loop_cond(st0, cond_o, 1u, cs);
     if (e != cudaSuccess) return abort_capture(cs, "the first outer round", e);
