@@ -3,6 +3,8 @@ declares (no compute calls: this runs without a GPU)."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -27,6 +29,45 @@ def test_library_exports_every_declared_symbol():
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
     assert set(rd.EXPORTS) == set(_declared())
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_header_is_plain_c_and_links_against_the_library(tmp_path):
+    """A C99 caller with every warning as an error: the header needs no C++ and no CUDA headers,
+    and a program calling the method's entry points links against the built library."""
+    from paper_2305_03945_gb300 import build
+    lib = build.build()
+    src = tmp_path / "caller.c"
+    src.write_text("""
+#include <stdio.h>
+#include "rd_pdhg.h"
+int run(double *d_u) {
+  rd_grid g = {2, {64, 64, 1}, {1.0, 1.0, 1.0}};
+  rd_reaction rx = {RD_RX_ALLEN_CAHN, 1, 0.1, 10.0, {0}};
+  rd_precond pc = {RD_PC_STABILIZED, 2.0};
+  rd_opts o;
+  rd_pdhg *h = NULL;
+  rd_step_info info;
+  rd_opts_default(&o);
+  o.precision = RD_PREC_FP32_DC;
+  if (rd_pdhg_create(&h, &g, RD_BC_PERIODIC, RD_OP_LAPLACIAN, &rx, 1e-2, 1.0, 1.0, &pc, &o, NULL) != RD_OK) {
+    fprintf(stderr, "%s\\n", rd_last_error());
+    return 1;
+  }
+  rd_pdhg_step(h, d_u, d_u, &info);
+  rd_pdhg_solve(h, d_u, 2, NULL);
+  rd_pdhg_destroy(h);
+  return info.status;
+}
+""")
+    obj, so = tmp_path / "caller.o", tmp_path / "libcaller.so"
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fPIC", "-I", inc, "-c",
+                        str(src), "-o", str(obj)], stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    assert r.returncode == 0, r.stdout.decode()
+    r = subprocess.run(["gcc", "-shared", "-o", str(so), str(obj), "-L", os.path.dirname(lib), "-lrd_pdhg"],
+                       stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    assert r.returncode == 0, r.stdout.decode()
 
 
 def test_status_strings_and_argument_checks_without_gpu():
