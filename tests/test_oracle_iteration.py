@@ -271,6 +271,30 @@ def test_paper_allen_cahn_two_disks_at_most_200_iterations():
     assert max(i["iterations"] for i in infos) <= g["max_iterations"]
 
 
+def test_allen_cahn_circle_shrinks_by_its_curvature_law():
+    """Section 3.1.1's shrinking circle: with a = eps, b = 1/eps the zero level set of Allen-Cahn
+    moves with normal speed eps times its curvature, so a circle's radius follows
+    r(t)^2 = r0^2 - 2 eps t (asymptotically in eps; a sanity band).  On [-0.25, 0.25)^2 with
+    eps = 0.02, 64 points a side (h < eps) and h_t = 2e-3, the radius of the area {u > 0} after 100
+    implicit steps (t = 0.2, r from 0.2 to 0.179) stays within 2% of the law; a mistaken scaling
+    of either term (a = eps^2, or b = 1 / eps^2) moves it by far more.  The C++ oracle on all host
+    cores (the numpy one takes about 15 s here)."""
+    from oracle import cpp_oracle
+    n, side, eps, r0, dt, steps = 64, 0.5, 0.02, 0.2, 2e-3, 100
+    pb = WL.Problem(nx=n, ny=n, lx=side, ly=side, bc="periodic", op="laplacian", kind="allen_cahn",
+                    a=eps, b=1 / eps, dt=dt, tau_u=0.5, tau_p=0.5, tol=1e-7, tol_kind="res_abs")
+    x = -side / 2 + np.arange(n) * side / n
+    X, Y = np.meshgrid(x, x)
+    u0 = np.where(X ** 2 + Y ** 2 < r0 ** 2, 1.0, -1.0)[None]
+    cpp_oracle.set_threads(0)
+    U, infos = cpp_oracle.solve(pb, u0, steps)
+    assert len(infos) == steps and all(i["status"] == cpp_oracle.OK for i in infos)
+    h = side / n
+    r = math.sqrt(np.sum(U[0] > 0) * h * h / math.pi)
+    law = math.sqrt(r0 ** 2 - 2 * eps * steps * dt)
+    assert abs(r / law - 1) <= 0.02, (r, law)
+
+
 def test_paper_schnakenberg_about_30_iterations():
     """Section 3.4.1: about 30 PDHG iterations per time step (band 20..40)."""
     w = WL.config_schnakenberg(GOLDEN["schnakenberg"]["n"], 3)
