@@ -308,6 +308,21 @@ def test_not_converged_status():
     assert info["status"] == O.NOT_CONVERGED and info["iterations"] == 3
 
 
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_non_finite_state_diverges_before_any_update(bad):
+    """A NaN or Inf in U^k makes the first measure non-finite: DIVERGED with 0 updates, in both
+    oracles, and the returned U is U^k."""
+    from oracle import cpp_oracle
+    w = WL.config_allen_cahn_periodic(16, 1)
+    uk = w.u0.copy()
+    uk[0, 3, 5] = bad
+    for M in (O, cpp_oracle):
+        with np.errstate(invalid="ignore", over="ignore"):
+            U, info = M.pdhg_step(w.problem.replace(tol_kind="f_rel", tol=1e-11), uk)
+        assert info["status"] == M.DIVERGED and info["iterations"] == 0
+        assert np.array_equal(U, uk, equal_nan=True)
+
+
 def test_zero_state_converges_immediately():
     w = WL.config_allen_cahn_periodic(16, 1)
     U, info = O.pdhg_step(w.problem.replace(tol_kind="f_rel", tol=1e-11), np.zeros((1, 16, 16)))
