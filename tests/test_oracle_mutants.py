@@ -20,12 +20,13 @@ import numpy as np
 import pytest
 
 import test_oracle_3d as T3
+import test_oracle_adapt as AD
 import test_oracle_cpp as CPP
 import test_oracle_iteration as IT
 import test_oracle_operators as OPS
 import test_oracle_reactions as RX
 import test_oracle_stabilized as ST
-from oracle import cpp_oracle, rd_oracle
+from oracle import adapt, cpp_oracle, rd_oracle, theory
 
 SRC = inspect.getsource(rd_oracle)
 GS = (2e-3, 1e-3, 0.04, 0.06)
@@ -207,21 +208,22 @@ MUTANTS = [
 ]
 
 
-def _mutant_module(edits):
-    src = SRC
+def _mutant_module(edits, module=rd_oracle):
+    src = SRC if module is rd_oracle else inspect.getsource(module)
     for old, new in edits:
-        assert src.count(old) == 1, "the line the mutant edits is not unique in the oracle: %r" % old
+        assert src.count(old) == 1, "the line the mutant edits is not unique in %s: %r" % (module.__name__, old)
         src = src.replace(old, new)
     m = types.ModuleType("rd_oracle_mutant")
+    m.__package__ = module.__package__      # the module's own relative imports
     exec(compile(src, "rd_oracle_mutant", "exec"), m.__dict__)
     return m
 
 
-def _plant(monkeypatch, edits):
-    m = _mutant_module(edits)
+def _plant(monkeypatch, edits, module=rd_oracle):
+    m = _mutant_module(edits, module)
     for name, obj in vars(m).items():
-        if isinstance(obj, types.FunctionType) and isinstance(getattr(rd_oracle, name, None), types.FunctionType):
-            monkeypatch.setattr(rd_oracle, name, obj)
+        if isinstance(obj, types.FunctionType) and isinstance(getattr(module, name, None), types.FunctionType):
+            monkeypatch.setattr(module, name, obj)
 
 
 def _fails(pin):
@@ -257,6 +259,59 @@ def test_a_neutral_edit_fails_no_pin(monkeypatch):
     failed = [name for name, pin in PINS.items() if _fails(pin)]
     assert failed == []
 
+
+# ------------------------------------------------------------------------------------------
+# the adaptive step-size rule (oracle/adapt.py) and the linear theory (oracle/theory.py)
+# ------------------------------------------------------------------------------------------
+
+AUX_PINS = {
+    "rule_shrink": lambda: AD.test_step_size_rule_cases(0.4, 41, 0.2),
+    "rule_at_n_hi": lambda: AD.test_step_size_rule_cases(0.4, 40, 0.4),
+    "rule_at_n_lo": lambda: AD.test_step_size_rule_cases(0.4, 25, 0.4),
+    "rule_cap": lambda: AD.test_step_size_rule_cases(0.8, 3, 0.8),
+    "no_rule_fires": AD.test_no_rule_fires_equals_fixed_steps,
+    "failed_steps": AD.test_failed_steps_shrink_and_rule_holds,
+    "rate": IT.test_rate_function_and_bound,
+    "iteration_matrix": IT.test_random_data_follow_preconditioned_iteration_matrix,
+    "eta_gamma": lambda: IT.test_eta_gamma_closed_forms(3.0),
+    "recurrence": lambda: IT.test_single_mode_history_matches_recurrence("periodic", "laplacian", (0.7, 0.7), 1.0, "linear"),
+}
+
+AUX_MUTANTS = [
+    (adapt, "shrink already at M = N^*", [("if m > n_hi:", "if m >= n_hi:")], ["rule_at_n_hi"]),
+    (adapt, "enlarge already at M = N_*", [("if m < n_lo:", "if m <= n_lo:")], ["rule_at_n_lo"]),
+    (adapt, "no cap at h_t^0", [("return up if up <= dt0 else dt", "return up")], ["rule_cap"]),
+    (adapt, "shrink by 1/eta", [("return eta * dt", "return dt / eta")], ["rule_shrink"]),
+    (adapt, "last step not shortened to t_end", [("h = min(dt, t_end - t)", "h = dt")], ["failed_steps"]),
+    (adapt, "accepted step does not advance the state", [("U = Un\n", "U = U\n")], ["no_rule_fires", "failed_steps"]),
+    (theory, "f(t) = 1 - t below 1", [("return math.sqrt(1 - t)", "return 1 - t")], ["rate"]),
+    (theory, "f(t) above 1 with t^2 + t", [("return t - 1 + math.sqrt(t * t - t)", "return t - 1 + math.sqrt(t * t + t)")],
+     ["rate"]),
+    (theory, "iteration matrix without the extrapolation",
+     [("return np.array([[1 - (1 + omega) * t, -tau_u * lam], [tau_p * lam, 1.0]])",
+       "return np.array([[1 - omega * t, -tau_u * lam], [tau_p * lam, 1.0]])")], ["iteration_matrix", "rate"]),
+    (theory, "eta_* bracket with kappa for 2 kappa", [("+ 2 * kappa - 0.25 / k2", "+ kappa - 0.25 / k2")], ["eta_gamma"]),
+    (theory, "gamma_* with 1 for 2", [("return math.sqrt(1 - 2 / _bracket(kappa))", "return math.sqrt(1 - 1 / _bracket(kappa))")],
+     ["eta_gamma"]),
+    (theory, "single-mode recurrence without the extrapolation",
+     [("pt = p + (1 + omega) * tau_p * y", "pt = p + tau_p * y")], ["recurrence"]),
+]
+
+
+@pytest.mark.parametrize("name", sorted(AUX_PINS))
+def test_aux_pins_pass_on_the_oracle(name):
+    AUX_PINS[name]()
+
+
+@pytest.mark.parametrize("module,name,edits,pins", AUX_MUTANTS, ids=[m[1] for m in AUX_MUTANTS])
+def test_planted_mistake_in_the_rule_or_theory_fails_a_pin(monkeypatch, module, name, edits, pins):
+    _plant(monkeypatch, edits, module)
+    assert any(_fails(AUX_PINS[p]) for p in pins), "no pin caught: " + name
+
+
+def test_every_aux_pin_is_used():
+    used = {p for _, _, _, pins in AUX_MUTANTS for p in pins}
+    assert used == set(AUX_PINS), set(AUX_PINS) - used
 
 # ------------------------------------------------------------------------------------------
 # the C++ oracle
