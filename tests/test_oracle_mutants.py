@@ -26,7 +26,7 @@ import test_oracle_iteration as IT
 import test_oracle_operators as OPS
 import test_oracle_reactions as RX
 import test_oracle_stabilized as ST
-from oracle import adapt, cpp_oracle, rd_oracle, theory
+from oracle import adapt, cpp_oracle, dense, rd_oracle, theory
 
 SRC = inspect.getsource(rd_oracle)
 GS = (2e-3, 1e-3, 0.04, 0.06)
@@ -261,7 +261,8 @@ def test_a_neutral_edit_fails_no_pin(monkeypatch):
 
 
 # ------------------------------------------------------------------------------------------
-# the adaptive step-size rule (oracle/adapt.py) and the linear theory (oracle/theory.py)
+# the adaptive step-size rule (oracle/adapt.py), the linear theory (oracle/theory.py) and the
+# dense matrices the pins compare against (oracle/dense.py)
 # ------------------------------------------------------------------------------------------
 
 AUX_PINS = {
@@ -275,6 +276,12 @@ AUX_PINS = {
     "iteration_matrix": IT.test_random_data_follow_preconditioned_iteration_matrix,
     "eta_gamma": lambda: IT.test_eta_gamma_closed_forms(3.0),
     "recurrence": lambda: IT.test_single_mode_history_matches_recurrence("periodic", "laplacian", (0.7, 0.7), 1.0, "linear"),
+    "neumann_diagonals_as_printed": OPS.test_neumann_block_diagonals_as_printed,
+    "dense_periodic_block_matrix": lambda: OPS.test_stencil_equals_paper_block_matrix("periodic", 5),
+    "dense_jacobian_ac": lambda: OPS.test_adjoint_jacobian_by_complex_step("periodic", "allen_cahn", "laplacian", ()),
+    "dense_F_gs": lambda: OPS.test_residual_matches_dense_form("periodic", "gray_scott", "laplacian", GS),
+    "dense_G_ac": lambda: OPS.test_ginv_matches_dense_solve("periodic", "allen_cahn", "laplacian", ()),
+    "dense_G_ch": lambda: OPS.test_ginv_matches_dense_solve("neumann", "ch_implicit", "neg_biharmonic", ()),
 }
 
 AUX_MUTANTS = [
@@ -295,6 +302,22 @@ AUX_MUTANTS = [
      ["eta_gamma"]),
     (theory, "single-mode recurrence without the extrapolation",
      [("pt = p + (1 + omega) * tau_p * y", "pt = p + tau_p * y")], ["recurrence"]),
+    (dense, "Lap^N with interior diagonals in the edge blocks",
+     [("L1 = _tridiag(n, [-2.0] + [-3.0] * (n - 2) + [-2.0])", "L1 = _tridiag(n, [-3.0] * n)")],
+     ["neumann_diagonals_as_printed"]),
+    (dense, "Lap^P without its corner entries", [("L[0, n - 1] = 1.0", "L[0, n - 1] = 0.0")],
+     ["dense_periodic_block_matrix"]),
+    (dense, "dense Allen-Cahn Jacobian with W'' = 3u^2 + 1",
+     [("return A + np.diag(dt * b * (3 * U ** 2 - 1))", "return A + np.diag(dt * b * (3 * U ** 2 + 1))")],
+     ["dense_jacobian_ac"]),
+    (dense, "dense Gray-Scott u v^2 with the wrong sign",
+     [("Fu = Au @ u - uk + dt * (u * v * v) - dt * Ff * (1 - u)", "Fu = Au @ u - uk - dt * (u * v * v) - dt * Ff * (1 - u)")],
+     ["dense_F_gs"]),
+    (dense, "dense G = A_lin instead of A_lin^2",
+     [("G[c * n:(c + 1) * n, c * n:(c + 1) * n] = A @ A", "G[c * n:(c + 1) * n, c * n:(c + 1) * n] = A")],
+     ["dense_G_ac"]),
+    (dense, "dense Cahn-Hilliard A_lin with the other sign", [("return [I + pb.a * pb.dt * (L @ L)]", "return [I - pb.a * pb.dt * (L @ L)]")],
+     ["dense_G_ch"]),
 ]
 
 
