@@ -47,3 +47,27 @@ def test_poisson_arrivals_have_the_rate():
     gaps = np.diff(np.concatenate([[0.0], t]))
     assert np.all(gaps > 0) and abs(gaps.mean() * 8.0 - 1) < 0.03
     assert np.array_equal(t, WL.poisson_arrivals(20000, rate=8.0))
+
+
+def test_gray_scott_patches_recipe():
+    """u = 1, v = 0 outside the patches, (0.5, 0.25) inside, each value within 1% noise; the
+    patches (side n / 12.8, 10 of them, possibly overlapping) cover at most 10 side^2 points."""
+    n = 128
+    U = WL.gray_scott_patches(4000, n)
+    u, v = U[0], U[1]
+    assert U.shape == (2, n, n)
+    inside = v > 0
+    assert np.all(np.abs(u[~inside] - 1) <= 0.01 + 1e-15) and np.all(v[~inside] == 0)
+    assert np.all(np.abs(u[inside] / 0.5 - 1) <= 0.01 + 1e-15) and np.all(np.abs(v[inside] / 0.25 - 1) <= 0.01 + 1e-15)
+    side = round(n / 12.8)
+    assert side * side <= inside.sum() <= 10 * side * side
+
+
+def test_smoothed_tanh_recipe():
+    """tanh of smoothed noise scaled by its standard deviation: values in (-1, 1), zero-mean to
+    sampling error, and smooth on the 8-cell scale (neighbour differences far below the range)."""
+    u = WL.smoothed_tanh(2000, 256, 256)
+    assert u.shape == (256, 256) and np.all(np.abs(u) < 1)
+    assert abs(u.mean()) < 0.2
+    assert np.max(np.abs(np.diff(u, axis=1))) < 0.25 * (u.max() - u.min())
+    assert np.array_equal(u, WL.smoothed_tanh(2000, 256, 256))
